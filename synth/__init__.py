@@ -1,0 +1,261 @@
+"""Seeded synthetic inputs for the low-rank MEG workloads.
+
+This module only draws data: planted matrices, noise, sampling masks,
+measurement vectors, arrival traces.  It holds none of the method's
+arithmetic (no gradient, no eigensolver, no mirror step), so both the
+CPU oracle and the CUDA path may take their inputs from here.
+
+Every array that the GPU stores in reduced precision is rounded here, at
+generation time, so that both sides see bit-identical data:
+
+* dense data for the mixed-precision path is rounded to bfloat16
+  (round-to-nearest-even) and returned as float64 values together with
+  the raw uint16 bit patterns;
+* CSR values are rounded to float32;
+* measurement vectors are rounded to bfloat16.
+
+Workload recipes (the paper's experiments, Section 7, are synthetic):
+
+* ``dense_quadratic``: M = U diag(w) U^T + E, U orthonormal (QR of a
+  Gaussian matrix), E symmetric with i.i.d. N(0, sigma^2) entries on and
+  above the diagonal, mirrored below.
+* ``completion``: planted trace-1 rank-r PSD M, Omega a uniform sample of
+  upper-triangle positions (diagonal included), mirrored.
+* ``measurements``: a_i ~ N(0, I_n), X* trace-1 rank-r PSD,
+  y_i = a_i^T X* a_i (noiseless).
+* ``linear``: C symmetric with i.i.d. N(0,1) upper triangle.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+__all__ = [
+    "bf16_round", "bf16_bits", "sym_noise", "orthonormal", "dense_quadratic",
+    "completion", "measurements", "linear", "arrival_trace", "DenseQuadratic",
+    "Completion", "Measurements", "Linear", "config",
+]
+
+
+# ---------------------------------------------------------------- rounding
+def bf16_bits(x: np.ndarray) -> np.ndarray:
+    """Round float values to bfloat16 (nearest, ties to even); uint16 bits."""
+    f = np.ascontiguousarray(np.asarray(x, dtype=np.float64).astype(np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    bias = ((u >> np.uint64(16)) & np.uint64(1)) + np.uint64(0x7FFF)
+    u = ((u + bias) >> np.uint64(16)) & np.uint64(0xFFFF)
+    return u.astype(np.uint16)
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Values of ``bf16_bits(x)`` as float64."""
+    b = bf16_bits(x).astype(np.uint32) << np.uint32(16)
+    return b.view(np.float32).astype(np.float64)
+
+
+def _round(x: np.ndarray, storage: str) -> np.ndarray:
+    if storage == "f64":
+        return np.asarray(x, dtype=np.float64)
+    if storage == "f32":
+        return np.asarray(x, dtype=np.float64).astype(np.float32).astype(np.float64)
+    if storage == "bf16":
+        return bf16_round(x)
+    raise ValueError(f"unknown storage {storage!r}")
+
+
+# ---------------------------------------------------------------- pieces
+def orthonormal(rng: np.random.Generator, n: int, r: int) -> np.ndarray:
+    """Orthonormal n x r matrix: the Q factor of a Gaussian n x r matrix."""
+    q, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    return q
+
+
+def sym_noise(rng: np.random.Generator, n: int, sigma: float) -> np.ndarray:
+    """Symmetric noise: i.i.d. N(0, sigma^2) on and above the diagonal."""
+    e = np.triu(rng.standard_normal((n, n)) * sigma)
+    return e + np.triu(e, 1).T
+
+
+@dataclasses.dataclass
+class DenseQuadratic:
+    """f(X) = 1/2 ||X - M||_F^2 over the spectrahedron."""
+    n: int
+    M: np.ndarray            # float64 values (already rounded to `storage`)
+    storage: str             # "f64" | "f32" | "bf16"
+    U: np.ndarray            # planted factor (for diagnostics only)
+    w: np.ndarray            # planted weights
+
+    def bits(self) -> np.ndarray:
+        """Row-major data in the storage format (bf16 -> uint16 bits)."""
+        if self.storage == "bf16":
+            return bf16_bits(self.M)
+        if self.storage == "f32":
+            return self.M.astype(np.float32)
+        return self.M
+
+
+def dense_quadratic(n: int, r: int, seed: int, weights=None, sigma: float = 1e-5,
+                    storage: str = "f64") -> DenseQuadratic:
+    """Planted rank-r trace-1 PSD matrix plus symmetric Gaussian noise.
+
+    ``weights`` None draws w ~ Dirichlet(1_r); otherwise the given weights.
+    """
+    rng = np.random.default_rng(seed)
+    U = orthonormal(rng, n, r)
+    if weights is None:
+        w = rng.dirichlet(np.ones(r))
+    else:
+        w = np.asarray(weights, dtype=np.float64)
+    M = (U * w) @ U.T + sym_noise(rng, n, sigma)
+    M = 0.5 * (M + M.T)
+    return DenseQuadratic(n=n, M=_round(M, storage), storage=storage, U=U, w=w)
+
+
+@dataclasses.dataclass
+class Linear:
+    """f(X) = <C, X>."""
+    n: int
+    C: np.ndarray
+    storage: str
+
+    def bits(self) -> np.ndarray:
+        if self.storage == "bf16":
+            return bf16_bits(self.C)
+        if self.storage == "f32":
+            return self.C.astype(np.float32)
+        return self.C
+
+
+def linear(n: int, seed: int, scale: float = 1.0, storage: str = "f64") -> Linear:
+    rng = np.random.default_rng(seed)
+    C = sym_noise(rng, n, scale)
+    return Linear(n=n, C=_round(C, storage), storage=storage)
+
+
+@dataclasses.dataclass
+class Completion:
+    """f(X) = 1/2 sum_{(i,j) in Omega} (X_ij - M_ij)^2, Omega mirrored.
+
+    CSR arrays hold every stored (i, j) once per direction: an off-diagonal
+    sample appears as (i, j) and (j, i); a diagonal sample once.
+    """
+    n: int
+    rowptr: np.ndarray       # int32 [n+1]
+    col: np.ndarray          # int32 [nnz], sorted within each row
+    val: np.ndarray          # float64 values of M_ij rounded to float32
+    U: np.ndarray
+    w: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+
+def completion(n: int, r: int, frac: float, seed: int) -> Completion:
+    """Planted trace-1 rank-r PSD M, a uniform fraction of the upper triangle."""
+    rng = np.random.default_rng(seed)
+    U = orthonormal(rng, n, r)
+    w = rng.dirichlet(np.ones(r))
+    n_up = n * (n + 1) // 2
+    cnt = int(round(frac * n_up))
+    # sample distinct linear indices of the upper triangle (incl. diagonal)
+    lin = np.unique(rng.integers(0, n_up, size=int(cnt * 1.02) + 16, dtype=np.int64))
+    lin = rng.permutation(lin)[:cnt]
+    lin.sort()
+    # row i of the upper triangle starts at i*n - i*(i-1)/2
+    starts = np.arange(n, dtype=np.int64) * n - (np.arange(n, dtype=np.int64) * (np.arange(n, dtype=np.int64) - 1)) // 2
+    i = np.searchsorted(starts, lin, side="right") - 1
+    j = i + (lin - starts[i])
+    off = i != j
+    rows = np.concatenate([i, j[off]])
+    cols = np.concatenate([j, i[off]])
+    order = np.lexsort((cols, rows))
+    rows, cols = rows[order], cols[order]
+    vals = np.einsum("kr,kr->k", U[rows] * w, U[cols])
+    vals = vals.astype(np.float32).astype(np.float64)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return Completion(n=n, rowptr=rowptr.astype(np.int32), col=cols.astype(np.int32),
+                      val=vals, U=U, w=w)
+
+
+@dataclasses.dataclass
+class Measurements:
+    """f(X) = (1/m) sum_i (a_i^T X a_i - y_i)^2, sampled L at a time."""
+    n: int
+    A: np.ndarray            # m x n, float64 values rounded to bf16
+    y: np.ndarray            # m, float64
+    L: int                   # minibatch size
+    U: np.ndarray
+    w: np.ndarray
+
+    @property
+    def m(self) -> int:
+        return int(self.A.shape[0])
+
+    def bits(self) -> np.ndarray:
+        return bf16_bits(self.A)
+
+
+def measurements(n: int, r: int, m: int, L: int, seed: int,
+                 chunk: int = 4096) -> Measurements:
+    """a_i ~ N(0, I_n) rounded to bf16, y_i = a_i^T X* a_i in float64."""
+    rng = np.random.default_rng(seed)
+    U = orthonormal(rng, n, r)
+    w = rng.dirichlet(np.ones(r))
+    A = np.empty((m, n), dtype=np.float64)
+    y = np.empty(m, dtype=np.float64)
+    for s in range(0, m, chunk):
+        e = min(m, s + chunk)
+        a = bf16_round(rng.standard_normal((e - s, n)))
+        A[s:e] = a
+        p = a @ U
+        y[s:e] = (p * p) @ w
+    return Measurements(n=n, A=A, y=y, L=L, U=U, w=w)
+
+
+def arrival_trace(count: int, rate: float, seed: int, n_lo: int = 64, n_hi: int = 1024,
+                  r_max: int = 8):
+    """Poisson arrivals: (time_s, n, r, kind) with n log-uniform, r uniform."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    times = np.cumsum(gaps)
+    n = np.floor(np.exp(rng.uniform(math.log(n_lo), math.log(n_hi), size=count))).astype(int)
+    r = rng.integers(1, r_max + 1, size=count)
+    kind = rng.integers(0, 2, size=count)   # 0: dense quadratic, 1: measurements
+    return [(float(times[i]), int(n[i]), int(r[i]), int(kind[i])) for i in range(count)]
+
+
+# ---------------------------------------------------------------- named workloads
+CONFIG0_WEIGHTS = (0.4, 0.25, 0.15, 0.12, 0.08)
+
+
+def config(i: int, scale: Optional[int] = None, storage: Optional[str] = None):
+    """The named workloads, seeds 1000 + i.
+
+    ``scale`` replaces n by a smaller value with the same recipe (test sizes).
+    0: dense quadratic n=200 r=5, fixed weights, sigma=1e-4, float64.
+    1: dense quadratic n=4096 r=10, Dirichlet weights, sigma=1e-5, bf16.
+    2: completion n=20000 r=8, 1% of the upper triangle.
+    3: measurements n=2048 r=4, m=50000, L=256.
+    """
+    seed = 1000 + i
+    if i == 0:
+        n = scale or 200
+        return dense_quadratic(n, 5, seed, weights=CONFIG0_WEIGHTS, sigma=1e-4,
+                               storage=storage or "f64")
+    if i == 1:
+        n = scale or 4096
+        return dense_quadratic(n, 10, seed, sigma=1e-5, storage=storage or "bf16")
+    if i == 2:
+        n = scale or 20000
+        return completion(n, 8, 0.01 if scale is None else max(0.01, 200.0 / n), seed)
+    if i == 3:
+        n = scale or 2048
+        m = 50000 if scale is None else 20 * n
+        return measurements(n, 4, m, 256 if scale is None else 64, seed)
+    raise ValueError(i)

@@ -1,0 +1,368 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms, exact special cases computed at 50 digits, invariants, brute
+force on tiny inputs, and the inequalities of Lemma 2.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import synth
+from oracle import meg
+from oracle.linalg import eigh_desc, jacobi_eigh, logsumexp, project_simplex, project_spectrahedron
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_factored(rng, n, r):
+    V = synth.orthonormal(rng, n, r)
+    lam = rng.dirichlet(np.ones(r))
+    return meg.init_X1(V, lam, meg.eps_schedule(0))
+
+
+# ---------------------------------------------------------------- generators
+def test_bf16_rounding_known_values():
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, -2.5, 1e-3, 0.0])
+    got = synth.bf16_round(x)
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: ties go to the even mantissa (1.0)
+    # 1 + 3*2^-9 = 1.005859375 rounds up to 1 + 2^-7
+    np.testing.assert_array_equal(got[:4], [1.0, 1.0, 1.0 + 2.0 ** -7, -2.5])
+    assert abs(got[4] - 1e-3) <= 2.0 ** -9 * 1e-3
+    assert got[5] == 0.0
+
+
+def test_completion_sample_is_mirrored_and_sorted():
+    c = synth.completion(80, 3, 0.1, seed=5)
+    rows = np.repeat(np.arange(c.n), np.diff(c.rowptr))
+    S = {(int(i), int(j)) for i, j in zip(rows, c.col)}
+    assert all((j, i) in S for (i, j) in S)
+    for i in range(c.n):
+        seg = c.col[c.rowptr[i]:c.rowptr[i + 1]]
+        assert np.all(np.diff(seg) > 0)
+    planted = (c.U * c.w) @ c.U.T
+    np.testing.assert_allclose(c.val, planted[rows, c.col], rtol=1e-6, atol=1e-7)
+
+
+# ---------------------------------------------------------------- SplitMix64
+def test_splitmix64_reference_outputs():
+    # first outputs of SplitMix64 started at seed 0 (Steele, Lea & Flood 2014,
+    # as distributed with the xoshiro/xorshift reference generators)
+    g = meg.SPLITMIX_GAMMA
+    outs = [meg.splitmix64(k * g) for k in (1, 2, 3)]
+    assert outs == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_minibatch_indices_are_uniform():
+    m, L = 10, 256
+    idx = np.concatenate([meg.minibatch_indices(7, t, L, m) for t in range(1, 41)])
+    counts = np.bincount(idx, minlength=m)
+    chi2 = float(np.sum((counts - idx.size / m) ** 2 / (idx.size / m)))
+    assert chi2 < 35.0          # 9 degrees of freedom, p ~ 1e-4
+    assert not np.array_equal(meg.minibatch_indices(7, 1, L, m), meg.minibatch_indices(7, 2, L, m))
+
+
+# ---------------------------------------------------------------- projections
+def test_simplex_projection_kkt():
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        v = rng.standard_normal(rng.integers(1, 12)) * 2
+        w = project_simplex(v)
+        assert abs(w.sum() - 1) < 1e-12 and np.all(w >= 0)
+        # KKT: v - w = theta on the support, v - w <= theta off it
+        theta = float(np.mean((v - w)[w > 0]))
+        np.testing.assert_allclose((v - w)[w > 0], theta, atol=1e-12)
+        assert np.all(v[w == 0] <= theta + 1e-12)
+
+
+def test_spectrahedron_projection_is_optimal():
+    rng = np.random.default_rng(1)
+    n = 8
+    Y = rng.standard_normal((n, n))
+    Y = 0.3 * (Y + Y.T)
+    P = project_spectrahedron(Y)
+    assert abs(np.trace(P) - 1) < 1e-12 and np.linalg.eigvalsh(P)[0] > -1e-12
+    f = lambda X: 0.5 * np.sum((X - Y) ** 2)
+    for _ in range(200):   # any other point of S_n is no closer
+        Z = rng.standard_normal((n, 3))
+        Z = Z @ Z.T
+        Z /= np.trace(Z)
+        assert f(P) <= f(Z) + 1e-12
+    # first-order optimality: <grad f(P), Z - P> >= 0 for the extreme points Z = v v^T
+    G = P - Y
+    assert np.linalg.eigvalsh(G)[0] >= np.sum(G * P) - 1e-10
+
+
+# ---------------------------------------------------------------- eigen-solvers
+def test_jacobi_matches_eigh_bruteforce():
+    rng = np.random.default_rng(2)
+    for n in (1, 2, 3, 7, 16):
+        A = rng.standard_normal((n, n))
+        A = A + A.T
+        w1, _ = eigh_desc(A)
+        w2, V2 = jacobi_eigh(A)
+        np.testing.assert_allclose(w1, w2, atol=1e-12)
+        np.testing.assert_allclose(V2.T @ A @ V2, np.diag(w2), atol=1e-11)
+
+
+def test_orth_iteration_planted_spectrum():
+    rng = np.random.default_rng(3)
+    n, k = 120, 8
+    Q = synth.orthonormal(rng, n, n)
+    d = np.concatenate([[5.0, 4.0, 3.5, 3.0, 2.0], np.linspace(1.0, 0.1, n - 5)])
+    A = (Q * d) @ Q.T
+    th, X, _ = meg.orth_iteration(lambda W: A @ W, rng.standard_normal((n, k)), need=5, shift=0.0)
+    np.testing.assert_allclose(th[:5], d[:5], rtol=1e-12)
+    np.testing.assert_allclose(X.T @ X, np.eye(k), atol=1e-12)
+
+
+# ---------------------------------------------------------------- factored algebra
+def test_factored_frobenius_identity():
+    rng = np.random.default_rng(4)
+    a = _rand_factored(rng, 40, 3)
+    b = _rand_factored(rng, 40, 5)
+    np.testing.assert_allclose(meg.frob_inner(a, b), np.sum(a.dense() * b.dense()), rtol=1e-13)
+    np.testing.assert_allclose(meg.frob_dist(a, b), np.linalg.norm(a.dense() - b.dense()), rtol=1e-10)
+    W = rng.standard_normal((40, 4))
+    np.testing.assert_allclose(a.apply(W), a.dense() @ W, atol=1e-14)
+    np.testing.assert_allclose(a.log_dense(), sla.logm(a.dense()).real, atol=1e-9)
+    np.testing.assert_allclose(a.log_apply(W), a.log_dense() @ W, atol=1e-12)
+
+
+def test_iterates_stay_in_spectrahedron():
+    prob = synth.config(0, scale=60)
+    obj = meg.DenseQuadratic(prob.M)
+    V0, lam0 = meg.warm_start(obj, 5)
+
+    def check(t, X, info):
+        assert abs(X.trace() - 1.0) < 1e-13
+        assert np.all(X.mu > 0) and X.s > 0
+        np.testing.assert_allclose(X.V.T @ X.V, np.eye(X.r), atol=1e-12)
+        w = np.linalg.eigvalsh(X.dense())
+        assert w[0] > 0
+    meg.lowrank_meg(obj, V0, lam0, 15, 1.0, record=check)
+
+
+# ---------------------------------------------------------------- exact MEG closed form
+def test_full_meg_linear_closed_form():
+    """Linear f: log Z_{t+1} = log Z_t - eta C - (log b_t) I, so
+    Z_{T+1} = exp(log Z_1 - eta T C) / Tr(...).  Evaluated with SciPy's
+    Pade/Schur expm and logm (not the eigen-decompositions of the oracle)."""
+    rng = np.random.default_rng(5)
+    n, T, eta = 10, 7, 0.3
+    C = synth.linear(n, seed=9).C
+    B = rng.standard_normal((n, n))
+    Z1 = B @ B.T + 0.5 * np.eye(n)
+    Z1 /= np.trace(Z1)
+    Z = meg.full_meg(meg.Linear(C), Z1, T, eta)
+    E = sla.expm(sla.logm(Z1).real - eta * T * C)
+    np.testing.assert_allclose(Z, E / np.trace(E), atol=1e-12)
+
+
+# ---------------------------------------------------------------- diagonal special case
+def _load_golden():
+    with open(os.path.join(GOLDEN, "diag_recursion.json")) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _load_golden(), ids=lambda c: c["name"])
+def test_diagonal_recursion_golden(case):
+    n, r, T, eta = case["n"], case["r"], case["T"], case["eta"]
+    data = np.array(case["data"])
+    obj = meg.Linear(np.diag(data)) if case["kind"] == "linear" else meg.DenseQuadratic(np.diag(data))
+    V0 = np.eye(n)[:, :r]
+    seen = {}
+    meg.lowrank_meg(obj, V0, np.array(case["lam0"]), T, eta,
+                    record=lambda t, X, info: seen.setdefault(t, (X, info)))
+    for t in range(1, T + 1):
+        X, info = seen[t]
+        x_ref = np.array([float(v) for v in case["x"][t - 1]])
+        np.testing.assert_allclose(np.diag(X.dense()), x_ref, rtol=1e-11, atol=1e-300)
+        np.testing.assert_allclose(info.sig[: r + 1], [float(v) for v in case["sig_top"][t - 1]], rtol=1e-12)
+        assert abs(info.cert - float(case["cert"][t - 1])) < 1e-10
+
+
+def test_rotation_equivariance():
+    """X(Q C Q^T, Q X0 Q^T) = Q X(C, X0) Q^T for orthogonal Q."""
+    rng = np.random.default_rng(6)
+    n, r = 30, 3
+    M = synth.dense_quadratic(n, r, seed=11, sigma=1e-3).M
+    Q = synth.orthonormal(rng, n, n)
+    obj1, obj2 = meg.DenseQuadratic(M), meg.DenseQuadratic(Q @ M @ Q.T)
+    V0, lam0 = meg.warm_start(obj1, r)
+    X1, _ = meg.lowrank_meg(obj1, V0, lam0, 8, 1.0)
+    X2, _ = meg.lowrank_meg(obj2, Q @ V0, lam0, 8, 1.0)
+    np.testing.assert_allclose(Q @ X1.dense() @ Q.T, X2.dense(), atol=1e-12)
+
+
+# ---------------------------------------------------------------- Lemma 2
+def _state_after(obj, r, t_steps):
+    V0, lam0 = meg.warm_start(obj, r)
+    X, _ = meg.lowrank_meg(obj, V0, lam0, t_steps, 1.0)
+    return X
+
+
+def test_lemma2_exact_spectrum_and_bound():
+    rng = np.random.default_rng(7)
+    n, r = 40, 3
+    obj = meg.DenseQuadratic(synth.dense_quadratic(n, r, seed=12, sigma=2e-3).M)
+    X = _state_after(obj, r, 3)
+    t, eta = 4, 1.0
+    eps = meg.eps_schedule(t)
+    Xd = X.dense()
+    G = obj.grad_dense(X, t)
+    Zp, sig_all = meg.full_meg_step(Xd, G, eta)
+    Xp, info, _ = meg.lowrank_step(X, obj, t, eta, eps)
+    np.testing.assert_allclose(info.sig, sig_all, atol=1e-12)
+    # spectrum of D = log Z+ - log X+ (proof of Lemma 2)
+    D = sla.logm(Zp).real - sla.logm(Xp.dense()).real
+    got = np.sort(np.linalg.eigvalsh(0.5 * (D + D.T)))
+    want = np.sort(meg.lemma2_D_spectrum(sig_all, r, eps))
+    np.testing.assert_allclose(got, want, atol=1e-8)
+    # the bound of Lemma 2, for B(Z+, X+) and for B(X*, X+) - B(X*, Z+) with X* in S_n
+    bound = max(2 * eps, info.cert_exact)
+    assert meg.bregman(Zp, Xp.dense()) <= bound + 1e-12
+    for _ in range(5):
+        P = rng.standard_normal((n, 2))
+        Xs = P @ P.T
+        Xs /= np.trace(Xs)
+        assert meg.bregman(Xs, Xp.dense()) - meg.bregman(Xs, Zp) <= bound + 1e-9
+
+
+def test_certificate_b_r1_is_conservative():
+    """b_{r+1} <= b_n, so the b_{r+1} certificate is never below the exact one."""
+    n, r = 50, 4
+    obj = meg.DenseQuadratic(synth.dense_quadratic(n, r, seed=13, sigma=1e-3).M)
+    V0, lam0 = meg.warm_start(obj, r)
+    _, infos = meg.lowrank_meg(obj, V0, lam0, 10, 1.0)
+    for info in infos:
+        assert info.cert >= info.cert_exact - 1e-14
+        assert info.cert_exact == pytest.approx(
+            math.log(n - r) + info.sig[r] - math.log(info.eps) - logsumexp(info.sig), abs=1e-12)
+
+
+def test_lowrank_equals_full_meg_when_rank_suffices():
+    """When the certificate holds, B(Z+, X+) <= 2 eps_t (Lemma 2): the
+    low-rank step is within the stated Bregman distance of exact MEG.
+    The target has trace 1.3 so that strict complementarity holds
+    (Assumption 1; Section 7 takes tau < Tr M for the same reason)."""
+    n, r = 60, 2
+    obj = meg.DenseQuadratic(synth.dense_quadratic(n, r, seed=14, sigma=1e-5, weights=(0.9, 0.4)).M)
+    X = _state_after(obj, r, 2)
+    held = 0
+    for t in range(3, 12):
+        eps = meg.eps_schedule(t)
+        Zp, _ = meg.full_meg_step(X.dense(), obj.grad_dense(X, t), 1.0)
+        Xp, info, _ = meg.lowrank_step(X, obj, t, 1.0, eps)
+        if info.cert_exact <= 2 * eps:
+            held += 1
+            assert meg.bregman(Zp, Xp.dense()) <= 2 * eps + 1e-12
+        X = Xp
+    assert held >= 8
+
+
+# ---------------------------------------------------------------- optima
+def test_quadratic_planted_optimum_reached():
+    """M in S_n: X* = M and f* = 0; the iterates approach M."""
+    n, r = 50, 3
+    prob = synth.dense_quadratic(n, r, seed=15, sigma=0.0, weights=(0.5, 0.3, 0.2))
+    obj = meg.DenseQuadratic(prob.M)
+    V0, lam0 = meg.warm_start(obj, r)
+    # the warm start of eq. (exp:init) recovers M exactly here
+    np.testing.assert_allclose((V0 * lam0) @ V0.T, prob.M, atol=1e-12)
+    T = 60
+    X, infos = meg.lowrank_meg(obj, V0, lam0, T, 1.0)
+    # the iterate keeps eps_T of its trace off the range of M (Definition 2),
+    # so the distance to M is of the order of eps_T
+    assert np.linalg.norm(X.dense() - prob.M) <= 2 * meg.eps_schedule(T)
+    assert obj.value(X) <= 2 * meg.eps_schedule(T) ** 2
+
+
+def test_quadratic_noisy_matches_projection():
+    """M not in S_n: the limit is Pi_{S_n}(M) of eq. (euclidProj); Lemma 1:
+    its range is spanned by bottom eigenvectors of grad f(X*)."""
+    n, r = 40, 3
+    M = synth.dense_quadratic(n, r, seed=16, sigma=0.0, weights=(0.5, 0.3, 0.2)).M * 1.2
+    Xstar = project_spectrahedron(M)
+    G = Xstar - M
+    w, U = np.linalg.eigh(G)
+    rk = int(np.sum(np.linalg.eigvalsh(Xstar) > 1e-10))
+    assert rk == r
+    P = U[:, :rk] @ U[:, :rk].T
+    np.testing.assert_allclose(P @ Xstar @ P, Xstar, atol=1e-10)
+    obj = meg.DenseQuadratic(M)
+    V0, lam0 = meg.warm_start(obj, r)
+    T = 200
+    X, _ = meg.lowrank_meg(obj, V0, lam0, T, 1.0)
+    # X_T keeps eps_T of its trace on the complement of range(X*), which costs
+    # at most eps_T (lambda_max - lambda_min)(grad f(X*)) in objective value
+    gap = obj.value(X) - obj.value_dense(Xstar)
+    assert -1e-14 <= gap <= 1.5 * meg.eps_schedule(T) * (w[-1] - w[0])
+    assert np.linalg.norm(X.dense() - Xstar) <= 2 * meg.eps_schedule(T)
+
+
+def test_linear_optimum_bruteforce():
+    """min_{S_n} <C, X> = lambda_min(C) at v v^T (Lemma 1); brute force
+    by sphere sampling at n = 3 and Jacobi at n <= 16; low-rank MEG with
+    r = 1 approaches it."""
+    rng = np.random.default_rng(17)
+    C3 = synth.linear(3, seed=18).C
+    u = rng.standard_normal((200000, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    brute = float(np.min(np.einsum("ij,jk,ik->i", u, C3, u)))
+    assert abs(brute - jacobi_eigh(C3)[0][-1]) < 1e-3
+    n = 16
+    C = synth.linear(n, seed=19).C
+    w, V = jacobi_eigh(C)
+    obj = meg.Linear(C)
+    V0, lam0 = meg.warm_start(obj, 1)
+    X, _ = meg.lowrank_meg(obj, V0, lam0, 300, 0.5)
+    assert obj.value(X) - w[-1] < 2e-3
+    assert abs(abs(float(X.V[:, 0] @ V[:, -1])) - 1) < 1e-8
+
+
+# ---------------------------------------------------------------- eigensolver variants
+@pytest.mark.parametrize("kind", ["dense_quadratic", "completion", "measurements", "linear"])
+def test_exact_and_subspace_variants_agree(kind):
+    n, r, T = 70, 3, 6
+    if kind == "dense_quadratic":
+        obj = meg.DenseQuadratic(synth.dense_quadratic(n, r, seed=20, sigma=1e-4).M)
+        eta = 1.0
+    elif kind == "completion":
+        c = synth.completion(n, r, 0.5, seed=21)
+        obj = meg.Completion(n, c.rowptr, c.col, c.val)
+        eta = 1.0
+    elif kind == "measurements":
+        p = synth.measurements(n, r, 20 * n, 32, seed=22)
+        obj = meg.Measurements(p.A, p.y, p.L, seed=5)
+        eta = 1.0 / (4 * (1 + n / p.L))
+    else:
+        obj = meg.Linear(synth.linear(n, seed=23).C)
+        eta = 0.3
+    if kind == "linear":
+        r = 1        # the optimum of a linear objective has rank one (Lemma 1)
+    V0, lam0 = meg.warm_start(obj, r)
+    Xa, ia = meg.lowrank_meg(obj, V0, lam0, T, eta, method="exact")
+    Xb, ib = meg.lowrank_meg(obj, V0, lam0, T, eta, method="subspace", k=r + 4)
+    assert meg.frob_dist(Xa, Xb) <= 1e-9 * np.linalg.norm(Xa.dense())
+    for a, b in zip(ia, ib):
+        np.testing.assert_allclose(a.sig[:r], b.sig[:r], rtol=1e-10)
+
+
+def test_stochastic_gradient_is_unbiased():
+    n, r = 12, 2
+    p = synth.measurements(n, r, 60, 16, seed=24)
+    obj = meg.Measurements(p.A, p.y, p.L, seed=3)
+    rng = np.random.default_rng(25)
+    X = _rand_factored(rng, n, r)
+    full = (2.0 / obj.m) * (p.A.T * (obj.quad(X, np.arange(obj.m)) - p.y)) @ p.A
+    avg = np.mean([obj.grad_dense(X, t) for t in range(1, 3001)], axis=0)
+    assert np.linalg.norm(avg - full) < 0.08 * np.linalg.norm(full)
+    # the implicit product equals the dense stochastic gradient times W
+    W = rng.standard_normal((n, 3))
+    np.testing.assert_allclose(obj.grad_apply(X, W, 4), obj.grad_dense(X, 4) @ W, atol=1e-10)
