@@ -1,0 +1,219 @@
+/*
+ * meg.h -- C ABI of the GB300 low-rank Matrix Exponentiated Gradient library.
+ *
+ * The library minimises a convex f over the spectrahedron
+ *     S_n = { X symmetric, X >= 0, Tr X = 1 }                (eq. Model)
+ * with the low-rank MEG method of Garber & Kaplan (Algorithm 2): each
+ * iteration takes the top-r eigen-decomposition of the mirror matrix
+ *     M_t = log X_t - eta_t grad f(X_t)
+ * and sets
+ *     X_{t+1} = (1 - eps_t) Y^r / a_t + eps_t/(n - r) (I - V V^T),
+ *     Y^r = V diag(exp sigma_1..r) V^T,  a_t = sum_{i<=r} exp sigma_i
+ * (Definition 2, eq. LowRankMDvonNeumannUpdate).  X_t is held in the
+ * factored form of eq. (eigenFastUpdate): V (n x r, orthonormal), mu (r)
+ * and s, X = V diag(mu) V^T + s (I - V V^T).  The eigenpairs come from a
+ * warm-started block subspace iteration with CholeskyQR2 and a
+ * Rayleigh-Ritz step (Section 3).
+ *
+ * Conventions for every call:
+ *   - Matrices are row-major.  "host" pointers are ordinary CPU memory,
+ *     "device" pointers are CUDA global memory of the current device.
+ *   - All calls are ordered on the solve's CUDA stream (meg_options.stream,
+ *     NULL = the legacy default stream).  meg_create, meg_set_objective
+ *     and meg_step only enqueue work; meg_certificate, meg_get_iterate,
+ *     meg_get_ritz, meg_objective and meg_solve synchronise that stream.
+ *   - Errors are returned as meg_status; nothing throws across the ABI.
+ *     meg_last_error() gives a thread-local message for the last failure.
+ *   - A solve that hit MEG_ERR_NUMERIC or MEG_ERR_TIMEOUT on the device
+ *     answers MEG_ERR_STATE to every later call except meg_destroy.
+ */
+#ifndef MEG_H
+#define MEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct meg_solve_s* meg_handle;   /* one solve; owned by the library */
+typedef struct meg_group_s* meg_group;    /* several solves stepped together */
+
+typedef enum {
+    MEG_OK = 0,
+    MEG_ERR_INVALID_ARG = 1,
+    MEG_ERR_OOM = 2,
+    MEG_ERR_CUDA = 3,
+    MEG_ERR_NUMERIC = 4,       /* Cholesky breakdown, non-finite Ritz value */
+    MEG_ERR_NOT_CONVERGED = 5, /* meg_solve reached max_iters */
+    MEG_ERR_TIMEOUT = 6,       /* a bounded device wait gave up */
+    MEG_ERR_STATE = 7          /* handle unusable (earlier error, wrong order) */
+} meg_status;
+
+/* Arithmetic of the path (precision modes). */
+enum {
+    MEG_FP64 = 0,        /* every array and operation in float64 */
+    MEG_FP32 = 1,        /* float32 arrays and products; compensated
+                            (double-word) reductions; float64 k x k island */
+    MEG_MIXED_BF16 = 2   /* as MEG_FP32, dense data in bfloat16 and the dense
+                            product on tcgen05 tensor cores (fp32 accumulate) */
+};
+
+/* Objective kinds (meg_objective_desc.kind). */
+enum {
+    MEG_DENSE_QUAD = 0,  /* f = 1/2 ||X - M||_F^2,  grad f = X - M            */
+    MEG_CSR_QUAD = 1,    /* f = 1/2 sum_{(i,j) in Omega} (X_ij - M_ij)^2,
+                            Omega mirrored, grad f = P_Omega(X - M)           */
+    MEG_MEAS_STOCH = 2,  /* f = (1/m) sum_i (a_i^T X a_i - y_i)^2; step t uses
+                            the minibatch gradient (2/L) sum_b r_b a_b a_b^T   */
+    MEG_LINEAR = 3       /* f = <C, X>,  grad f = C                          */
+};
+
+/*
+ * Options of one solve (Algorithm 2 inputs).
+ *   n, r       : dimension and SVD rank, 1 <= r <= n - 1, r <= 30.
+ *   p          : extra subspace vectors, k = r + p, 1 <= p, k <= min(n, 32).
+ *                (p >= 1 because the certificate needs sigma_{r+1}.)
+ *   q          : subspace-iteration products per MEG iteration, 1..8.
+ *   precision  : MEG_FP64 | MEG_FP32 | MEG_MIXED_BF16.
+ *   eta        : constant step size eta_t = eta > 0.
+ *   eps_a, eps_c, eps_pow : eps_t = eps_a / (t + eps_c + 1)^eps_pow
+ *                (Section 7: 0.8, 10, 2); every eps_t must lie in (0, 3/4]
+ *                (Lemma 2).
+ *   max_iters, tol : defaults for meg_solve.
+ *   seed       : seeds the extra subspace vectors and the minibatch stream.
+ *   stream     : cudaStream_t (NULL = default stream).
+ */
+typedef struct {
+    int n, r, p, q;
+    int precision;
+    double eta;
+    double eps_a, eps_c, eps_pow;
+    int max_iters;
+    double tol;
+    uint64_t seed;
+    void* stream;
+} meg_options;
+
+/*
+ * Objective data.  Every array is a caller-owned DEVICE pointer, borrowed
+ * for the lifetime of the handle (the library never frees or writes it).
+ *   dense  (DENSE_QUAD: M; LINEAR: C): n x n row-major symmetric;
+ *          element type double (MEG_FP64), float (MEG_FP32) or bfloat16
+ *          bit patterns, uint16 (MEG_MIXED_BF16).
+ *   rowptr, col, val, nnz (CSR_QUAD): CSR of the mirrored sample Omega,
+ *          int32 rowptr[n+1], int32 col[nnz] (sorted within a row),
+ *          val[nnz] = M_ij as double (MEG_FP64) or float (otherwise).
+ *   A, y, m, L (MEAS_STOCH): A m x n row-major, double (MEG_FP64) or
+ *          bfloat16 bits (otherwise); y[m] double; minibatch size L.
+ */
+typedef struct {
+    int kind;
+    const void* dense;
+    const int* rowptr;
+    const int* col;
+    const void* val;
+    int64_t nnz;
+    const void* A;
+    const double* y;
+    int64_t m;
+    int L;
+} meg_objective_desc;
+
+/*
+ * meg_create -- allocate a solve and set X_1 (Algorithm 2, Initialization):
+ *   X_1 = (1 - eps_0) X_0 + (eps_0/n) I,  X_0 = V0 diag(lam0) V0^T.
+ * V0: host, n x r row-major, orthonormal columns; lam0: host, r values on
+ * the unit simplex.  V0 == NULL leaves X_1 unset until meg_warm_start.
+ * The library copies V0/lam0; the caller keeps ownership.
+ * Errors: MEG_ERR_INVALID_ARG (sizes, schedule), MEG_ERR_OOM, MEG_ERR_CUDA.
+ */
+meg_status meg_create(const meg_options* opt, const double* V0, const double* lam0,
+                      meg_handle* out);
+
+/* meg_set_objective -- attach f (problem statement, eq. Model).  The
+ * descriptor is copied, the arrays are borrowed.  CSR row pointers are
+ * validated on the host copy the call makes (monotone, in range).
+ * Errors: MEG_ERR_INVALID_ARG, MEG_ERR_CUDA. */
+meg_status meg_set_objective(meg_handle h, const meg_objective_desc* d);
+
+/* meg_warm_start -- X_0 of eq. (exp:init) with U = 0: the top-r
+ * eigenpairs of -grad f(0) by `products` subspace-iteration products on
+ * the device, eigenvalues projected onto the unit simplex, then X_1 as in
+ * meg_create.  Needs the objective.  Synchronises the stream. */
+meg_status meg_warm_start(meg_handle h, int products);
+
+/* meg_step -- run `nsteps` iterations of Algorithm 2 (t -> t + nsteps),
+ * enqueued on the stream without a host synchronisation. */
+meg_status meg_step(meg_handle h, int nsteps);
+
+/* meg_solve -- iterate until the relative objective gap
+ * (f(X_t) - fstar)/(f(X_1) - fstar) <= tol or max_iters iterations;
+ * fstar = 0 unless meg_set_fstar gave one.  f is evaluated every 10
+ * iterations with meg_objective's accurate pass.  *iters_out (may be
+ * NULL) receives the iterations run.  Returns MEG_ERR_NOT_CONVERGED when
+ * max_iters is reached first. */
+meg_status meg_solve(meg_handle h, double tol, int max_iters, int* iters_out);
+
+/* meg_set_fstar -- known optimal value for meg_solve's relative gap. */
+meg_status meg_set_fstar(meg_handle h, double fstar);
+
+/* meg_certificate -- certificate of the last iteration t (Lemma 2 with
+ * b = b_{r+1}, eq. convergenceGuaranteeExperiment2):
+ *   C_t = log((n - r) lambda_{r+1}(Y_t) / (eps_t b_{r+1})),
+ * *holds = (C_t <= 2 eps_t); *first_hold_iter = first t at which it held
+ * (0 if never).  Any output pointer may be NULL. */
+meg_status meg_certificate(meg_handle h, double* C_t, int* holds, int* first_hold_iter);
+
+/* meg_get_iterate -- copy X_t's factors to host memory: V n x r row-major
+ * (float64), mu[r], s.  Any output pointer may be NULL. */
+meg_status meg_get_iterate(meg_handle h, double* V, double* mu, double* s);
+
+/* meg_get_ritz -- the k leading Ritz values sigma_1 >= ... >= sigma_k of
+ * M_t from the last iteration (host, float64) and that iteration's t. */
+meg_status meg_get_ritz(meg_handle h, double* sigma, int* t);
+
+/* meg_objective -- f(X_t) for the current iterate, by a dense pass over
+ * the objective data (DENSE_QUAD, LINEAR), over Omega (CSR_QUAD) or over
+ * all m measurements (MEAS_STOCH), accumulated with compensation. */
+meg_status meg_objective(meg_handle h, double* f);
+
+/* Checkpoint / resume.  The state of a solve is everything the next
+ * iteration reads: the float64 small state (t, mu, s, shift bounds,
+ * certificate history, V^T W, W^T W), V (n x r) and the subspace block W.
+ * meg_state_size gives the byte count; meg_get_state copies it to host
+ * memory `buf`, meg_set_state restores it into a solve created with the
+ * same n, r, p and precision (objective data are not part of the state).
+ * Iterating T steps, saving, restoring and iterating T more gives the
+ * same bits as 2T steps.  Both calls synchronise the stream. */
+int64_t meg_state_size(meg_handle h);
+meg_status meg_get_state(meg_handle h, void* buf, int64_t bytes);
+meg_status meg_set_state(meg_handle h, const void* buf, int64_t bytes);
+
+/* meg_destroy -- free the solve (waits for its stream). NULL is a no-op. */
+meg_status meg_destroy(meg_handle h);
+
+/* meg_last_error -- message of the calling thread's last failure. */
+const char* meg_last_error(void);
+
+/*
+ * Groups: step several solves (any n, r, kind; one precision and one q)
+ * with grouped kernels, one launch per kernel for the whole group, the
+ * step captured once as a CUDA graph.  The solves keep their own state;
+ * results equal those of stepping each alone.  A solve belongs to at
+ * most one group at a time; the group borrows the handles.
+ */
+meg_status meg_group_create(const meg_handle* solves, int count, void* stream, meg_group* out);
+meg_status meg_group_step(meg_group g, int nsteps);
+meg_status meg_group_destroy(meg_group g);
+
+/* Device-memory footprint in bytes of one solve (library-owned buffers,
+ * not the caller's objective data), for admission control. */
+int64_t meg_footprint(int n, int r, int p, int precision, int kind);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MEG_H */

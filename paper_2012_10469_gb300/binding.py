@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libmeg.so (include/meg.h), same names as the C ABI.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Objective data and streams come from PyTorch (device tensors,
+``torch.cuda.current_stream().cuda_stream``).  Loading fails loudly when
+the library has not been built or cannot be opened.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libmeg.so")
+
+MEG_OK, MEG_ERR_INVALID_ARG, MEG_ERR_OOM, MEG_ERR_CUDA, MEG_ERR_NUMERIC, MEG_ERR_NOT_CONVERGED, \
+    MEG_ERR_TIMEOUT, MEG_ERR_STATE = range(8)
+MEG_FP64, MEG_FP32, MEG_MIXED_BF16 = 0, 1, 2
+MEG_DENSE_QUAD, MEG_CSR_QUAD, MEG_MEAS_STOCH, MEG_LINEAR = 0, 1, 2, 3
+PRECISION = {"fp64": MEG_FP64, "fp32": MEG_FP32, "bf16": MEG_MIXED_BF16}
+# slots of the small state (csrc/meg_dev.cuh, SmallSlot)
+SM_T, SM_EPS, SM_S, SM_LOGS, SM_SHIFT, SM_C0, SM_ALPHA, SM_GNORM, SM_FEST, SM_CERT, SM_HOLDS, \
+    SM_FIRST_HOLD, SM_STATUS, SM_TRD, SM_FROD2, SM_LAST_T, SM_LSE, SM_RSS, SM_RESID_BOUND, SM_ETA = range(20)
+SM_MU, SM_DCOEF, SM_SIGMA = 32, 64, 96
+SM_TOTAL = 128 + 7 * 1024
+
+
+class meg_options(C.Structure):
+    _fields_ = [("n", C.c_int), ("r", C.c_int), ("p", C.c_int), ("q", C.c_int),
+                ("precision", C.c_int), ("eta", C.c_double), ("eps_a", C.c_double),
+                ("eps_c", C.c_double), ("eps_pow", C.c_double), ("max_iters", C.c_int),
+                ("tol", C.c_double), ("seed", C.c_uint64), ("stream", C.c_void_p)]
+
+
+class meg_objective_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("dense", C.c_void_p), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p), ("nnz", C.c_int64),
+                ("A", C.c_void_p), ("y", C.c_void_p), ("m", C.c_int64), ("L", C.c_int)]
+
+
+class MegError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+_lib: Optional[C.CDLL] = None
+_P = C.POINTER
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Open libmeg.so and declare its entry points (raises if missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmeg.so not built ({path}); run paper_2012_10469_gb300.build.build()")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    sig = {
+        "meg_create": (C.c_int, [_P(meg_options), _P(C.c_double), _P(C.c_double), _P(H)]),
+        "meg_set_objective": (C.c_int, [H, _P(meg_objective_desc)]),
+        "meg_warm_start": (C.c_int, [H, C.c_int]),
+        "meg_step": (C.c_int, [H, C.c_int]),
+        "meg_solve": (C.c_int, [H, C.c_double, C.c_int, _P(C.c_int)]),
+        "meg_set_fstar": (C.c_int, [H, C.c_double]),
+        "meg_certificate": (C.c_int, [H, _P(C.c_double), _P(C.c_int), _P(C.c_int)]),
+        "meg_get_iterate": (C.c_int, [H, _P(C.c_double), _P(C.c_double), _P(C.c_double)]),
+        "meg_get_ritz": (C.c_int, [H, _P(C.c_double), _P(C.c_int)]),
+        "meg_objective": (C.c_int, [H, _P(C.c_double)]),
+        "meg_destroy": (C.c_int, [H]),
+        "meg_last_error": (C.c_char_p, []),
+        "meg_group_create": (C.c_int, [_P(H), C.c_int, C.c_void_p, _P(H)]),
+        "meg_group_step": (C.c_int, [H, C.c_int]),
+        "meg_group_destroy": (C.c_int, [H]),
+        "meg_footprint": (C.c_int64, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "meg_state_size": (C.c_int64, [H]),
+        "meg_get_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
+        "meg_set_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names declared by include/meg.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(HERE), "include", "meg.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"^\s*(?:meg_status|const char\*|int64_t)\s+(meg_\w+)\s*\(", text, re.M)))
+
+
+def _check(status: int, what: str):
+    if status != MEG_OK:
+        msg = _lib.meg_last_error().decode() if _lib is not None else ""
+        raise MegError(status, f"{what}: {msg}")
+
+
+def _dptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    return int(x.data_ptr())
+
+
+def _f64p(a: np.ndarray):
+    return a.ctypes.data_as(_P(C.c_double))
+
+
+def meg_last_error() -> str:
+    return load().meg_last_error().decode()
+
+
+def meg_footprint(n, r, p, precision, kind) -> int:
+    return int(load().meg_footprint(n, r, p, precision, kind))
+
+
+class Solve:
+    """One solve (meg_handle) with the C ABI's calls as methods."""
+
+    def __init__(self, n: int, r: int, p: int = 4, q: int = 2, precision: int = MEG_FP64,
+                 eta: float = 1.0, eps=(0.8, 10.0, 2.0), seed: int = 1, V0=None, lam0=None,
+                 stream=None, max_iters: int = 1000, tol: float = 1e-6):
+        lib = load()
+        self.n, self.r, self.k = n, r, r + p
+        self.precision = precision
+        self._keep = []
+        opt = meg_options(n=n, r=r, p=p, q=q, precision=precision, eta=eta, eps_a=eps[0], eps_c=eps[1],
+                          eps_pow=eps[2], max_iters=max_iters, tol=tol, seed=seed,
+                          stream=None if stream is None else int(stream))
+        h = C.c_void_p()
+        if V0 is not None:
+            V0 = np.ascontiguousarray(V0, dtype=np.float64)
+            lam0 = np.ascontiguousarray(lam0, dtype=np.float64)
+            st = lib.meg_create(C.byref(opt), _f64p(V0), _f64p(lam0), C.byref(h))
+        else:
+            st = lib.meg_create(C.byref(opt), None, None, C.byref(h))
+        _check(st, "meg_create")
+        self.h = h
+
+    # -- objective
+    def meg_set_objective(self, kind, dense=None, rowptr=None, col=None, val=None, A=None, y=None, L=0):
+        """Tensors are borrowed (kept alive by this object)."""
+        self._keep = [t for t in (dense, rowptr, col, val, A, y) if t is not None]
+        d = meg_objective_desc(kind=kind, dense=_dptr(dense), rowptr=_dptr(rowptr), col=_dptr(col),
+                               val=_dptr(val), nnz=0 if col is None else int(col.numel()),
+                               A=_dptr(A), y=_dptr(y), m=0 if A is None else int(A.shape[0]), L=L)
+        _check(load().meg_set_objective(self.h, C.byref(d)), "meg_set_objective")
+
+    def meg_warm_start(self, products: int = 40):
+        _check(load().meg_warm_start(self.h, products), "meg_warm_start")
+
+    def meg_step(self, nsteps: int = 1):
+        _check(load().meg_step(self.h, nsteps), "meg_step")
+
+    def meg_solve(self, tol: float, max_iters: int):
+        it = C.c_int(0)
+        st = load().meg_solve(self.h, tol, max_iters, C.byref(it))
+        if st not in (MEG_OK, MEG_ERR_NOT_CONVERGED):
+            _check(st, "meg_solve")
+        return it.value, st == MEG_OK
+
+    def meg_set_fstar(self, fstar: float):
+        _check(load().meg_set_fstar(self.h, fstar), "meg_set_fstar")
+
+    def meg_certificate(self):
+        c, holds, first = C.c_double(), C.c_int(), C.c_int()
+        _check(load().meg_certificate(self.h, C.byref(c), C.byref(holds), C.byref(first)), "meg_certificate")
+        return c.value, bool(holds.value), first.value
+
+    def meg_get_iterate(self):
+        V = np.empty((self.n, self.r), dtype=np.float64)
+        mu = np.empty(self.r, dtype=np.float64)
+        s = C.c_double()
+        _check(load().meg_get_iterate(self.h, _f64p(V), _f64p(mu), C.byref(s)), "meg_get_iterate")
+        return V, mu, s.value
+
+    def meg_get_ritz(self):
+        sig = np.empty(self.k, dtype=np.float64)
+        t = C.c_int()
+        _check(load().meg_get_ritz(self.h, _f64p(sig), C.byref(t)), "meg_get_ritz")
+        return sig, t.value
+
+    def meg_objective(self) -> float:
+        f = C.c_double()
+        _check(load().meg_objective(self.h, C.byref(f)), "meg_objective")
+        return f.value
+
+    def meg_get_state(self) -> bytes:
+        lib = load()
+        nb = int(lib.meg_state_size(self.h))
+        buf = C.create_string_buffer(nb)
+        _check(lib.meg_get_state(self.h, buf, nb), "meg_get_state")
+        return buf.raw
+
+    def meg_set_state(self, state: bytes):
+        buf = C.create_string_buffer(state, len(state))
+        _check(load().meg_set_state(self.h, buf, len(state)), "meg_set_state")
+
+    def small_state(self) -> np.ndarray:
+        """The float64 small state (scalars, mu, Ritz values, k x k blocks)."""
+        st = self.meg_get_state()
+        return np.frombuffer(st, dtype=np.float64, count=SM_TOTAL, offset=64).copy()
+
+    def meg_destroy(self):
+        if getattr(self, "h", None):
+            load().meg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.meg_destroy()
+        except Exception:
+            pass
+
+
+class Group:
+    """Several solves stepped with grouped kernels (meg_group)."""
+
+    def __init__(self, solves, stream=None):
+        lib = load()
+        self.solves = list(solves)
+        arr = (C.c_void_p * len(self.solves))(*[s.h for s in self.solves])
+        g = C.c_void_p()
+        _check(lib.meg_group_create(arr, len(self.solves), None if stream is None else int(stream),
+                                    C.byref(g)), "meg_group_create")
+        self.g = g
+
+    def meg_group_step(self, nsteps: int = 1):
+        _check(load().meg_group_step(self.g, nsteps), "meg_group_step")
+
+    def meg_group_destroy(self):
+        if getattr(self, "g", None):
+            load().meg_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.meg_group_destroy()
+        except Exception:
+            pass

@@ -1,0 +1,1035 @@
+// Row kernels of one low-rank MEG iteration (Algorithm 2, Garber & Kaplan),
+// grouped over solves, and the float64 k x k island run by the last block of
+// each reduction.
+//
+// Per iteration t, for each solve (X_t = V diag(mu) V^T + s (I - V V^T)):
+//   begin    : eps_t, the operator M_t - c I = V diag(d) V^T + (c0 - c) I + alpha * G_f
+//              with G_f the gradient part (Section 3, closed-form log X), and
+//              the shift c (see k_begin)
+//   product  : Y = G_f W (dense, CSR or measurement kernel)
+//   combine  : Z = alpha Y + V (d o U) + (c0 - c) W,  U = V^T W;  Z^T Z, W^T Y
+//              last block: Rayleigh-Ritz on span W (final product), exp-map
+//              (Definition 2), certificate (Lemma 2), CholeskyQR factor
+//   orth1/2  : W <- CholeskyQR2(Z) (two passes), V_{t+1} = W Q_r; V^T W, W^T W
+#include <math.h>
+
+#include "kxk.cuh"
+#include "meg_dev.cuh"
+
+namespace {
+
+constexpr int NT = 256;              // threads of every row kernel
+
+// --------------------------------------------------------------------------
+// Two-level deterministic last-block reduction of per-block double-word
+// partials.  Every block of a solve passes its E entries in `mine`; the last
+// block of each group of RED_GROUP blocks sums the group in block order, the
+// last group-finisher sums the groups in order and gets the totals in `out`.
+// Returns true in exactly one block per solve.  No block waits on another.
+__device__ bool red_two_level(const SolveDev& s, int lb, const dw* mine, dw* out, int E) {
+    const int tid = threadIdx.x;
+    const int stride = 2 * RED_MAX_ENTRIES;
+    float* part = s.part;
+    const int ngroups = (s.nb_red + RED_GROUP - 1) / RED_GROUP;
+    __shared__ int am_last;
+    for (int e = tid; e < E; e += blockDim.x) {
+        part[(size_t)lb * stride + 2 * e] = mine[e].hi;
+        part[(size_t)lb * stride + 2 * e + 1] = mine[e].lo;
+    }
+    __threadfence();
+    __syncthreads();
+    const int g = lb / RED_GROUP;
+    const int g0 = g * RED_GROUP, gsz = min(RED_GROUP, s.nb_red - g0);
+    if (tid == 0) am_last = (atomicAdd(&s.ctr[g], 1u) == (unsigned)(gsz - 1));
+    __syncthreads();
+    if (!am_last) return false;
+    if (tid == 0) s.ctr[g] = 0u;
+    for (int e = tid; e < E; e += blockDim.x) {
+        dw acc = {0.f, 0.f};
+        for (int b = g0; b < g0 + gsz; ++b) {
+            dw v = {__ldcg(part + (size_t)b * stride + 2 * e), __ldcg(part + (size_t)b * stride + 2 * e + 1)};
+            dw_add(acc, v);
+        }
+        part[(size_t)(s.nb_red + g) * stride + 2 * e] = acc.hi;
+        part[(size_t)(s.nb_red + g) * stride + 2 * e + 1] = acc.lo;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) am_last = (atomicAdd(&s.ctr[ngroups], 1u) == (unsigned)(ngroups - 1));
+    __syncthreads();
+    if (!am_last) return false;
+    if (tid == 0) s.ctr[ngroups] = 0u;
+    for (int e = tid; e < E; e += blockDim.x) {
+        dw acc = {0.f, 0.f};
+        for (int gg = 0; gg < ngroups; ++gg) {
+            size_t o = (size_t)(s.nb_red + gg) * stride + 2 * e;
+            dw v = {__ldcg(part + o), __ldcg(part + o + 1)};
+            dw_add(acc, v);
+        }
+        out[e] = acc;
+    }
+    __syncthreads();
+    return true;
+}
+
+// index e of the packed upper triangle (column by column) -> (i, j), i <= j
+__device__ __forceinline__ void tri_decode(int e, int& i, int& j) {
+    int jj = (int)((sqrtf(8.f * e + 1.f) - 1.f) * 0.5f);
+    while ((jj + 1) * (jj + 2) / 2 <= e) ++jj;
+    while (jj * (jj + 1) / 2 > e) --jj;
+    j = jj;
+    i = e - jj * (jj + 1) / 2;
+}
+
+__device__ __forceinline__ void unpack_sym(const dw* src, double* dst, int k) {
+    const int nsym = k * (k + 1) / 2;
+    for (int e = threadIdx.x; e < nsym; e += blockDim.x) {
+        int i, j;
+        tri_decode(e, i, j);
+        double v = dw_value(src[e]);
+        dst[i * MEG_LDK + j] = v;
+        dst[j * MEG_LDK + i] = v;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void store_kxk(double* g, const double* s, int m, int n) {
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) g[(e / n) * 32 + e % n] = s[(e / n) * MEG_LDK + e % n];
+}
+
+__device__ __forceinline__ void load_kxk(const double* g, double* s, int m, int n) {
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) s[(e / n) * MEG_LDK + e % n] = g[(e / n) * 32 + e % n];
+    __syncthreads();
+}
+
+__device__ __forceinline__ double lse(const double* x, int cnt) {
+    double m = x[0];
+    for (int i = 1; i < cnt; ++i) m = fmax(m, x[i]);
+    double acc = 0.0;
+    for (int i = 0; i < cnt; ++i) acc += exp(x[i] - m);
+    return m + log(acc);
+}
+
+}  // namespace
+
+// ==========================================================================
+// begin: per-iteration scalars (one block of 32 threads per solve).
+//
+// M_t = log X_t - eta grad f(X_t) in closed form (Section 3):
+//   log X_t = V diag(log mu - log s) V^T + log s I.
+// Dense quadratic: grad f = X - M, so M_t = V diag(log mu - log s - eta (mu - s)) V^T
+//   + (log s - eta s) I + eta M  (alpha = +eta, gradient part Y = M W).
+// Other kinds: the gradient part enters with alpha = -eta.
+// Shift: subspace iteration finds the eigenvalues largest in magnitude, the
+// wanted ones are the algebraically largest of M_t, whose spectrum is
+// negative.  Reading adopted: iterate on M_t - c I with
+// c = min(log s, min log mu) - eta * g, g a bound on ||grad f||_2 (Frobenius
+// norm of the gradient or of its minibatch form), which makes M_t - c I
+// positive semidefinite; the Ritz values are shifted back exactly.
+// Warm start (mode 1) runs the same machinery on -grad f(0) - c I.
+__global__ void k_begin(const SolveDev* sds, int ns) {
+    const int si = blockIdx.x;
+    if (si >= ns) return;
+    const SolveDev& s = sds[si];
+    double* sm = s.sm;
+    if (threadIdx.x != 0) return;
+    const int r = s.r;
+    if (s.mode == 1) {
+        for (int l = 0; l < r; ++l) sm[SM_DCOEF + l] = 0.0;
+        sm[SM_C0] = 0.0;
+        sm[SM_ALPHA] = (s.kind == MEG_DENSE_QUAD) ? 1.0 : -1.0;
+        double g0;
+        if (s.kind == MEG_MEAS_STOCH) g0 = sm[SM_RESID_BOUND];
+        else if (s.kind == MEG_CSR_QUAD) g0 = sm[SM_RSS];
+        else g0 = sqrt(sm[SM_FROD2]);
+        sm[SM_SHIFT] = -1.0001 * g0 - 1e-300;
+        return;
+    }
+    const double t = sm[SM_T];
+    const double eps = eps_of(s, t);
+    sm[SM_EPS] = eps;
+    const double sv = sm[SM_S];
+    const double logs = log(sv);
+    sm[SM_LOGS] = logs;
+    const double eta = s.eta;
+    double lmin = logs;
+    for (int l = 0; l < r; ++l) {
+        double mu = sm[SM_MU + l];
+        double d = log(mu) - logs;
+        lmin = fmin(lmin, log(mu));
+        if (s.kind == MEG_DENSE_QUAD) d -= eta * (mu - sv);
+        sm[SM_DCOEF + l] = d;
+    }
+    sm[SM_C0] = (s.kind == MEG_DENSE_QUAD) ? logs - eta * sv : logs;
+    sm[SM_ALPHA] = (s.kind == MEG_DENSE_QUAD) ? eta : -eta;
+    double g;
+    switch (s.kind) {
+        case MEG_DENSE_QUAD: g = sm[SM_GNORM]; break;
+        case MEG_LINEAR: g = sqrt(sm[SM_FROD2]); break;
+        case MEG_CSR_QUAD: g = sm[SM_RSS]; break;
+        default: g = sm[SM_RESID_BOUND]; break;
+    }
+    sm[SM_SHIFT] = lmin - eta * g - 1e-12 * fabs(lmin);
+}
+
+// ==========================================================================
+// combine: Z = (M_t - c I) W for the block's rows, reductions, last block.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int phase) {
+    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_RED];
+    if (lb < 0 || lb >= s.nb_red) return;
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+
+    extern __shared__ __align__(16) unsigned char smraw[];
+    // layout: Bc[r*k] Coef, sW/sZ/sY [rows_red*k] T, ent dw[2*528], then k x k doubles
+    Coef<T>* Bc = (Coef<T>*)smraw;
+    T* sW = (T*)(Bc + MEG_RMAX * MEG_KMAX);
+    T* sZ = sW + s.rows_red * k;
+    T* sY = sZ + s.rows_red * k;
+    dw* ent = (dw*)(((uintptr_t)(sY + s.rows_red * k) + 15) & ~(uintptr_t)15);
+    double* kx = (double*)(ent + 2 * 528);
+    __shared__ Coef<T> c_id, c_al;
+
+    const double* sm = s.sm;
+    const bool init = (phase == PH_INIT);
+    if (!init) {
+        for (int e = tid; e < r * k; e += NT) {
+            int l = e / k, j = e % k;
+            Bc[e].set(sm[SM_DCOEF + l] * sm[SM_U + l * 32 + j]);
+        }
+        if (tid == 0) {
+            c_id.set(sm[SM_C0] - sm[SM_SHIFT]);
+            c_al.set(sm[SM_ALPHA]);
+        }
+    }
+    __syncthreads();
+
+    const T* W = (const T*)s.W;
+    const double* V = s.V;
+    T* Z = (T*)s.Z;
+    const bool dense = (s.kind == MEG_DENSE_QUAD || s.kind == MEG_LINEAR);
+    for (int idx = tid; idx < nr * k; idx += NT) {
+        const int i = row0 + idx / k, j = idx % k;
+        const T w = W[(size_t)i * k + j];
+        T z, y = 0;
+        if (init) {
+            z = w;
+        } else {
+            if (dense) {
+                const T* Ys = (const T*)s.Ys;
+                for (int p = 0; p < s.nb_ds; ++p) y += Ys[((size_t)p * n + i) * k + j];
+            } else {
+                y = ((const T*)s.Y)[(size_t)i * k + j];
+            }
+            z = c_al.mul(y);
+            z = c_id.fma_(w, z);
+            for (int l = 0; l < r; ++l) z = Bc[l * k + j].fma_((T)V[(size_t)i * r + l], z);
+        }
+        Z[(size_t)i * k + j] = z;
+        sW[idx] = w;
+        sZ[idx] = z;
+        sY[idx] = y;
+    }
+    __syncthreads();
+
+    const int nsym = k * (k + 1) / 2;
+    const bool fin = (phase == PH_FINAL);
+    const int E = fin ? 2 * nsym : nsym;
+    for (int e = tid; e < E; e += NT) {
+        int m = e / nsym, i, j;
+        tri_decode(e % nsym, i, j);
+        Acc<T> a;
+        a.zero();
+        if (m == 0) {
+            for (int q = 0; q < nr; ++q) a.add_prod(sZ[q * k + i], sZ[q * k + j]);
+        } else {
+            for (int q = 0; q < nr; ++q) a.add_prod(sW[q * k + i], sY[q * k + j]);
+        }
+        ent[e] = a.as_dw();
+    }
+    __syncthreads();
+    if (!red_two_level(s, lb, ent, ent, E)) return;
+
+    // ---------------- last block of this solve: k x k island (float64)
+    double* S1 = kx;
+    double* A = S1 + 32 * MEG_LDK;
+    double* Bm = A + 32 * MEG_LDK;
+    double* C = Bm + 32 * MEG_LDK;
+    double* Qg = C + 32 * MEG_LDK;
+    double* JB = Qg + 32 * MEG_LDK;     // Jacobi scratch
+    double* wv = JB + 32 * MEG_LDK;     // [32]
+    double* pr = wv + 32;               // [96]
+    double* pdg = pr + 96;              // [32] v_i^T D v_i
+    __shared__ int flag;
+    double* smw = s.sm;
+    unpack_sym(ent, S1, k);
+    if (!fin) {
+        // W' = Z L^{-T}, L = chol(Z^T Z)
+        for (int e = tid; e < k * k; e += NT) A[(e / k) * MEG_LDK + e % k] = S1[(e / k) * MEG_LDK + e % k];
+        __syncthreads();
+        if (!kxk_chol(A, k, &flag) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+        kxk_inv_lower_T(A, C, k);
+        store_kxk(smw + SM_M1, C, k, k);
+        return;
+    }
+    // ---- Rayleigh-Ritz on span W (Section 3, three steps):
+    //   H = W^T (M_t - c I) W = U^T diag(d) U + (c0 - c) G + alpha P,  G = W^T W,
+    //   eigenpairs of the pencil (H, G) -> Ritz values theta, G-orthonormal Qg.
+    double* P = A;
+    unpack_sym(ent + nsym, P, k);
+    double* G = Bm;
+    load_kxk(smw + SM_G, G, k, k);
+    double* U = C;
+    load_kxk(smw + SM_U, U, r, k);
+    const double d_id = smw[SM_C0] - smw[SM_SHIFT], alpha = smw[SM_ALPHA], shift = smw[SM_SHIFT];
+    double* H = Qg;
+    for (int e = tid; e < k * k; e += NT) {
+        int i = e / k, j = e % k;
+        double h = d_id * G[i * MEG_LDK + j] + alpha * P[i * MEG_LDK + j];
+        for (int l = 0; l < r; ++l) h += U[l * MEG_LDK + i] * smw[SM_DCOEF + l] * U[l * MEG_LDK + j];
+        H[i * MEG_LDK + j] = h;
+    }
+    __syncthreads();
+    // G = L L^T; Ht = L^{-1} H L^{-T}
+    if (!kxk_chol(G, k, &flag) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+    double* Li = U;                       // U no longer needed (H is built)
+    kxk_inv_lower_T(G, Li, k);            // Li = L^{-T} (upper)
+    double* T1 = G;                       // L no longer needed
+    kxk_mm(H, false, Li, T1, k, k, k);    // T1 = H L^{-T}
+    kxk_mm(Li, true, T1, H, k, k, k);     // H <- L^{-1} H L^{-T}
+    double* Qt = T1;
+    kxk_jacobi(H, Qt, JB, wv, pr, k, 30);
+    kxk_mm(Li, false, Qt, Qg, k, k, k);   // Qg = L^{-T} Qt  (G-orthonormal Ritz coordinates)
+    // v_i^T D v_i = (Qg^T P Qg)_ii for the objective estimate (dense data)
+    kxk_mm(P, false, Qg, JB, k, k, r);    // JB = P Qg[:, :r]
+    if (tid < r) {
+        double acc = 0.0;
+        for (int a = 0; a < k; ++a) acc += Qg[a * MEG_LDK + tid] * JB[a * MEG_LDK + tid];
+        pdg[tid] = acc;
+    }
+    __syncthreads();
+
+    // Ritz values sigma_i = theta_i + c, kept in shared memory
+    __shared__ double sig[MEG_KMAX];
+    __shared__ double mun[MEG_KMAX];
+    if (tid < k) {
+        sig[tid] = wv[tid] + shift;
+        smw[SM_SIGMA + tid] = sig[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int i = 0; i < k; ++i)
+            if (!isfinite(sig[i])) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+        const double t = smw[SM_T];
+        if (s.mode == 1) {
+            // eq. (exp:init), U = 0: eigenvalues of -grad f(0) projected on the simplex
+            for (int i = 0; i < r; ++i) mun[i] = sig[i];
+            simplex_project(mun, r);
+            const double eps0 = eps_of(s, 0.0);
+            for (int i = 0; i < r; ++i) smw[SM_MU + i] = (1.0 - eps0) * mun[i] + eps0 / n;
+            smw[SM_S] = eps0 / n;
+            smw[SM_T] = 1.0;
+            smw[SM_LAST_T] = 0.0;
+            smw[SM_CERT] = 0.0;
+            smw[SM_HOLDS] = 0.0;
+            smw[SM_FIRST_HOLD] = 0.0;
+        } else {
+            const double eps = smw[SM_EPS];
+            // Lemma 2 certificate with b_{r+1} (eq. convergenceGuaranteeExperiment2):
+            //   C_t = log((n - r) e^{sigma_{r+1}} / (eps_t b_{r+1})),  b_{r+1} = sum_{i<=r+1} e^{sigma_i}
+            const double lse_r1 = lse(sig, r + 1);
+            const double cert = log((double)(n - r)) + sig[r] - log(eps) - lse_r1;
+            const int holds = cert <= 2.0 * eps;
+            // Definition 2: mu_i = (1 - eps) e^{sigma_i} / sum_{j<=r} e^{sigma_j}, s = eps/(n - r)
+            const double lse_r = lse(sig, r);
+            for (int i = 0; i < r; ++i) mun[i] = (1.0 - eps) * exp(sig[i] - lse_r);
+            const double s_new = eps / (double)(n - r);
+            smw[SM_LSE] = lse_r;
+            smw[SM_CERT] = cert;
+            smw[SM_HOLDS] = holds;
+            if (holds && smw[SM_FIRST_HOLD] == 0.0) smw[SM_FIRST_HOLD] = t;
+            smw[SM_LAST_T] = t;
+            if (s.kind == MEG_DENSE_QUAD || s.kind == MEG_LINEAR) {
+                // <X_{t+1}, D> = sum_i (mu_i - s) v_i^T D v_i + s Tr D
+                double xd = s_new * smw[SM_TRD], x2 = (double)(n - r) * s_new * s_new;
+                for (int i = 0; i < r; ++i) {
+                    xd += (mun[i] - s_new) * pdg[i];
+                    x2 += mun[i] * mun[i];
+                }
+                if (s.kind == MEG_DENSE_QUAD) {
+                    const double f = 0.5 * x2 - xd + 0.5 * smw[SM_FROD2];
+                    smw[SM_FEST] = f;
+                    smw[SM_GNORM] = 1.25 * sqrt(fmax(2.0 * f, 0.0));
+                } else {
+                    smw[SM_FEST] = xd;
+                }
+            }
+            for (int i = 0; i < r; ++i) smw[SM_MU + i] = mun[i];
+            smw[SM_S] = s_new;
+            smw[SM_T] = t + 1.0;
+        }
+    }
+    __syncthreads();
+    // V_{t+1} = W Qg[:, :r];  next block W' from CholQR of Z Qg (Ritz-ordered)
+    store_kxk(smw + SM_QV, Qg, k, r);
+    kxk_mm(S1, false, Qg, Bm, k, k, k);   // S1 Qg
+    kxk_mm(Qg, true, Bm, A, k, k, k);     // Qg^T S1 Qg
+    if (!kxk_chol(A, k, &flag) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+    kxk_inv_lower_T(A, C, k);             // L^{-T}
+    kxk_mm(Qg, false, C, Bm, k, k, k);    // M1 = Qg L^{-T}
+    store_kxk(smw + SM_M1, Bm, k, k);
+}
+
+// ==========================================================================
+// orth1: W' = Z M1 (first CholeskyQR pass); final phase also V_{t+1} = W Qv.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_orth1(const SolveDev* sds, int ns, int phase) {
+    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_RED];
+    if (lb < 0 || lb >= s.nb_red) return;
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* M1 = (T*)smraw;                                  // k x k
+    Coef<T>* Qv = (Coef<T>*)(M1 + MEG_KMAX * MEG_KMAX); // k x r
+    T* sW = (T*)(Qv + MEG_KMAX * MEG_RMAX);
+    dw* ent = (dw*)(((uintptr_t)(sW + s.rows_red * k) + 15) & ~(uintptr_t)15);
+    double* kx = (double*)(ent + 528);
+    const double* sm = s.sm;
+    const bool fin = (phase == PH_FINAL);
+    for (int e = tid; e < k * k; e += NT) M1[e] = (T)sm[SM_M1 + (e / k) * 32 + e % k];
+    if (fin)
+        for (int e = tid; e < k * r; e += NT) Qv[e].set(sm[SM_QV + (e / r) * 32 + e % r]);
+    __syncthreads();
+    const T* Z = (const T*)s.Z;
+    const T* W = (const T*)s.W;
+    T* Wp = (T*)s.Wp;
+    double* Vn = s.Vn;
+    for (int idx = tid; idx < nr * k; idx += NT) {
+        const int q = idx / k, j = idx % k, i = row0 + q;
+        T acc = 0;
+        for (int l = 0; l < k; ++l) acc += Z[(size_t)i * k + l] * M1[l * k + j];
+        Wp[(size_t)i * k + j] = acc;
+        sW[idx] = acc;
+    }
+    if (fin) {
+        for (int idx = tid; idx < nr * r; idx += NT) {
+            const int i = row0 + idx / r, j = idx % r;
+            // V_{t+1} = W Qv evaluated exactly enough to keep X_{t+1} at float64 accuracy
+            if constexpr (sizeof(T) == 8) {
+                double acc = 0.0;
+                for (int l = 0; l < k; ++l) acc = Qv[l * r + j].fma_(W[(size_t)i * k + l], acc);
+                Vn[(size_t)i * r + j] = acc;
+            } else {
+                dw acc = {0.f, 0.f};
+                for (int l = 0; l < k; ++l) {
+                    const float w = W[(size_t)i * k + l];
+                    dot2_acc(acc, w, Qv[l * r + j].hi);
+                    dot2_acc(acc, w, Qv[l * r + j].lo);
+                }
+                Vn[(size_t)i * r + j] = dw_value(acc);
+            }
+        }
+    }
+    __syncthreads();
+    const int nsym = k * (k + 1) / 2;
+    for (int e = tid; e < nsym; e += NT) {
+        int i, j;
+        tri_decode(e, i, j);
+        Acc<T> a;
+        a.zero();
+        for (int q = 0; q < nr; ++q) a.add_prod(sW[q * k + i], sW[q * k + j]);
+        ent[e] = a.as_dw();
+    }
+    __syncthreads();
+    if (!red_two_level(s, lb, ent, ent, nsym)) return;
+    double* A = kx;
+    double* C = A + 32 * MEG_LDK;
+    __shared__ int flag;
+    unpack_sym(ent, A, k);
+    if (!kxk_chol(A, k, &flag) && tid == 0) s.sm[SM_STATUS] = MEG_ERR_NUMERIC;
+    kxk_inv_lower_T(A, C, k);
+    store_kxk(s.sm + SM_M2, C, k, k);
+}
+
+// ==========================================================================
+// orth2: W = W' M2 (second CholeskyQR pass); final phase commits V = V_{t+1}.
+// Reductions U = V^T W and G = W^T W for the next product's operator and
+// Rayleigh-Ritz step.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int phase) {
+    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_RED];
+    if (lb < 0 || lb >= s.nb_red) return;
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* M2 = (T*)smraw;
+    T* sW = M2 + MEG_KMAX * MEG_KMAX;
+    double* sV = (double*)(((uintptr_t)(sW + s.rows_red * k) + 7) & ~(uintptr_t)7);
+    dw* ent = (dw*)(((uintptr_t)(sV + s.rows_red * r) + 15) & ~(uintptr_t)15);
+    const double* sm = s.sm;
+    const bool fin = (phase == PH_FINAL);
+    for (int e = tid; e < k * k; e += NT) M2[e] = (T)sm[SM_M2 + (e / k) * 32 + e % k];
+    __syncthreads();
+    const T* Wp = (const T*)s.Wp;
+    T* W = (T*)s.W;
+    double* V = s.V;
+    const double* Vn = s.Vn;
+    for (int idx = tid; idx < nr * k; idx += NT) {
+        const int i = row0 + idx / k, j = idx % k;
+        T acc = 0;
+        for (int l = 0; l < k; ++l) acc += Wp[(size_t)i * k + l] * M2[l * k + j];
+        W[(size_t)i * k + j] = acc;
+        sW[idx] = acc;
+    }
+    for (int idx = tid; idx < nr * r; idx += NT) {
+        const int i = row0 + idx / r, j = idx % r;
+        double v;
+        if (fin) {
+            v = Vn[(size_t)i * r + j];
+            V[(size_t)i * r + j] = v;
+        } else {
+            v = V[(size_t)i * r + j];
+        }
+        sV[idx] = v;
+    }
+    __syncthreads();
+    const int nsym = k * (k + 1) / 2;
+    const int E = nsym + r * k;
+    for (int e = tid; e < E; e += NT) {
+        Acc<T> a;
+        a.zero();
+        if (e < nsym) {
+            int i, j;
+            tri_decode(e, i, j);
+            for (int q = 0; q < nr; ++q) a.add_prod(sW[q * k + i], sW[q * k + j]);
+        } else {
+            int l = (e - nsym) / k, j = (e - nsym) % k;
+            for (int q = 0; q < nr; ++q) {
+                const double v = sV[q * r + l];
+                if constexpr (sizeof(T) == 8) {
+                    a.add_prod(v, sW[q * k + j]);
+                } else {      // V is float64: split into two floats, both products exact in Dot2
+                    const float hi = (float)v, lo = (float)(v - (double)hi);
+                    a.add_prod(hi, sW[q * k + j]);
+                    a.add_prod(lo, sW[q * k + j]);
+                }
+            }
+        }
+        ent[e] = a.as_dw();
+    }
+    __syncthreads();
+    if (!red_two_level(s, lb, ent, ent, E)) return;
+    double* smw = s.sm;
+    for (int e = tid; e < nsym; e += NT) {
+        int i, j;
+        tri_decode(e, i, j);
+        double v = dw_value(ent[e]);
+        smw[SM_G + i * 32 + j] = v;
+        smw[SM_G + j * 32 + i] = v;
+    }
+    for (int e = tid; e < r * k; e += NT) smw[SM_U + (e / k) * 32 + e % k] = dw_value(ent[nsym + e]);
+}
+
+// ==========================================================================
+// Dense gradient part: Ys[split] = D[:, Ks] W[Ks, :]  (FFMA, T = double/float).
+// 64-row tiles, K tiles of 32, k <= 32 columns; each split of K writes its
+// own partial (summed in k_combine).
+template <typename T> __device__ __forceinline__ T load_d(const void* D, size_t idx, int prec) {
+    if (prec == MEG_MIXED_BF16) {
+        unsigned short b = ((const unsigned short*)D)[idx];
+        return (T)__uint_as_float(((unsigned)b) << 16);
+    }
+    return ((const T*)D)[idx];
+}
+
+template <typename T, typename TD> __device__ __forceinline__ T load_dt(const TD* D, size_t idx) {
+    return (T)D[idx];
+}
+template <> __device__ __forceinline__ float load_dt<float, unsigned short>(const unsigned short* D, size_t idx) {
+    return __uint_as_float(((unsigned)D[idx]) << 16);
+}
+
+template <typename T, typename TD>
+__global__ void __launch_bounds__(NT) k_dense(const SolveDev* sds, int ns) {
+    const int si = find_solve(sds, ns, PK_DENSE, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_DENSE];
+    if (lb < 0 || lb >= s.nb_dm * s.nb_ds) return;
+    const int n = s.n, k = s.k, tid = threadIdx.x;
+    const int mt = lb % s.nb_dm, sp = lb / s.nb_dm;
+    const int m0 = mt * 64;
+    const int k0 = sp * s.ks_len, k1 = min(n, k0 + s.ks_len);
+    __shared__ T Ds[32][64 + 1];
+    __shared__ __align__(16) T Ws[32][32];
+    const TD* D = (const TD*)s.D;
+    const T* W = (const T*)s.W;
+    const int ty = tid >> 3, tx = tid & 7;     // rows ty, ty+32; cols 4 tx .. 4 tx + 3
+    T acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    for (int kb = k0; kb < k1; kb += 32) {
+        for (int e = tid; e < 64 * 32; e += NT) {
+            int row = e >> 5, col = e & 31;
+            int gi = m0 + row, gk = kb + col;
+            Ds[col][row] = (gi < n && gk < k1) ? load_dt<T, TD>(D, (size_t)gi * n + gk) : (T)0;
+        }
+        for (int e = tid; e < 32 * 32; e += NT) {
+            int kk = e >> 5, c = e & 31;
+            int gk = kb + kk;
+            Ws[kk][c] = (gk < k1 && c < k) ? W[(size_t)gk * k + c] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 32; ++kk) {
+            T d0 = Ds[kk][ty], d1 = Ds[kk][ty + 32];
+            T w0 = Ws[kk][4 * tx], w1 = Ws[kk][4 * tx + 1], w2 = Ws[kk][4 * tx + 2], w3 = Ws[kk][4 * tx + 3];
+            acc[0][0] += d0 * w0; acc[0][1] += d0 * w1; acc[0][2] += d0 * w2; acc[0][3] += d0 * w3;
+            acc[1][0] += d1 * w0; acc[1][1] += d1 * w1; acc[1][2] += d1 * w2; acc[1][3] += d1 * w3;
+        }
+        __syncthreads();
+    }
+    T* Ys = (T*)s.Ys + (size_t)sp * n * k;
+    for (int a = 0; a < 2; ++a) {
+        int gi = m0 + ty + 32 * a;
+        if (gi >= n) continue;
+        for (int b = 0; b < 4; ++b) {
+            int c = 4 * tx + b;
+            if (c < k) Ys[(size_t)gi * k + c] = acc[a][b];
+        }
+    }
+}
+
+// ==========================================================================
+// CSR gradient part (matrix completion): Y = P_Omega(X - M) W, the residual
+// R_ij = X_ij - M_ij formed on the fly from the factors (never stored).
+// One warp per row.  Also sum of R_ij^2 (for the shift bound of the next
+// iteration), reduced deterministically through per-block partials.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_csr(const SolveDev* sds, int ns) {
+    const int si = find_solve(sds, ns, PK_CSR, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_CSR];
+    if (lb < 0 || lb >= s.nb_csr) return;
+    const int n = s.n, k = s.k, r = s.r;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = lb * (NT / 32) + warp;
+    __shared__ double coef[MEG_RMAX + 1];
+    __shared__ double wsum[NT / 32];
+    const bool warm = (s.mode == 1);
+    if (threadIdx.x < r) coef[threadIdx.x] = warm ? 0.0 : s.sm[SM_MU + threadIdx.x] - s.sm[SM_S];
+    if (threadIdx.x == 0) coef[MEG_RMAX] = warm ? 0.0 : s.sm[SM_S];
+    __syncthreads();
+    const double* V = s.V;
+    const T* W = (const T*)s.W;
+    const T* val = (const T*)s.val;
+    double rabs = 0.0;        // sum_j |R_ij| of this row: ||P_Omega(X - M)||_2 <= max_i of it
+    if (i < n) {
+        T vi[MEG_RMAX];
+        // V_il (mu_l - s) formed in float64 and rounded once: the rounding errors are
+        // independent across (i, l) instead of a shared error in (mu_l - s)
+        for (int l = 0; l < r; ++l) vi[l] = (T)(V[(size_t)i * r + l] * coef[l]);
+        T z[MEG_KMAX];
+        for (int c = 0; c < k; ++c) z[c] = 0;
+        const int b = s.rowptr[i], e = s.rowptr[i + 1];
+        for (int p = b + lane; p < e; p += 32) {
+            const int j = s.col[p];
+            T x = (j == i) ? (T)coef[MEG_RMAX] : (T)0;
+            for (int l = 0; l < r; ++l) x += vi[l] * (T)V[(size_t)j * r + l];
+            const T R = x - val[p];
+            rabs += fabs((double)R);
+            for (int c = 0; c < k; ++c) z[c] += R * W[(size_t)j * k + c];
+        }
+        for (int c = 0; c < k; ++c) {
+            T v = z[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) ((T*)s.Y)[(size_t)i * k + c] = v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) rabs += __shfl_xor_sync(0xffffffffu, rabs, o);
+    if (lane == 0) wsum[warp] = rabs;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t = fmax(t, wsum[w]);
+        double* pr = s.meas;                  // CSR kinds use the scratch for row-block sums
+        pr[lb] = t;
+        __threadfence();
+        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 1;
+        unsigned prev = atomicAdd(c, 1u);
+        if (prev == (unsigned)(s.nb_csr - 1)) {
+            *c = 0u;
+            double tot = 0.0;
+            for (int q = 0; q < s.nb_csr; ++q) tot = fmax(tot, __ldcg(pr + q));
+            s.sm[SM_RSS] = tot;
+        }
+    }
+}
+
+// ==========================================================================
+// Measurement objective.  Minibatch of step t: L indices drawn with
+// replacement by SplitMix64 (index j: splitmix64(seed + (t L + j + 1) gamma)
+// mod m); mode 1 (warm start) uses every measurement once.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <typename T> __device__ __forceinline__ T load_a(const void* A, size_t idx);
+template <> __device__ __forceinline__ double load_a<double>(const void* A, size_t idx) {
+    return ((const double*)A)[idx];
+}
+template <> __device__ __forceinline__ float load_a<float>(const void* A, size_t idx) {
+    unsigned short b = ((const unsigned short*)A)[idx];
+    return __uint_as_float(((unsigned)b) << 16);
+}
+
+// one block per batch element b: r_b = a^T X a - y (mode 0) or -y (mode 1),
+// ||a||^2 and T_b = a^T W (k values)
+template <typename T>
+__global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) {
+    const int si = find_solve(sds, ns, PK_MEAS, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int b = blockIdx.x - s.off[PK_MEAS];
+    if (b < 0 || b >= s.nb_meas) return;
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const bool warm = (s.mode == 1);
+    const int64_t idx = warm ? (int64_t)b
+        : (int64_t)(splitmix64(s.seed + ((uint64_t)s.sm[SM_T] * (uint64_t)s.L + (uint64_t)b + 1ull) *
+                               0x9E3779B97F4A7C15ull) % (uint64_t)s.m);
+    const double* V = s.V;
+    const T* W = (const T*)s.W;
+    T acc[MEG_RMAX + 1 + MEG_KMAX];
+    const int nacc = r + 1 + k;
+    for (int c = 0; c < nacc; ++c) acc[c] = 0;
+    for (int i = tid; i < n; i += NT) {
+        T a = load_a<T>(s.A, (size_t)idx * n + i);
+        if (!warm)
+            for (int l = 0; l < r; ++l) acc[l] += a * (T)V[(size_t)i * r + l];
+        acc[r] += a * a;
+        for (int c = 0; c < k; ++c) acc[r + 1 + c] += a * W[(size_t)i * k + c];
+    }
+    __shared__ double red[NT / 32][MEG_RMAX + 1 + MEG_KMAX];
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int c = 0; c < nacc; ++c) {
+        double v = (double)acc[c];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][c] = v;
+    }
+    __syncthreads();
+    if (tid < nacc) {
+        double v = 0.0;
+        for (int w = 0; w < NT / 32; ++w) v += red[w][tid];
+        red[0][tid] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double sv = warm ? 0.0 : s.sm[SM_S];
+        double q = sv * red[0][r];
+        if (!warm)
+            for (int l = 0; l < r; ++l) q += (s.sm[SM_MU + l] - sv) * red[0][l] * red[0][l];
+        const double res = q - s.y[idx];
+        const int Lb = s.nb_meas;
+        double* sc = s.meas;              // [Lb] residual, [Lb] ||a||^2, [Lb x 32] T_b
+        sc[b] = res;
+        sc[Lb + b] = red[0][r];
+        if (!warm) s.bidx[b] = (int)idx;
+        __threadfence();
+        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
+        unsigned prev = atomicAdd(c, 1u);
+        if (prev == (unsigned)(Lb - 1)) {
+            *c = 0u;
+            // Minibatch (mode 0): the L vectors a_b are nearly orthogonal, so the
+            // eigenvalues of (2/L) sum r_b a_b a_b^T are close to (2/L) r_b ||a_b||^2;
+            // estimate ||grad||_2 by (2/L) max_b |r_b| ||a_b||^2 (1 + sqrt(L/n))^2.
+            // The estimate only sets the shift (convergence speed); Rayleigh-Ritz is exact.
+            // Warm start (mode 1, r_b = -y_b): lambda_min(-grad f(0)) >= -(2/m) sum_{y<0} |y| ||a||^2.
+            double bound = 0.0;
+            if (warm) {
+                for (int q2 = 0; q2 < Lb; ++q2) {
+                    double rb = __ldcg(sc + q2);
+                    if (rb > 0.0) bound += rb * __ldcg(sc + Lb + q2);
+                }
+                bound *= 2.0 / (double)Lb;
+            } else {
+                for (int q2 = 0; q2 < Lb; ++q2) bound = fmax(bound, fabs(__ldcg(sc + q2)) * __ldcg(sc + Lb + q2));
+                const double f = 1.0 + sqrt((double)Lb / (double)n);
+                bound *= 2.0 / (double)Lb * f * f;
+            }
+            s.sm[SM_RESID_BOUND] = bound;
+        }
+    }
+    if (tid < k) s.meas[2 * (size_t)s.nb_meas + (size_t)b * MEG_KMAX + tid] = red[0][r + 1 + tid];
+}
+
+// Y = (2/L) sum_b r_b a_b (a_b^T W): one block per 64 rows of Y.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_meas_apply(const SolveDev* sds, int ns) {
+    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_RED];
+    if (lb < 0 || lb >= s.nb_red || s.kind != MEG_MEAS_STOCH) return;
+    const int n = s.n, k = s.k, tid = threadIdx.x;
+    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    const bool warm = (s.mode == 1);
+    const int Lb = s.nb_meas;
+    const double scale = 2.0 / (double)Lb;
+    const double* sc = s.meas;
+    __shared__ T Sb[64][MEG_KMAX];
+    T acc[4] = {0, 0, 0, 0};
+    const int nout = nr * k;
+    for (int b0 = 0; b0 < Lb; b0 += 64) {
+        const int bn = min(64, Lb - b0);
+        __syncthreads();
+        for (int e = tid; e < bn * k; e += NT) {
+            int bb = e / k, c = e % k;
+            Sb[bb][c] = (T)(scale * sc[b0 + bb] * sc[2 * (size_t)Lb + (size_t)(b0 + bb) * MEG_KMAX + c]);
+        }
+        __syncthreads();
+        for (int q = 0; q < 4; ++q) {
+            int o = tid + q * NT;
+            if (o >= nout) break;
+            int i = row0 + o / k, c = o % k;
+            T a2 = acc[q];
+            for (int bb = 0; bb < bn; ++bb) {
+                int64_t idx = warm ? (int64_t)(b0 + bb) : (int64_t)s.bidx[b0 + bb];
+                a2 += load_a<T>(s.A, (size_t)idx * n + i) * Sb[bb][c];
+            }
+            acc[q] = a2;
+        }
+    }
+    for (int q = 0; q < 4; ++q) {
+        int o = tid + q * NT;
+        if (o >= nout) break;
+        int i = row0 + o / k, c = o % k;
+        ((T*)s.Y)[(size_t)i * k + c] = acc[q];
+    }
+}
+
+// ==========================================================================
+// Accurate objective f(X_t): dense pass / Omega pass / all measurements.
+// The quantities that cancel (X_ij - M_ij, a^T X a - y) are formed in
+// double-word arithmetic from float64 V (Dot2 with both factors split into
+// float pairs), then squared and summed with compensation; deterministic
+// last-block total.  Float64 storage uses plain float64 arithmetic.
+struct XdotDw {
+    // x += w * v with w, v float64 values, both split into float pairs
+    __device__ __forceinline__ static void acc(dw& x, double w, double v) {
+        const float wh = (float)w, wl = (float)(w - (double)wh);
+        const float vh = (float)v, vl = (float)(v - (double)vh);
+        dot2_acc(x, wh, vh);
+        dot2_acc(x, wh, vl);
+        dot2_acc(x, wl, vh);
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ double load_val(const void* val, int64_t p) { return (double)((const T*)val)[p]; }
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, double* out) {
+    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_RED];
+    if (lb < 0 || lb >= s.nb_red) return;
+    const int n = s.n, r = s.r, tid = threadIdx.x;
+    const double* V = s.V;
+    __shared__ double coef[MEG_RMAX + 1];
+    if (tid < r) coef[tid] = s.sm[SM_MU + tid] - s.sm[SM_S];
+    if (tid == 0) coef[MEG_RMAX] = s.sm[SM_S];
+    __syncthreads();
+    Acc<T> acc;
+    acc.zero();
+    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red);
+    const bool dense = (s.kind == MEG_DENSE_QUAD || s.kind == MEG_LINEAR);
+    if (dense || s.kind == MEG_CSR_QUAD) {
+        for (int i = row0; i < row1; ++i) {
+            double wi[MEG_RMAX];
+            for (int l = 0; l < r; ++l) wi[l] = V[(size_t)i * r + l] * coef[l];
+            const int64_t pb = dense ? 0 : s.rowptr[i], pe = dense ? n : s.rowptr[i + 1];
+            for (int64_t p = pb + tid; p < pe; p += NT) {
+                const int j = dense ? (int)p : s.col[p];
+                const double d = dense ? (double)load_d<T>(s.D, (size_t)i * n + j, s.prec) : load_val<T>(s.val, p);
+                if constexpr (sizeof(T) == 8) {
+                    double x = (j == i) ? coef[MEG_RMAX] : 0.0;
+                    for (int l = 0; l < r; ++l) x = fma(wi[l], V[(size_t)j * r + l], x);
+                    if (s.kind == MEG_LINEAR) acc.add_prod(x, d);
+                    else { const double R = x - d; acc.add_prod(R, R); }
+                } else {
+                    dw x = dw_from_double((j == i) ? coef[MEG_RMAX] : 0.0);
+                    for (int l = 0; l < r; ++l) XdotDw::acc(x, wi[l], V[(size_t)j * r + l]);
+                    if (s.kind == MEG_LINEAR) {
+                        dot2_acc(acc.v, x.hi, (float)d);
+                        dot2_acc(acc.v, x.lo, (float)d);
+                    } else {
+                        float e, hi;
+                        two_sum(x.hi, -(float)d, hi, e);       // d is exactly a float
+                        const float R = __fadd_rn(hi, __fadd_rn(e, x.lo));
+                        acc.add_prod(R, R);
+                    }
+                }
+            }
+        }
+    } else {
+        // measurements: rows of this block index measurement blocks over m
+        const int64_t per = (s.m + s.nb_red - 1) / s.nb_red;
+        const int64_t i0 = (int64_t)lb * per, i1 = min((int64_t)s.m, i0 + per);
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int64_t i = i0 + warp; i < i1; i += NT / 32) {
+            dw p[MEG_RMAX + 1];
+            for (int l = 0; l <= r; ++l) p[l] = {0.f, 0.f};
+            for (int j = lane; j < n; j += 32) {
+                const double a = (double)load_a<T>(s.A, (size_t)i * n + j);
+                for (int l = 0; l < r; ++l) XdotDw::acc(p[l], a, V[(size_t)j * r + l]);
+                XdotDw::acc(p[r], a, a);
+            }
+            double pv[MEG_RMAX + 1];
+            for (int l = 0; l <= r; ++l) {
+                double v = dw_value(p[l]);
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                pv[l] = v;
+            }
+            if (lane == 0) {
+                double q = coef[MEG_RMAX] * pv[r];
+                for (int l = 0; l < r; ++l) q += coef[l] * pv[l] * pv[l];
+                const double R = q - s.y[i];
+                const double w = R * R / (double)s.m;
+                if constexpr (sizeof(T) == 8) acc.add_prod(w, 1.0);
+                else {
+                    const float wh = (float)w;
+                    acc.add_prod(wh, 1.f);
+                    acc.add_prod((float)(w - (double)wh), 1.f);
+                }
+            }
+        }
+    }
+    __shared__ dw ent[NT];
+    ent[tid] = acc.as_dw();
+    __syncthreads();
+    if (tid == 0) {
+        dw a = {0.f, 0.f};
+        for (int q = 0; q < NT; ++q) dw_add(a, ent[q]);
+        ent[0] = a;
+    }
+    __syncthreads();
+    __shared__ dw fin;
+    if (!red_two_level(s, lb, ent, &fin, 1)) return;
+    if (tid == 0) {
+        double v = dw_value(fin);
+        if (s.kind == MEG_DENSE_QUAD || s.kind == MEG_CSR_QUAD) v *= 0.5;
+        out[si] = v;
+    }
+}
+
+// ==========================================================================
+// host launch wrappers
+namespace {
+size_t combine_smem(int prec) {
+    size_t tsz = prec == MEG_FP64 ? 8 : 4;
+    size_t coef = (prec == MEG_FP64 ? 8 : 8) * MEG_RMAX * MEG_KMAX;
+    size_t rows = 3 * 16 * MEG_KMAX * tsz;          // rows_red <= 16
+    size_t ent = 2 * 528 * sizeof(dw) + 16;
+    size_t kx = (6 * 32 * MEG_LDK + 32 + 96 + 32) * sizeof(double);
+    return coef + rows + ent + kx;
+}
+size_t orth1_smem(int prec) {
+    size_t tsz = prec == MEG_FP64 ? 8 : 4;
+    return MEG_KMAX * MEG_KMAX * tsz + 8 * MEG_KMAX * MEG_RMAX + 16 * MEG_KMAX * tsz + 528 * sizeof(dw) + 16 +
+           2 * 32 * MEG_LDK * sizeof(double);
+}
+size_t orth2_smem(int prec) {
+    size_t tsz = prec == MEG_FP64 ? 8 : 4;
+    return MEG_KMAX * MEG_KMAX * tsz + 16 * MEG_KMAX * tsz + 8 + 16 * MEG_RMAX * 8 + RED_MAX_ENTRIES * sizeof(dw) + 16;
+}
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+}  // namespace
+
+cudaError_t init_kernel_attributes() {
+    cudaError_t e;
+    if ((e = set_smem(k_combine<double>, combine_smem(MEG_FP64))) != cudaSuccess) return e;
+    if ((e = set_smem(k_combine<float>, combine_smem(MEG_FP32))) != cudaSuccess) return e;
+    if ((e = set_smem(k_orth1<double>, orth1_smem(MEG_FP64))) != cudaSuccess) return e;
+    if ((e = set_smem(k_orth1<float>, orth1_smem(MEG_FP32))) != cudaSuccess) return e;
+    if ((e = set_smem(k_orth2<double>, orth2_smem(MEG_FP64))) != cudaSuccess) return e;
+    if ((e = set_smem(k_orth2<float>, orth2_smem(MEG_FP32))) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_begin(const GroupLaunch& g) {
+    k_begin<<<g.ns, 32, 0, g.stream>>>(g.d_solves, g.ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense(const GroupLaunch& g) {
+    if (g.blocks[PK_DENSE] == 0) return cudaSuccess;
+    if (g.prec == MEG_FP64) k_dense<double, double><<<g.blocks[PK_DENSE], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    else if (g.prec == MEG_FP32) k_dense<float, float><<<g.blocks[PK_DENSE], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    else k_dense<float, unsigned short><<<g.blocks[PK_DENSE], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr(const GroupLaunch& g) {
+    if (g.blocks[PK_CSR] == 0) return cudaSuccess;
+    if (g.prec == MEG_FP64) k_csr<double><<<g.blocks[PK_CSR], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    else k_csr<float><<<g.blocks[PK_CSR], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_meas_batch(const GroupLaunch& g) {
+    if (g.blocks[PK_MEAS] == 0) return cudaSuccess;
+    if (g.prec == MEG_FP64) k_meas_batch<double><<<g.blocks[PK_MEAS], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    else k_meas_batch<float><<<g.blocks[PK_MEAS], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_meas_apply(const GroupLaunch& g) {
+    if (g.blocks[PK_MEAS] == 0) return cudaSuccess;
+    if (g.prec == MEG_FP64) k_meas_apply<double><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    else k_meas_apply<float><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const GroupLaunch& g, int phase) {
+    size_t sm = combine_smem(g.prec);
+    if (g.prec == MEG_FP64) {
+        k_combine<double><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+    } else {
+        k_combine<float><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orth1(const GroupLaunch& g, int phase) {
+    size_t sm = orth1_smem(g.prec);
+    if (g.prec == MEG_FP64) {
+        k_orth1<double><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+    } else {
+        k_orth1<float><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orth2(const GroupLaunch& g, int phase) {
+    size_t sm = orth2_smem(g.prec);
+    if (g.prec == MEG_FP64) {
+        k_orth2<double><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+    } else {
+        k_orth2<float><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective(const GroupLaunch& g, double* out_f) {
+    if (g.prec == MEG_FP64) k_objective<double><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns, out_f);
+    else k_objective<float><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns, out_f);
+    return cudaGetLastError();
+}

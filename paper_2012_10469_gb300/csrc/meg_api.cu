@@ -1,0 +1,735 @@
+// C ABI of the low-rank MEG library (declared in include/meg.h).
+//
+// Host-side responsibilities: argument checks, device buffers of each solve,
+// the order of kernel launches in one iteration of Algorithm 2, CUDA graphs
+// of an iteration, grouped launches over several solves.  Every arithmetic
+// step of the method runs in the kernels of kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "meg_dev.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+meg_status fail(meg_status st, const std::string& msg) {
+    g_last_error = msg;
+    return st;
+}
+
+#define CU(expr)                                                                              \
+    do {                                                                                      \
+        cudaError_t _e = (expr);                                                              \
+        if (_e != cudaSuccess)                                                                \
+            return fail(MEG_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));   \
+    } while (0)
+
+std::once_flag g_attr_once;
+cudaError_t g_attr_err = cudaSuccess;
+
+cudaError_t ensure_attributes() {
+    std::call_once(g_attr_once, [] { g_attr_err = init_kernel_attributes(); });
+    return g_attr_err;
+}
+
+constexpr int ROWS_RED = 16;
+
+size_t tsize(int prec) { return prec == MEG_FP64 ? 8 : 4; }
+
+int dense_splits(int n) {
+    const int nb_dm = (n + 63) / 64;
+    int target = 2 * 152;
+    int s = std::max(1, (target + nb_dm - 1) / nb_dm);
+    s = std::min(s, std::max(1, n / 128));
+    return std::max(1, s);
+}
+
+}  // namespace
+
+struct meg_solve_s {
+    meg_options opt{};
+    int n = 0, r = 0, k = 0, q = 0, prec = 0;
+    cudaStream_t stream = nullptr;
+    // device buffers (owned)
+    void *V = nullptr, *Vn = nullptr, *W = nullptr, *Wp = nullptr, *Z = nullptr, *Y = nullptr, *Ys = nullptr;
+    float* part = nullptr;
+    unsigned* ctr = nullptr;
+    double* sm = nullptr;
+    double* meas = nullptr;
+    int* bidx = nullptr;
+    double* d_f = nullptr;
+    SolveDev desc{};
+    SolveDev* d_desc = nullptr;   // solo descriptor (offsets 0)
+    bool has_obj = false, has_x = false;
+    meg_objective_desc obj{};
+    double fstar = 0.0;
+    // solo graph of one iteration
+    cudaGraphExec_t gexec = nullptr;
+    bool in_group = false;
+    cudaStream_t group_stream = nullptr;   // stream of the group while in one
+    bool own_stream = false;               // created by the library (caller gave NULL)
+};
+
+struct meg_group_s {
+    std::vector<meg_solve_s*> solves;
+    SolveDev* d_desc = nullptr;
+    GroupLaunch gl{};
+    bool has_dense = false, has_csr = false, has_meas = false;
+    int q = 0;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool own_stream = false;
+};
+
+namespace {
+
+void compute_partition(meg_solve_s* h, SolveDev& d) {
+    d.rows_red = ROWS_RED;
+    d.nb_red = (h->n + ROWS_RED - 1) / ROWS_RED;
+    d.nb_dm = (h->n + 63) / 64;
+    d.nb_ds = dense_splits(h->n);
+    int kl = (h->n + d.nb_ds - 1) / d.nb_ds;
+    d.ks_len = ((kl + 31) / 32) * 32;
+    d.nb_ds = (h->n + d.ks_len - 1) / d.ks_len;
+    d.nb_csr = (h->n + 7) / 8;
+    d.nb_meas = 0;
+}
+
+int blocks_of(const SolveDev& d, int kind) {
+    switch (kind) {
+        case PK_RED: return d.nb_red;
+        case PK_DENSE: return (d.kind == MEG_DENSE_QUAD || d.kind == MEG_LINEAR) ? d.nb_dm * d.nb_ds : 0;
+        case PK_CSR: return d.kind == MEG_CSR_QUAD ? d.nb_csr : 0;
+        default: return d.kind == MEG_MEAS_STOCH ? d.nb_meas : 0;
+    }
+}
+
+GroupLaunch solo_launch(meg_solve_s* h) {
+    GroupLaunch g{};
+    g.d_solves = h->d_desc;
+    g.ns = 1;
+    for (int p = 0; p < PK_COUNT; ++p) g.blocks[p] = blocks_of(h->desc, p);
+    g.prec = h->prec;
+    g.stream = h->stream;
+    return g;
+}
+
+meg_status upload_desc(meg_solve_s* h, const SolveDev& d) {
+    CU(cudaMemcpyAsync(h->d_desc, &d, sizeof(SolveDev), cudaMemcpyHostToDevice, h->stream));
+    return MEG_OK;
+}
+
+// One iteration of Algorithm 2 (or one warm-start product set), enqueued.
+meg_status enqueue_iteration(const GroupLaunch& g, bool has_dense, bool has_csr, bool has_meas, int q) {
+    for (int j = 0; j < q; ++j) {
+        const int phase = (j == q - 1) ? PH_FINAL : PH_ADVANCE;
+        if (has_meas) CU(launch_meas_batch(g));
+        if (j == 0) CU(launch_begin(g));
+        if (has_dense) CU(launch_dense(g));
+        if (has_csr) CU(launch_csr(g));
+        if (has_meas) CU(launch_meas_apply(g));
+        CU(launch_combine(g, phase));
+        CU(launch_orth1(g, phase));
+        CU(launch_orth2(g, phase));
+    }
+    return MEG_OK;
+}
+
+meg_status enqueue_init_orth(const GroupLaunch& g) {
+    CU(launch_combine(g, PH_INIT));
+    CU(launch_orth1(g, PH_INIT));
+    CU(launch_orth2(g, PH_INIT));
+    return MEG_OK;
+}
+
+template <typename T>
+void to_storage(const std::vector<double>& src, std::vector<unsigned char>& out) {
+    out.resize(src.size() * sizeof(T));
+    T* p = (T*)out.data();
+    for (size_t i = 0; i < src.size(); ++i) p[i] = (T)src[i];
+}
+
+meg_status upload_T(meg_solve_s* h, void* dst, const std::vector<double>& src) {
+    std::vector<unsigned char> buf;
+    if (h->prec == MEG_FP64) to_storage<double>(src, buf);
+    else to_storage<float>(src, buf);
+    CU(cudaMemcpyAsync(dst, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));   // buf is a local
+    return MEG_OK;
+}
+
+meg_status upload_f64(meg_solve_s* h, void* dst, const std::vector<double>& src) {
+    CU(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return MEG_OK;
+}
+
+// Work of a group runs on the group's stream: order the solve's stream after it.
+meg_status join_group_stream(meg_solve_s* h) {
+    if (h->in_group && h->group_stream != h->stream) CU(cudaStreamSynchronize(h->group_stream));
+    return MEG_OK;
+}
+
+meg_status check_device_status(meg_solve_s* h) {
+    if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
+    double st = 0.0;
+    CU(cudaMemcpyAsync(&st, h->sm + SM_STATUS, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (st != 0.0) {
+        char msg[128];
+        snprintf(msg, sizeof msg, "device reported status %d (numeric breakdown in a k x k step)", (int)st);
+        return fail((meg_status)(int)st, msg);
+    }
+    return MEG_OK;
+}
+
+// f(X_t) by the accurate pass; also refreshes the shift bounds that depend on it.
+meg_status eval_objective(meg_solve_s* h, double* f) {
+    GroupLaunch g = solo_launch(h);
+    CU(launch_objective(g, h->d_f));
+    double v = 0.0;
+    CU(cudaMemcpyAsync(&v, h->d_f, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    *f = v;
+    return MEG_OK;
+}
+
+meg_status refresh_bounds(meg_solve_s* h) {
+    if (!h->has_obj || !h->has_x) return MEG_OK;
+    if (h->obj.kind == MEG_CSR_QUAD) {
+        // one CSR gradient pass at X_t leaves max_i sum_j |R_ij| in the state
+        CU(launch_csr(solo_launch(h)));
+        CU(cudaStreamSynchronize(h->stream));
+        return MEG_OK;
+    }
+    if (h->obj.kind != MEG_DENSE_QUAD) return MEG_OK;
+    double f = 0.0;
+    meg_status st = eval_objective(h, &f);
+    if (st != MEG_OK) return st;
+    double vals[1];
+    int slot;
+    vals[0] = 1.25 * std::sqrt(std::max(2.0 * f, 0.0));
+    slot = SM_GNORM;
+    CU(cudaMemcpyAsync(h->sm + slot, vals, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return MEG_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* meg_last_error(void) { return g_last_error.c_str(); }
+
+int64_t meg_footprint(int n, int r, int p, int precision, int kind) {
+    if (n <= 0 || r <= 0 || p <= 0) return -1;
+    const int64_t k = r + p;
+    const int64_t ts = precision == MEG_FP64 ? 8 : 4;
+    const int64_t nb_red = (n + ROWS_RED - 1) / ROWS_RED;
+    const int64_t groups = (nb_red + RED_GROUP - 1) / RED_GROUP;
+    int64_t b = 0;
+    b += ts * (int64_t)n * (2 * r + 4 * k);
+    if (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR) b += ts * (int64_t)dense_splits(n) * n * k;
+    b += 4 * (nb_red + groups) * 2 * RED_MAX_ENTRIES;
+    b += 4 * (groups + 3) + 8 * SM_TOTAL + 8;
+    return b;
+}
+
+meg_status meg_create(const meg_options* opt, const double* V0, const double* lam0, meg_handle* out) {
+    if (!opt || !out) return fail(MEG_ERR_INVALID_ARG, "meg_create: null argument");
+    *out = nullptr;
+    const int n = opt->n, r = opt->r, p = opt->p, q = opt->q;
+    if (n < 2 || r < 1 || r > MEG_RMAX || r > n - 1)
+        return fail(MEG_ERR_INVALID_ARG, "meg_create: need 1 <= r <= min(n - 1, 30)");
+    if (p < 1 || r + p > MEG_KMAX || r + p > n)
+        return fail(MEG_ERR_INVALID_ARG, "meg_create: need p >= 1 and r + p <= min(n, 32)");
+    if (q < 1 || q > 8) return fail(MEG_ERR_INVALID_ARG, "meg_create: need 1 <= q <= 8");
+    if (opt->precision < MEG_FP64 || opt->precision > MEG_MIXED_BF16)
+        return fail(MEG_ERR_INVALID_ARG, "meg_create: unknown precision");
+    if (!(opt->eta > 0.0) || !std::isfinite(opt->eta)) return fail(MEG_ERR_INVALID_ARG, "meg_create: eta must be > 0");
+    if (!(opt->eps_a > 0.0) || !(opt->eps_c >= 0.0) || !(opt->eps_pow >= 0.0))
+        return fail(MEG_ERR_INVALID_ARG, "meg_create: eps schedule parameters");
+    const double eps0 = opt->eps_a / std::pow(opt->eps_c + 1.0, opt->eps_pow);
+    if (!(eps0 > 0.0 && eps0 <= 0.75))
+        return fail(MEG_ERR_INVALID_ARG, "meg_create: eps_t must lie in (0, 3/4] (Lemma 2)");
+    if ((V0 == nullptr) != (lam0 == nullptr))
+        return fail(MEG_ERR_INVALID_ARG, "meg_create: give both V0 and lam0 or neither");
+    if (lam0) {
+        double sum = 0.0;
+        for (int i = 0; i < r; ++i) {
+            if (!(lam0[i] >= 0.0)) return fail(MEG_ERR_INVALID_ARG, "meg_create: lam0 must be >= 0");
+            sum += lam0[i];
+        }
+        if (std::fabs(sum - 1.0) > 1e-9) return fail(MEG_ERR_INVALID_ARG, "meg_create: lam0 must sum to 1");
+    }
+    if (cudaError_t e = ensure_attributes(); e != cudaSuccess)
+        return fail(MEG_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+
+    meg_solve_s* h = new meg_solve_s();
+    h->opt = *opt;
+    h->n = n; h->r = r; h->k = r + p; h->q = q; h->prec = opt->precision;
+    h->stream = (cudaStream_t)opt->stream;
+    if (!h->stream) {
+        // CUDA graphs cannot be captured on the legacy default stream: use a
+        // blocking stream of our own, which stays ordered with the legacy stream.
+        if (cudaStreamCreate(&h->stream) != cudaSuccess) {
+            delete h;
+            return fail(MEG_ERR_CUDA, "meg_create: stream creation failed");
+        }
+        h->own_stream = true;
+    }
+    SolveDev& d = h->desc;
+    d.n = n; d.r = r; d.k = h->k; d.kind = -1; d.prec = h->prec; d.q = q; d.mode = 0;
+    d.eta = opt->eta; d.eps_a = opt->eps_a; d.eps_c = opt->eps_c; d.eps_pow = opt->eps_pow; d.seed = opt->seed;
+    compute_partition(h, d);
+    const size_t ts = tsize(h->prec);
+    const int k = h->k;
+    const int groups = (d.nb_red + RED_GROUP - 1) / RED_GROUP;
+    auto alloc = [&](void** ptr, size_t bytes) -> bool {
+        return cudaMalloc(ptr, std::max<size_t>(bytes, 16)) == cudaSuccess;
+    };
+    bool ok = alloc(&h->V, 8 * n * r) && alloc(&h->Vn, 8 * n * r) && alloc(&h->W, ts * n * k) &&
+              alloc(&h->Wp, ts * n * k) && alloc(&h->Z, ts * n * k) && alloc(&h->Y, ts * n * k) &&
+              alloc((void**)&h->part, sizeof(float) * (d.nb_red + groups) * 2 * RED_MAX_ENTRIES) &&
+              alloc((void**)&h->ctr, sizeof(unsigned) * (groups + 3)) &&
+              alloc((void**)&h->sm, sizeof(double) * SM_TOTAL) && alloc((void**)&h->d_f, sizeof(double)) &&
+              alloc((void**)&h->d_desc, sizeof(SolveDev));
+    if (!ok) {
+        cudaGetLastError();
+        meg_destroy(h);
+        return fail(MEG_ERR_OOM, "meg_create: device allocation failed");
+    }
+    d.V = (double*)h->V; d.Vn = (double*)h->Vn; d.W = h->W; d.Wp = h->Wp; d.Z = h->Z; d.Y = h->Y; d.Ys = nullptr;
+    d.part = h->part; d.ctr = h->ctr; d.sm = h->sm; d.meas = nullptr; d.bidx = nullptr;
+    meg_status st;
+    std::vector<double> smh(SM_TOTAL, 0.0);
+    smh[SM_T] = 1.0;
+    smh[SM_ETA] = opt->eta;
+    if (V0) {
+        for (int i = 0; i < r; ++i) smh[SM_MU + i] = (1.0 - eps0) * lam0[i] + eps0 / n;
+        smh[SM_S] = eps0 / n;
+    }
+    if (cudaMemsetAsync(h->ctr, 0, sizeof(unsigned) * (groups + 3), h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->V, 0, 8 * n * r, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->W, 0, ts * n * k, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->sm, smh.data(), sizeof(double) * SM_TOTAL, cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess) {
+        meg_destroy(h);
+        return fail(MEG_ERR_CUDA, "meg_create: initial copies failed");
+    }
+    if ((st = upload_desc(h, d)) != MEG_OK) { meg_destroy(h); return st; }
+    if (V0) {
+        // W_1 = [V0 | P], P Gaussian (seeded); orthonormalised on the device
+        std::vector<double> vh((size_t)n * r), wh((size_t)n * k);
+        std::mt19937_64 gen(opt->seed ^ 0x5EEDC0DEull);
+        std::normal_distribution<double> nd(0.0, 1.0);
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < r; ++j) vh[(size_t)i * r + j] = wh[(size_t)i * k + j] = V0[(size_t)i * r + j];
+            for (int j = r; j < k; ++j) wh[(size_t)i * k + j] = nd(gen);
+        }
+        if ((st = upload_f64(h, h->V, vh)) != MEG_OK || (st = upload_T(h, h->W, wh)) != MEG_OK ||
+            (st = enqueue_init_orth(solo_launch(h))) != MEG_OK) {
+            meg_destroy(h);
+            return st;
+        }
+        h->has_x = true;
+    }
+    *out = h;
+    return MEG_OK;
+}
+
+meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
+    if (!h || !o) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: null argument");
+    if (h->in_group) return fail(MEG_ERR_STATE, "meg_set_objective: solve belongs to a group");
+    SolveDev& d = h->desc;
+    const int n = h->n, k = h->k;
+    if (o->kind == MEG_DENSE_QUAD || o->kind == MEG_LINEAR) {
+        if (!o->dense) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: dense data missing");
+    } else if (o->kind == MEG_CSR_QUAD) {
+        if (!o->rowptr || !o->col || !o->val || o->nnz < 0)
+            return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: CSR arrays missing");
+        std::vector<int> rp(n + 1);
+        CU(cudaMemcpyAsync(rp.data(), o->rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        if (rp[0] != 0 || rp[n] != o->nnz)
+            return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: rowptr[0] must be 0 and rowptr[n] == nnz");
+        for (int i = 0; i < n; ++i)
+            if (rp[i + 1] < rp[i]) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: rowptr not monotone");
+    } else if (o->kind == MEG_MEAS_STOCH) {
+        if (!o->A || !o->y || o->m < 1 || o->L < 1)
+            return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: measurement arrays missing");
+        if (o->m > 0x7fffffff) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: m too large");
+    } else {
+        return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: unknown kind");
+    }
+    h->obj = *o;
+    d.kind = o->kind;
+    d.D = o->dense; d.rowptr = o->rowptr; d.col = o->col; d.val = o->val; d.nnz = o->nnz;
+    d.A = o->A; d.y = o->y; d.m = o->m; d.L = o->L;
+    const size_t ts = tsize(h->prec);
+    if ((o->kind == MEG_DENSE_QUAD || o->kind == MEG_LINEAR) && !h->Ys) {
+        if (cudaMalloc(&h->Ys, ts * (size_t)d.nb_ds * n * k) != cudaSuccess)
+            return fail(MEG_ERR_OOM, "meg_set_objective: dense partials");
+    }
+    d.Ys = h->Ys;
+    if (o->kind == MEG_MEAS_STOCH || o->kind == MEG_CSR_QUAD) {
+        size_t cnt = o->kind == MEG_MEAS_STOCH ? (size_t)std::max<int64_t>(o->m, o->L) * (2 + MEG_KMAX)
+                                               : (size_t)d.nb_csr;
+        if (h->meas) cudaFree(h->meas);
+        if (h->bidx) cudaFree(h->bidx);
+        h->meas = nullptr; h->bidx = nullptr;
+        if (cudaMalloc((void**)&h->meas, sizeof(double) * cnt) != cudaSuccess ||
+            cudaMalloc((void**)&h->bidx, sizeof(int) * std::max(1, o->L)) != cudaSuccess)
+            return fail(MEG_ERR_OOM, "meg_set_objective: scratch");
+    }
+    d.meas = h->meas; d.bidx = h->bidx;
+    d.nb_meas = o->kind == MEG_MEAS_STOCH ? o->L : 0;
+    meg_status st = upload_desc(h, d);
+    if (st != MEG_OK) return st;
+    // statistics of the data used by the objective estimate and the shift: Tr D, ||D||_F^2
+    // (computed by the objective kernel on X = 0 and X = I/n would need two passes;
+    //  the k_objective pass on a zero iterate gives 1/2 ||D||^2 directly)
+    if (o->kind == MEG_DENSE_QUAD || o->kind == MEG_LINEAR || o->kind == MEG_CSR_QUAD) {
+        // evaluate with mu = s = 0 (X = 0): dense quadratic -> 1/2||D||^2, CSR -> 1/2 sum val^2
+        std::vector<double> smh(SM_TOTAL);
+        CU(cudaMemcpyAsync(smh.data(), h->sm, sizeof(double) * SM_TOTAL, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        std::vector<double> z = smh;
+        for (int i = 0; i < h->r; ++i) z[SM_MU + i] = 0.0;
+        z[SM_S] = 0.0;
+        SolveDev dq = d;
+        if (o->kind == MEG_LINEAR) dq.kind = MEG_DENSE_QUAD;      // same pass, sum of squares
+        CU(cudaMemcpyAsync(h->sm, z.data(), sizeof(double) * SM_TOTAL, cudaMemcpyHostToDevice, h->stream));
+        if ((st = upload_desc(h, dq)) != MEG_OK) return st;
+        double half_sq = 0.0;
+        if ((st = eval_objective(h, &half_sq)) != MEG_OK) return st;
+        // X = I/n: <X, D> = Tr D / n for the linear form
+        double trd = 0.0;
+        if (o->kind != MEG_CSR_QUAD) {
+            SolveDev dl = d;
+            dl.kind = MEG_LINEAR;
+            for (int i = 0; i < h->r; ++i) z[SM_MU + i] = 1.0 / n;   // X = I / n
+            z[SM_S] = 1.0 / n;
+            CU(cudaMemcpyAsync(h->sm, z.data(), sizeof(double) * SM_TOTAL, cudaMemcpyHostToDevice, h->stream));
+            if ((st = upload_desc(h, dl)) != MEG_OK) return st;
+            double v = 0.0;
+            if ((st = eval_objective(h, &v)) != MEG_OK) return st;
+            trd = v * n;
+        }
+        smh[SM_FROD2] = 2.0 * half_sq;
+        smh[SM_TRD] = trd;
+        CU(cudaMemcpyAsync(h->sm, smh.data(), sizeof(double) * SM_TOTAL, cudaMemcpyHostToDevice, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        if ((st = upload_desc(h, d)) != MEG_OK) return st;
+    }
+    h->has_obj = true;
+    if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    return refresh_bounds(h);
+}
+
+meg_status meg_warm_start(meg_handle h, int products) {
+    if (!h) return fail(MEG_ERR_INVALID_ARG, "meg_warm_start: null handle");
+    if (!h->has_obj) return fail(MEG_ERR_STATE, "meg_warm_start: objective not set");
+    if (products < 1) return fail(MEG_ERR_INVALID_ARG, "meg_warm_start: products >= 1");
+    if (h->in_group) return fail(MEG_ERR_STATE, "meg_warm_start: solve belongs to a group");
+    const int n = h->n, r = h->r, k = h->k;
+    meg_status st;
+    std::vector<double> vh((size_t)n * r), wh((size_t)n * k);
+    std::mt19937_64 gen(h->opt.seed ^ 0xA11CE5ull);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < k; ++j) {
+            double v = nd(gen);
+            wh[(size_t)i * k + j] = v;
+            if (j < r) vh[(size_t)i * r + j] = v;
+        }
+    if ((st = upload_f64(h, h->V, vh)) != MEG_OK || (st = upload_T(h, h->W, wh)) != MEG_OK) return st;
+    SolveDev dw = h->desc;
+    dw.mode = 1;
+    if (dw.kind == MEG_MEAS_STOCH) dw.nb_meas = (int)dw.m;
+    CU(cudaMemcpyAsync(h->d_desc, &dw, sizeof(SolveDev), cudaMemcpyHostToDevice, h->stream));
+    GroupLaunch g{};
+    g.d_solves = h->d_desc;
+    g.ns = 1;
+    for (int p = 0; p < PK_COUNT; ++p) g.blocks[p] = blocks_of(dw, p);
+    g.prec = h->prec;
+    g.stream = h->stream;
+    if ((st = enqueue_init_orth(g)) != MEG_OK) return st;
+    if (dw.kind == MEG_CSR_QUAD) CU(launch_csr(g));   // bound max_i sum_j |M_ij| for the shift
+    const bool dense = dw.kind == MEG_DENSE_QUAD || dw.kind == MEG_LINEAR;
+    for (int j = 0; j < products; ++j) {
+        const int phase = (j == products - 1) ? PH_FINAL : PH_ADVANCE;
+        if (dw.kind == MEG_MEAS_STOCH) CU(launch_meas_batch(g));
+        if (j == 0) CU(launch_begin(g));
+        if (dense) CU(launch_dense(g));
+        if (dw.kind == MEG_CSR_QUAD) CU(launch_csr(g));
+        if (dw.kind == MEG_MEAS_STOCH) CU(launch_meas_apply(g));
+        CU(launch_combine(g, phase));
+        CU(launch_orth1(g, phase));
+        CU(launch_orth2(g, phase));
+    }
+    if ((st = upload_desc(h, h->desc)) != MEG_OK) return st;
+    CU(cudaStreamSynchronize(h->stream));
+    h->has_x = true;
+    if ((st = check_device_status(h)) != MEG_OK) return st;
+    return refresh_bounds(h);
+}
+
+static meg_status ready(meg_handle h, const char* who) {
+    if (!h) return fail(MEG_ERR_INVALID_ARG, std::string(who) + ": null handle");
+    if (!h->has_obj || !h->has_x) return fail(MEG_ERR_STATE, std::string(who) + ": objective or X_1 not set");
+    return MEG_OK;
+}
+
+meg_status meg_step(meg_handle h, int nsteps) {
+    meg_status st = ready(h, "meg_step");
+    if (st != MEG_OK) return st;
+    if (h->in_group) return fail(MEG_ERR_STATE, "meg_step: solve belongs to a group");
+    if (nsteps < 0) return fail(MEG_ERR_INVALID_ARG, "meg_step: nsteps < 0");
+    if (!h->gexec) {
+        cudaGraph_t graph;
+        CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        const int kind = h->desc.kind;
+        st = enqueue_iteration(solo_launch(h), kind == MEG_DENSE_QUAD || kind == MEG_LINEAR,
+                               kind == MEG_CSR_QUAD, kind == MEG_MEAS_STOCH, h->q);
+        cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+        if (st != MEG_OK) return st;
+        if (ce != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    }
+    for (int i = 0; i < nsteps; ++i) CU(cudaGraphLaunch(h->gexec, h->stream));
+    return MEG_OK;
+}
+
+meg_status meg_set_fstar(meg_handle h, double fstar) {
+    if (!h) return fail(MEG_ERR_INVALID_ARG, "meg_set_fstar: null handle");
+    h->fstar = fstar;
+    return MEG_OK;
+}
+
+meg_status meg_objective(meg_handle h, double* f) {
+    meg_status st = ready(h, "meg_objective");
+    if (st != MEG_OK) return st;
+    if (!f) return fail(MEG_ERR_INVALID_ARG, "meg_objective: null output");
+    if ((st = check_device_status(h)) != MEG_OK) return st;
+    return eval_objective(h, f);
+}
+
+meg_status meg_solve(meg_handle h, double tol, int max_iters, int* iters_out) {
+    meg_status st = ready(h, "meg_solve");
+    if (st != MEG_OK) return st;
+    if (iters_out) *iters_out = 0;
+    double f1 = 0.0;
+    if ((st = meg_objective(h, &f1)) != MEG_OK) return st;
+    const double denom = f1 - h->fstar;
+    int done = 0;
+    while (done < max_iters) {
+        int chunk = std::min(10, max_iters - done);
+        if ((st = meg_step(h, chunk)) != MEG_OK) return st;
+        done += chunk;
+        double f = 0.0;
+        if ((st = meg_objective(h, &f)) != MEG_OK) return st;
+        if (iters_out) *iters_out = done;
+        if (!(denom > 0.0) || (f - h->fstar) <= tol * denom) return MEG_OK;
+    }
+    return fail(MEG_ERR_NOT_CONVERGED, "meg_solve: max_iters reached");
+}
+
+meg_status meg_certificate(meg_handle h, double* C_t, int* holds, int* first_hold_iter) {
+    meg_status st = ready(h, "meg_certificate");
+    if (st != MEG_OK) return st;
+    if ((st = check_device_status(h)) != MEG_OK) return st;
+    double v[SM_LAST_T + 1];
+    CU(cudaMemcpyAsync(v, h->sm, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (C_t) *C_t = v[SM_CERT];
+    if (holds) *holds = (int)v[SM_HOLDS];
+    if (first_hold_iter) *first_hold_iter = (int)v[SM_FIRST_HOLD];
+    return MEG_OK;
+}
+
+meg_status meg_get_ritz(meg_handle h, double* sigma, int* t) {
+    meg_status st = ready(h, "meg_get_ritz");
+    if (st != MEG_OK) return st;
+    if ((st = join_group_stream(h)) != MEG_OK) return st;
+    std::vector<double> v(SM_SIGMA + MEG_KMAX);
+    CU(cudaMemcpyAsync(v.data(), h->sm, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (sigma) for (int i = 0; i < h->k; ++i) sigma[i] = v[SM_SIGMA + i];
+    if (t) *t = (int)v[SM_LAST_T];
+    return check_device_status(h);
+}
+
+meg_status meg_get_iterate(meg_handle h, double* V, double* mu, double* s) {
+    if (!h) return fail(MEG_ERR_INVALID_ARG, "meg_get_iterate: null handle");
+    if (!h->has_x) return fail(MEG_ERR_STATE, "meg_get_iterate: X_1 not set");
+    if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
+    const int n = h->n, r = h->r;
+    std::vector<double> smh(SM_MU + MEG_KMAX);
+    CU(cudaMemcpyAsync(smh.data(), h->sm, sizeof(double) * smh.size(), cudaMemcpyDeviceToHost, h->stream));
+    if (V) CU(cudaMemcpyAsync(V, h->V, sizeof(double) * n * r, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (mu) for (int i = 0; i < r; ++i) mu[i] = smh[SM_MU + i];
+    if (s) *s = smh[SM_S];
+    return check_device_status(h);
+}
+
+// ---------------------------------------------------------------------------- checkpoint
+namespace {
+constexpr int64_t STATE_MAGIC = 0x4D45475354415445LL;   // "MEGSTATE"
+constexpr int STATE_HDR = 8;
+}
+
+int64_t meg_state_size(meg_handle h) {
+    if (!h) return -1;
+    return 8 * (STATE_HDR + (int64_t)SM_TOTAL + (int64_t)h->n * h->r) + (int64_t)tsize(h->prec) * h->n * h->k;
+}
+
+meg_status meg_get_state(meg_handle h, void* buf, int64_t bytes) {
+    if (!h || !buf) return fail(MEG_ERR_INVALID_ARG, "meg_get_state: null argument");
+    if (bytes < meg_state_size(h)) return fail(MEG_ERR_INVALID_ARG, "meg_get_state: buffer too small");
+    if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
+    int64_t* hdr = (int64_t*)buf;
+    hdr[0] = STATE_MAGIC; hdr[1] = h->n; hdr[2] = h->r; hdr[3] = h->k; hdr[4] = h->prec;
+    hdr[5] = h->desc.kind; hdr[6] = h->has_x; hdr[7] = 0;
+    char* p = (char*)buf + 8 * STATE_HDR;
+    CU(cudaMemcpyAsync(p, h->sm, 8 * SM_TOTAL, cudaMemcpyDeviceToHost, h->stream));
+    p += 8 * SM_TOTAL;
+    CU(cudaMemcpyAsync(p, h->V, 8 * (size_t)h->n * h->r, cudaMemcpyDeviceToHost, h->stream));
+    p += 8 * (size_t)h->n * h->r;
+    CU(cudaMemcpyAsync(p, h->W, tsize(h->prec) * (size_t)h->n * h->k, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return MEG_OK;
+}
+
+meg_status meg_set_state(meg_handle h, const void* buf, int64_t bytes) {
+    if (!h || !buf) return fail(MEG_ERR_INVALID_ARG, "meg_set_state: null argument");
+    if (bytes < meg_state_size(h)) return fail(MEG_ERR_INVALID_ARG, "meg_set_state: buffer too small");
+    const int64_t* hdr = (const int64_t*)buf;
+    if (hdr[0] != STATE_MAGIC || hdr[1] != h->n || hdr[2] != h->r || hdr[3] != h->k || hdr[4] != h->prec)
+        return fail(MEG_ERR_INVALID_ARG, "meg_set_state: state of a different solve shape or precision");
+    if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
+    const char* p = (const char*)buf + 8 * STATE_HDR;
+    CU(cudaMemcpyAsync(h->sm, p, 8 * SM_TOTAL, cudaMemcpyHostToDevice, h->stream));
+    p += 8 * SM_TOTAL;
+    CU(cudaMemcpyAsync(h->V, p, 8 * (size_t)h->n * h->r, cudaMemcpyHostToDevice, h->stream));
+    p += 8 * (size_t)h->n * h->r;
+    CU(cudaMemcpyAsync(h->W, p, tsize(h->prec) * (size_t)h->n * h->k, cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    h->has_x = hdr[6] != 0;
+    return MEG_OK;
+}
+
+meg_status meg_destroy(meg_handle h) {
+    if (!h) return MEG_OK;
+    cudaStreamSynchronize(h->stream);
+    if (h->in_group) cudaStreamSynchronize(h->group_stream);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    void* bufs[] = {h->V, h->Vn, h->W, h->Wp, h->Z, h->Y, h->Ys, h->part, h->ctr,
+                    h->sm, h->meas, h->bidx, h->d_f, h->d_desc};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return MEG_OK;
+}
+
+// ---------------------------------------------------------------------------- groups
+meg_status meg_group_create(const meg_handle* solves, int count, void* stream, meg_group* out) {
+    if (!solves || count < 1 || !out) return fail(MEG_ERR_INVALID_ARG, "meg_group_create: arguments");
+    *out = nullptr;
+    const int prec = solves[0]->prec, q = solves[0]->q;
+    for (int i = 0; i < count; ++i) {
+        meg_solve_s* h = solves[i];
+        if (!h || !h->has_obj || !h->has_x) return fail(MEG_ERR_STATE, "meg_group_create: solve not ready");
+        if (h->in_group) return fail(MEG_ERR_STATE, "meg_group_create: solve already in a group");
+        if (h->prec != prec || h->q != q)
+            return fail(MEG_ERR_INVALID_ARG, "meg_group_create: solves must share precision and q");
+    }
+    meg_group_s* g = new meg_group_s();
+    g->stream = (cudaStream_t)stream;
+    if (!g->stream) {
+        if (cudaStreamCreate(&g->stream) != cudaSuccess) {
+            delete g;
+            return fail(MEG_ERR_CUDA, "meg_group_create: stream creation failed");
+        }
+        g->own_stream = true;
+    }
+    g->q = q;
+    std::vector<SolveDev> descs(count);
+    int tot[PK_COUNT] = {0, 0, 0, 0};
+    for (int i = 0; i < count; ++i) {
+        meg_solve_s* h = solves[i];
+        g->solves.push_back(h);
+        descs[i] = h->desc;
+        for (int p = 0; p < PK_COUNT; ++p) {
+            descs[i].off[p] = tot[p];
+            tot[p] += blocks_of(h->desc, p);
+        }
+        const int kind = h->desc.kind;
+        g->has_dense |= (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR);
+        g->has_csr |= kind == MEG_CSR_QUAD;
+        g->has_meas |= kind == MEG_MEAS_STOCH;
+    }
+    if (cudaMalloc((void**)&g->d_desc, sizeof(SolveDev) * count) != cudaSuccess) {
+        if (g->own_stream) cudaStreamDestroy(g->stream);
+        delete g;
+        return fail(MEG_ERR_OOM, "meg_group_create: descriptors");
+    }
+    for (auto* h : g->solves) cudaStreamSynchronize(h->stream);
+    if (cudaMemcpy(g->d_desc, descs.data(), sizeof(SolveDev) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(g->d_desc);
+        if (g->own_stream) cudaStreamDestroy(g->stream);
+        delete g;
+        return fail(MEG_ERR_CUDA, "meg_group_create: descriptor copy");
+    }
+    g->gl.d_solves = g->d_desc;
+    g->gl.ns = count;
+    for (int p = 0; p < PK_COUNT; ++p) g->gl.blocks[p] = tot[p];
+    g->gl.prec = prec;
+    g->gl.stream = g->stream;
+    for (auto* h : g->solves) { h->in_group = true; h->group_stream = g->stream; }
+    *out = g;
+    return MEG_OK;
+}
+
+meg_status meg_group_step(meg_group g, int nsteps) {
+    if (!g) return fail(MEG_ERR_INVALID_ARG, "meg_group_step: null group");
+    if (!g->gexec) {
+        cudaGraph_t graph;
+        CU(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+        meg_status st = enqueue_iteration(g->gl, g->has_dense, g->has_csr, g->has_meas, g->q);
+        cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+        if (st != MEG_OK) return st;
+        if (ce != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&g->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    }
+    for (int i = 0; i < nsteps; ++i) CU(cudaGraphLaunch(g->gexec, g->stream));
+    return MEG_OK;
+}
+
+meg_status meg_group_destroy(meg_group g) {
+    if (!g) return MEG_OK;
+    cudaStreamSynchronize(g->stream);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
+    if (g->d_desc) cudaFree(g->d_desc);
+    for (auto* h : g->solves) { h->in_group = false; h->group_stream = nullptr; }
+    if (g->own_stream) cudaStreamDestroy(g->stream);
+    delete g;
+    return MEG_OK;
+}
+
+}  // extern "C"

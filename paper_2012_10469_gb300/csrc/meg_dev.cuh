@@ -1,0 +1,215 @@
+// Device-side structures and helpers of the low-rank MEG library.
+//
+// One "solve" is one instance of Algorithm 2 (Garber & Kaplan).  Kernels are
+// grouped: a launch covers every solve of a group, each block finds its solve
+// from per-solve block offsets.  Storage type T of the n x k blocks is double
+// (MEG_FP64) or float (MEG_FP32, MEG_MIXED_BF16).  The k x k "island" (Gram
+// matrices, Cholesky factors, Rayleigh-Ritz matrix, Ritz values, log-sum-exp,
+// certificate) is float64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/meg.h"
+
+#define MEG_KMAX 32
+#define MEG_RMAX 30
+#define MEG_LDK 33              // leading dimension of k x k matrices in shared memory
+
+// ---------------------------------------------------------------------------
+// Small float64 state of a solve: scalars followed by k x k blocks (ld 32).
+enum SmallSlot : int {
+    SM_T = 0,          // index t of the next iteration (X_t is the current iterate)
+    SM_EPS,            // eps_t of the iteration in progress
+    SM_S,              // s of X_t (spectrum value off span V)
+    SM_LOGS,           // log s
+    SM_SHIFT,          // c: the subspace iteration runs on M_t - c I
+    SM_C0,             // identity coefficient of M_t (without the shift)
+    SM_ALPHA,          // coefficient of the gradient product Y in M_t W
+    SM_GNORM,          // bound on ||grad f(X_t)||_2 used for the shift
+    SM_FEST,           // objective estimate (DENSE_QUAD, LINEAR)
+    SM_CERT,           // certificate of the last iteration
+    SM_HOLDS,          // 1 if it held
+    SM_FIRST_HOLD,     // first iteration at which it held (0 = never)
+    SM_STATUS,         // MEG_OK or an error code set on the device
+    SM_TRD,            // Tr D of the dense objective data
+    SM_FROD2,          // ||D||_F^2
+    SM_LAST_T,         // t of the iteration that produced the stored Ritz values
+    SM_LSE,            // log-sum-exp of sigma_1..r of the last iteration
+    SM_RSS,            // CSR: max_i sum_j |R_ij| of the last gradient pass (bounds ||grad f||_2)
+    SM_RESID_BOUND,    // MEAS: spectral estimate of the minibatch gradient (see k_meas_batch)
+    SM_ETA,            // eta
+    SM_MU = 32,        // [32] mu of X_t
+    SM_DCOEF = 64,     // [32] coefficients of V diag(.) V^T in M_t
+    SM_SIGMA = 96,     // [32] Ritz values of the last Rayleigh-Ritz, unshifted
+    SM_U = 128,        // V^T W       (r x k)
+    SM_G = SM_U + 1024,     // W^T W  (k x k)
+    SM_P = SM_G + 1024,     // W^T Y  (k x k)
+    SM_S1 = SM_P + 1024,    // Z^T Z  (k x k)
+    SM_M1 = SM_S1 + 1024,   // first CholQR right factor (k x k), W' = Z M1
+    SM_M2 = SM_M1 + 1024,   // second CholQR right factor, W = W' M2
+    SM_QV = SM_M2 + 1024,   // rotation to the Ritz vectors: V_{t+1} = W QV[:, :r]
+    SM_TOTAL = SM_QV + 1024
+};
+
+// Work-partition kinds (one offset table per kind in a group).
+enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_COUNT = 4 };
+
+#define RED_GROUP 16            // blocks per first-level group of a reduction
+#define RED_MAX_ENTRIES 1536    // >= k(k+1)/2 + r k for k <= 32, r <= 30 (orth2: 528 + 960)
+
+// Device descriptor of one solve.  Read-only for kernels (state lives in the
+// arrays it points to).
+struct SolveDev {
+    int n, r, k, kind, prec, q;
+    int mode;            // 0: MEG iterations, 1: warm start (operator -grad f(0))
+    int nb_red;          // blocks of the row-reduction kernels
+    int rows_red;        // rows per reduction block
+    int nb_dm, nb_ds;    // dense product: row tiles, K splits
+    int ks_len;          // K extent of one split (multiple of the K tile)
+    int nb_csr, nb_meas; // blocks of the CSR / measurement kernels
+    int off[PK_COUNT];   // first block of this solve in a grouped launch
+    double* V;           // n x r   float64 in every mode: V of X_t
+    double* Vn;          // n x r   float64: V of X_{t+1} being formed
+    void* W;             // n x k   (T)  current subspace block
+    void* Wp;            // n x k   (T)  after the first CholQR pass
+    void* Z;             // n x k   (T)  (M_t - c I) W
+    void* Y;             // n x k   (T)  gradient-part product
+    void* Ys;            // nb_ds x n x k (T) split-K partials of the dense product
+    float* part;         // reduction partials: [nb_red + groups][2 * RED_MAX_ENTRIES]
+    unsigned* ctr;       // reduction counters: [groups + 1]
+    double* sm;          // SmallSlot state
+    double* meas;        // measurement scratch: [L] residuals, [L] ||a||^2, [L x k] A_B W
+    int* bidx;           // [L] minibatch indices of the iteration in progress
+    // objective (borrowed)
+    const void* D;
+    const int* rowptr;
+    const int* col;
+    const void* val;
+    int64_t nnz;
+    const void* A;
+    const double* y;
+    int64_t m;
+    int L;
+    // schedule
+    double eta, eps_a, eps_c, eps_pow;
+    uint64_t seed;
+};
+
+// ---------------------------------------------------------------------------
+// Block -> solve lookup for grouped launches.
+__device__ __forceinline__ int find_solve(const SolveDev* sd, int ns, int kind, int b) {
+    int lo = 0, hi = ns - 1;
+    while (lo < hi) {                       // last solve with off[kind] <= b
+        int mid = (lo + hi + 1) >> 1;
+        if (sd[mid].off[kind] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Double-word (float + float) arithmetic for compensated reductions.
+// Error-free transformations: TwoSum (Knuth), TwoProduct via FMA; the
+// accumulation is Ogita, Rump & Oishi's Dot2 ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005).  __fadd_rn/__fmul_rn keep the
+// compiler from contracting the transformations into FMAs.
+struct dw { float hi, lo; };
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// acc += x * y (Dot2 step)
+__device__ __forceinline__ void dot2_acc(dw& acc, float x, float y) {
+    float p = __fmul_rn(x, y);
+    float pe = fmaf(x, y, -p);
+    float s, se;
+    two_sum(acc.hi, p, s, se);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(pe, se));
+}
+
+// acc += (b.hi + b.lo)
+__device__ __forceinline__ void dw_add(dw& acc, dw b) {
+    float s, e;
+    two_sum(acc.hi, b.hi, s, e);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, b.lo));
+}
+
+__device__ __forceinline__ double dw_value(dw a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ dw dw_from_double(double v) {
+    dw r;
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+}
+
+// Accumulator type per storage type: float64 sums for double storage,
+// double-word sums for float storage.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+    double v;
+    __device__ __forceinline__ void zero() { v = 0.0; }
+    __device__ __forceinline__ void add_prod(double x, double y) { v = fma(x, y, v); }
+    __device__ __forceinline__ dw as_dw() const { return dw_from_double(v); }
+};
+template <> struct Acc<float> {
+    dw v;
+    __device__ __forceinline__ void zero() { v.hi = 0.f; v.lo = 0.f; }
+    __device__ __forceinline__ void add_prod(float x, float y) { dot2_acc(v, x, y); }
+    __device__ __forceinline__ dw as_dw() const { return v; }
+};
+
+// A float64 coefficient applied to T data: a plain double for T = double,
+// a (hi, lo) float pair for T = float so that x * c keeps ~48 bits of c.
+template <typename T> struct Coef;
+template <> struct Coef<double> {
+    double c;
+    __device__ __forceinline__ void set(double v) { c = v; }
+    __device__ __forceinline__ double mul(double x) const { return x * c; }
+    __device__ __forceinline__ double fma_(double x, double acc) const { return fma(x, c, acc); }
+};
+template <> struct Coef<float> {
+    float hi, lo;
+    __device__ __forceinline__ void set(double v) { hi = (float)v; lo = (float)(v - (double)hi); }
+    __device__ __forceinline__ float mul(float x) const { return fmaf(x, lo, x * hi); }
+    __device__ __forceinline__ float fma_(float x, float acc) const { return fmaf(x, hi, fmaf(x, lo, acc)); }
+};
+
+// eps_t = a / (t + c + 1)^q  (Section 7 schedule, parameters of the solve)
+__device__ __forceinline__ double eps_of(const SolveDev& s, double t) {
+    return s.eps_a / pow(t + s.eps_c + 1.0, s.eps_pow);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch wrappers (defined in the kernel translation units).
+struct GroupLaunch {
+    const SolveDev* d_solves;   // device array of descriptors
+    int ns;                     // number of solves
+    int blocks[PK_COUNT];       // total blocks per partition kind
+    int prec;                   // storage precision of the group
+    cudaStream_t stream;
+};
+
+// mode of a reduction-kernel launch within an iteration
+enum RedPhase : int {
+    PH_INIT = 0,        // orthonormalise the initial block (W <- CholQR2(W))
+    PH_ADVANCE = 1,     // a product that only advances the subspace
+    PH_FINAL = 2        // the product whose W gets the Rayleigh-Ritz step
+};
+
+cudaError_t launch_begin(const GroupLaunch& g);
+cudaError_t launch_dense(const GroupLaunch& g);
+cudaError_t launch_csr(const GroupLaunch& g);
+cudaError_t launch_meas_batch(const GroupLaunch& g);
+cudaError_t launch_meas_apply(const GroupLaunch& g);
+cudaError_t launch_combine(const GroupLaunch& g, int phase);
+cudaError_t launch_orth1(const GroupLaunch& g, int phase);
+cudaError_t launch_orth2(const GroupLaunch& g, int phase);
+cudaError_t launch_objective(const GroupLaunch& g, double* out_f);
+cudaError_t init_kernel_attributes();
