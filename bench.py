@@ -1,0 +1,407 @@
+"""Benchmark of the low-rank MEG iteration (Algorithm 2) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload (dense quadratic recipe with n = 4096, r = 10): f(X) = 1/2||X - M||_F^2
+with M = U diag(w) U^T + E, w ~ Dirichlet(1), E symmetric N(0, 1e-5^2),
+data stored in bfloat16.  One step = one MEG iteration (gradient product,
+mirror operator, subspace iteration with CholeskyQR2, Rayleigh-Ritz,
+exp-map, certificate) for a batch of B = 8 independent instances stepped
+together by grouped kernels; the batch's data (268 MB) is larger than L2,
+so no step re-reads data from L2.  value = instance-iterations per second
+over all ranks.  Under torchrun every rank runs its own batch (weak
+scaling, no data-path collective).
+
+--impl reference times the CPU float64 oracle on the same workload (a
+bounded sample of iterations, on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MEG iters/s at n=4096 and solves/s p50/p99 vs plain FP32 GPU form at 1e-6 gap"
+N, R, P, Q = 4096, 10, 6, 2
+BATCH = 8
+SEED0 = 1001
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], "measured"
+    return 6800.0, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workload
+def make_batch(batch: int, seed0: int):
+    import synth
+    return [synth.dense_quadratic(N, R, seed=seed0 + i, sigma=1e-5, storage="bf16") for i in range(batch)]
+
+
+def gpu_solves(probs, device, stream):
+    """Create the batch's solves through the C ABI; warm start on the device."""
+    import torch
+    from paper_2012_10469_gb300 import binding as B
+    solves, dense = [], []
+    for i, prob in enumerate(probs):
+        bits = torch.from_numpy(np.ascontiguousarray(prob.bits().view(np.int16))).to(device)
+        s = B.Solve(N, R, p=P, q=Q, precision=B.MEG_MIXED_BF16, eta=1.0, seed=SEED0 + i, stream=stream)
+        s.meg_set_objective(B.MEG_DENSE_QUAD, dense=bits)
+        s.meg_warm_start(300)
+        solves.append(s)
+        dense.append(bits)
+    return solves, dense
+
+
+def algorithmic_bytes_dense_product():
+    """Minimum HBM traffic of one grouped dense product Y = M W over the batch:
+    M once (n^2 bf16) + W read + Y written (n k float32 each)."""
+    k = R + P
+    return BATCH * (N * N * 2 + 2 * N * k * 4)
+
+
+# --------------------------------------------------------------------------- CPU baseline (oracle)
+def oracle_sample(seconds: float):
+    """Time the float64 oracle's low-rank MEG iterations (subspace-iteration
+    eigensolver) on one instance of the workload, for about `seconds`."""
+    import synth
+    from oracle import meg
+    prob = synth.dense_quadratic(N, R, seed=SEED0, sigma=1e-5, storage="bf16")
+    obj = meg.DenseQuadratic(prob.M)
+    # warm start from the planted factors: the sample times iterations, not the start-up
+    X = meg.init_X1(prob.U, prob.w, meg.eps_schedule(0))
+    W = None
+    iters, t0 = 0, time.perf_counter()
+    while True:
+        X, info, W = meg.lowrank_step(X, obj, iters + 1, 1.0, meg.eps_schedule(iters + 1), method="subspace",
+                                      k=R + P, W0=W)
+        iters += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or iters >= 200:
+            break
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return iters / el, cores, iters, el
+
+
+# --------------------------------------------------------------------------- plain FP32 torch form
+def torch_fp32_form(prob, device, iters: int):
+    """The same iteration with plain float32 torch ops (cuBLAS/cuSOLVER), one
+    solve at a time, no graphs, no batching: the comparator the metric names."""
+    import torch
+    M = torch.from_numpy(prob.M.astype(np.float32)).to(device)
+    k = R + P
+    g = torch.Generator(device="cpu").manual_seed(7)
+    V = torch.from_numpy(prob.U.astype(np.float32)).to(device)
+    eps0 = 0.8 / 121.0
+    mu = torch.tensor(prob.w, dtype=torch.float32, device=device) * (1 - eps0) + eps0 / N
+    s = eps0 / N
+    W, _ = torch.linalg.qr(torch.cat([V, torch.randn(N, P, generator=g).to(device)], 1))
+    torch.linalg.eigh(W.T @ W)          # load cuSOLVER before timing
+    gnorm = 0.05
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(1, iters + 1):
+        eps = 0.8 / (t + 11.0) ** 2
+        logs = math.log(s)
+        d = torch.log(mu) - logs - (mu - s)
+        c0 = logs - s
+        shift = min(logs, float(torch.log(mu).min())) - gnorm
+        for j in range(Q):
+            Z = V @ (d[:, None] * (V.T @ W)) + (c0 - shift) * W + M @ W
+            if j < Q - 1:
+                W, _ = torch.linalg.qr(Z)
+        H = W.T @ Z
+        th, Qm = torch.linalg.eigh(0.5 * (H + H.T))
+        th, Qm = th.flip(0), Qm.flip(1)
+        sig = th + shift
+        lse = torch.logsumexp(sig[:R], 0)
+        mu = (1 - eps) * torch.exp(sig[:R] - lse)
+        s = eps / (N - R)
+        V = W @ Qm[:, :R]
+        W, _ = torch.linalg.qr(Z @ Qm)
+    e1.record()
+    torch.cuda.synchronize()
+    return iters / (e0.elapsed_time(e1) / 1e3)
+
+
+# --------------------------------------------------------------------------- main
+def run_reference(args):
+    """The oracle on the workload: each step is one float64 low-rank MEG
+    iteration of one instance (subspace-iteration eigensolver), on the host
+    cores; capped at about 150 s of stepping."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+    from oracle import meg
+    prob = synth.dense_quadratic(N, R, seed=SEED0, sigma=1e-5, storage="bf16")
+    obj = meg.DenseQuadratic(prob.M)
+    X = meg.init_X1(prob.U, prob.w, meg.eps_schedule(0))
+    W = None
+    t = 0
+    for _ in range(args.warmup):
+        t += 1
+        X, _, W = meg.lowrank_step(X, obj, t, 1.0, meg.eps_schedule(t), method="subspace", k=R + P, W0=W)
+    done, t0 = 0, time.perf_counter()
+    while done < args.steps and time.perf_counter() - t0 < 150.0:
+        t += 1
+        X, _, W = meg.lowrank_step(X, obj, t, 1.0, meg.eps_schedule(t), method="subspace", k=R + P, W0=W)
+        done += 1
+    el = time.perf_counter() - t0
+    value = done / el
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": 0,
+            "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * el / done,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"dense quadratic n={N} r={R}, one instance, oracle subspace-iteration "
+                                   f"eigensolver in float64", "global_batch": 1},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{done} of {args.steps} requested iterations (150 s cap)"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    from paper_2012_10469_gb300 import binding as B
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    B.load()
+    stream = torch.cuda.Stream(device)
+    probs = make_batch(BATCH, SEED0 + 100 * rank)
+    with torch.cuda.stream(stream):
+        solves, dense = gpu_solves(probs, device, stream.cuda_stream)
+    group = B.Group(solves, stream=stream.cuda_stream)
+    kps = group.meg_group_kernels_per_step()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    group.meg_group_step(max(3, args.warmup))
+    stream.synchronize()
+    # ---- timed region: K iterations of the whole batch, device-resident inputs
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("meg_timed")
+        e0.record(stream)
+        group.meg_group_step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    if ws > 1:
+        t = torch.tensor([ms], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * BATCH * args.steps / (ms / 1e3)
+
+    # ---- dominant kernel: grouped dense product, timed alone with CUDA events
+    prod_ms = group.meg_group_time_product(20)
+    hbm_peak, peak_kind = peaks()
+    alg = algorithmic_bytes_dense_product()
+    achieved = alg / (prod_ms / 1e3) / 1e9
+
+    # ---- end to end through the public API: each step uploads the batch's
+    # data from pinned host memory, runs the iteration, reads back each
+    # solve's certificate and Ritz values
+    pinned = [torch.from_numpy(np.ascontiguousarray(p.bits().view(np.int16))).pin_memory() for p in probs]
+    e2e_steps = max(3, min(args.steps, 50))
+    h2d = sum(p.numel() * 2 for p in pinned)
+    d2h = BATCH * (8 * 3 + 8 * (R + P) + 4)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            for dd, pp in zip(dense, pinned):
+                dd.copy_(pp, non_blocking=True)
+        group.meg_group_step(1)
+        for s_ in solves:
+            s_.meg_certificate()
+            s_.meg_get_ritz()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    e2e_value = ws * BATCH * e2e_steps / e2e_s
+
+    line = None
+    if rank == 0:
+        try:
+            torch_fp32_form(probs[0], device, 2)
+            fp32_form = {"value": torch_fp32_form(probs[0], device, 30), "unit": "iters/s",
+                         "what": "same iteration in plain float32 torch ops, one solve, no graphs"}
+        except Exception as ex:  # reported, never fatal
+            fp32_form = {"error": repr(ex)[:200]}
+        single = None
+        try:
+            single = single_solve_rate(probs[0], device)
+        except Exception as ex:  # reported, never fatal
+            single = {"error": repr(ex)}
+        cpu_rate, cores, it, el = oracle_sample(args.cpu_seconds)
+        line = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"dense quadratic n={N} r={R} k={R + P} q={Q}, {BATCH} independent "
+                                   f"instances per step (grouped kernels, CUDA graph), bf16 data, "
+                                   f"float32 subspace, float64 k x k island",
+                       "global_batch": ws * BATCH, "l2": "inputs larger than L2 (268 MB bf16 per rank)",
+                       "parallelism": f"replicas x{ws}"},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": kps * args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "grouped dense product k_dense (bf16 data, FFMA)",
+                         "peak_kind": f"{peak_kind} burst copy bandwidth", "ms_per_launch": prod_ms,
+                         "bytes_per_launch": alg},
+            "cpu_baseline": {"value": cpu_rate, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{it} oracle iterations (float64, subspace eigensolver) of one "
+                                       f"n={N} instance in {el:.1f} s"},
+            "fp32_torch_form": fp32_form,
+            "single_solve": single,
+        }
+    group.meg_group_destroy()
+    for s_ in solves:
+        s_.meg_destroy()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def single_solve_rate(prob, device, iters: int = 200):
+    """One instance alone (its 33.5 MB of data stays in L2): iterations/s."""
+    import torch
+    from paper_2012_10469_gb300 import binding as B
+    stream = torch.cuda.Stream(device)
+    bits = torch.from_numpy(np.ascontiguousarray(prob.bits().view(np.int16))).to(device)
+    s = B.Solve(N, R, p=P, q=Q, precision=B.MEG_MIXED_BF16, eta=1.0, seed=SEED0, stream=stream.cuda_stream)
+    s.meg_set_objective(B.MEG_DENSE_QUAD, dense=bits)
+    s.meg_warm_start(300)
+    s.meg_step(20)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.meg_step(iters)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rate = iters / (e0.elapsed_time(e1) / 1e3)
+    s.meg_destroy()
+    return {"value": rate, "unit": "iters/s", "note": "one n=4096 instance; its data fits in L2"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -208,6 +208,16 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
 meg_status meg_group_step(meg_group g, int nsteps);
 meg_status meg_group_destroy(meg_group g);
 
+/* Profiling: average device time of the group's gradient-product kernel
+ * (the dense or CSR product that dominates an iteration), from `reps`
+ * back-to-back launches between two CUDA events on the group's stream.
+ * The launches compute the product for the current W and leave the
+ * solves' iterates unchanged.  Synchronises the stream. */
+meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch);
+
+/* Number of kernels one meg_group_step iteration launches. */
+int meg_group_kernels_per_step(meg_group g);
+
 /* Device-memory footprint in bytes of one solve (library-owned buffers,
  * not the caller's objective data), for admission control. */
 int64_t meg_footprint(int n, int r, int p, int precision, int kind);

@@ -77,6 +77,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_group_step": (C.c_int, [H, C.c_int]),
         "meg_group_destroy": (C.c_int, [H]),
         "meg_footprint": (C.c_int64, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "meg_group_time_product": (C.c_int, [H, C.c_int, _P(C.c_float)]),
+        "meg_group_kernels_per_step": (C.c_int, [H]),
         "meg_state_size": (C.c_int64, [H]),
         "meg_get_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
         "meg_set_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
@@ -95,7 +97,7 @@ def exported_symbols():
     hdr = os.path.join(os.path.dirname(HERE), "include", "meg.h")
     with open(hdr) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^\s*(?:meg_status|const char\*|int64_t)\s+(meg_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:meg_status|const char\*|int64_t|int)\s+(meg_\w+)\s*\(", text, re.M)))
 
 
 def _check(status: int, what: str):
@@ -235,6 +237,14 @@ class Group:
 
     def meg_group_step(self, nsteps: int = 1):
         _check(load().meg_group_step(self.g, nsteps), "meg_group_step")
+
+    def meg_group_time_product(self, reps: int = 20) -> float:
+        ms = C.c_float()
+        _check(load().meg_group_time_product(self.g, reps, C.byref(ms)), "meg_group_time_product")
+        return ms.value
+
+    def meg_group_kernels_per_step(self) -> int:
+        return int(load().meg_group_kernels_per_step(self.g))
 
     def meg_group_destroy(self):
         if getattr(self, "g", None):

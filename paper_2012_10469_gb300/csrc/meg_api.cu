@@ -721,6 +721,36 @@ meg_status meg_group_step(meg_group g, int nsteps) {
     return MEG_OK;
 }
 
+meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch) {
+    if (!g || reps < 1 || !ms_per_launch) return fail(MEG_ERR_INVALID_ARG, "meg_group_time_product: arguments");
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    // one untimed launch, then `reps` back-to-back launches between two events
+    if (g->has_dense) CU(launch_dense(g->gl));
+    if (g->has_csr) CU(launch_csr(g->gl));
+    CU(cudaEventRecord(e0, g->stream));
+    for (int i = 0; i < reps; ++i) {
+        if (g->has_dense) CU(launch_dense(g->gl));
+        if (g->has_csr) CU(launch_csr(g->gl));
+    }
+    CU(cudaEventRecord(e1, g->stream));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms_per_launch = ms / reps;
+    return MEG_OK;
+}
+
+int meg_group_kernels_per_step(meg_group g) {
+    if (!g) return -1;
+    // per product: gradient-part kernel(s) + combine + orth1 + orth2 (+ minibatch pass); plus begin
+    const int per = (g->has_dense ? 1 : 0) + (g->has_csr ? 1 : 0) + (g->has_meas ? 2 : 0) + 3;
+    return g->q * per + 1;
+}
+
 meg_status meg_group_destroy(meg_group g) {
     if (!g) return MEG_OK;
     cudaStreamSynchronize(g->stream);
