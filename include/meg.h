@@ -218,6 +218,32 @@ meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch);
 /* Number of kernels one meg_group_step iteration launches. */
 int meg_group_kernels_per_step(meg_group g);
 
+/*
+ * meg_objective_dense_noalloc -- f(X) = 1/2 ||X - M||_F^2 for
+ * X = V diag(mu) V^T + s (I - V V^T), computed without allocating any
+ * device memory.  The paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc -- code running while a CUDA graph is captured
+ * in global or thread-local mode (allocation calls are refused there),
+ * serving loops bound to the device-memory budget they were admitted
+ * with, and hosts whose device memory is managed elsewhere.
+ *   V     : device, n x r row-major float64 (orthonormal columns)
+ *   mu    : host, r values;  s : the value of X off span V
+ *   M     : device, n x n row-major; double (MEG_FP64), float (MEG_FP32)
+ *           or bfloat16 bits (MEG_MIXED_BF16), as in meg_objective_desc
+ *   f_out : device, one double, written when the work on `stream` ends
+ * The reduction scratch is one fixed array of the library (about 35 KB
+ * per GPU that loads it, kept until the process exits), so n is limited
+ * to MEG_NOALLOC_MAX_N; larger n returns MEG_ERR_INVALID_ARG.  The first
+ * call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.
+ * Every call shares the array: calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race -- order them.
+ * The result equals meg_objective's for the same iterate and data.
+ */
+#define MEG_NOALLOC_MAX_N 65536
+meg_status meg_objective_dense_noalloc(const double* V, const double* mu, double s, int n, int r,
+                                       const void* M, int precision, double* f_out, void* stream);
+
 /* Device-memory footprint in bytes of one solve (library-owned buffers,
  * not the caller's objective data), for admission control. */
 int64_t meg_footprint(int n, int r, int p, int precision, int kind);

@@ -79,6 +79,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_footprint": (C.c_int64, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
         "meg_group_time_product": (C.c_int, [H, C.c_int, _P(C.c_float)]),
         "meg_group_kernels_per_step": (C.c_int, [H]),
+        "meg_objective_dense_noalloc": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_double, C.c_int, C.c_int,
+                                                  C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
         "meg_state_size": (C.c_int64, [H]),
         "meg_get_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
         "meg_set_state": (C.c_int, [H, C.c_void_p, C.c_int64]),

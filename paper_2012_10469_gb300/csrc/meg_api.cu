@@ -225,6 +225,10 @@ meg_status refresh_bounds(meg_solve_s* h) {
 
 }  // namespace
 
+namespace meg_internal {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}
+
 // ============================================================================
 extern "C" {
 
