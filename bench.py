@@ -340,7 +340,7 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"dense quadratic n={N} r={R} k={R + P} q={Q}, {BATCH} independent "
                                    f"instances per step (grouped kernels, CUDA graph), bf16 data, "
-                                   f"float32 subspace, float64 k x k island",
+                                   f"float32 subspace, float32 k x k island with double-word refinement",
                        "global_batch": ws * BATCH, "l2": "inputs larger than L2 (268 MB bf16 per rank)",
                        "parallelism": f"replicas x{ws}"},
             "clocks": clocks,
@@ -348,7 +348,7 @@ def run_gpu(args):
             "gpu_launches": kps * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": None,
-                         "kernel": "grouped dense product k_dense (bf16 data, FFMA)",
+                         "kernel": "grouped dense product k_dense_tc (bf16 tcgen05, TMA)",
                          "peak_kind": f"{peak_kind} burst copy bandwidth", "ms_per_launch": prod_ms,
                          "bytes_per_launch": alg},
             "cpu_baseline": {"value": cpu_rate, "unit": "iters/s", "cores": cores, "kind": "oracle",

@@ -185,6 +185,9 @@ meg_status meg_objective(meg_handle h, double* f);
  * meg_state_size gives the byte count; meg_get_state copies it to host
  * memory `buf`, meg_set_state restores it into a solve created with the
  * same n, r, p and precision (objective data are not part of the state).
+ * The buffer starts with eight int64 header words: a magic number, n, r,
+ * k, precision, objective kind, 1 if X_1 is set, and 1 if the dense
+ * product runs on the tensor cores (tcgen05) for this solve.
  * Iterating T steps, saving, restoring and iterating T more gives the
  * same bits as 2T steps.  Both calls synchronise the stream. */
 int64_t meg_state_size(meg_handle h);

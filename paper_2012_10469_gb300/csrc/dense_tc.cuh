@@ -1,0 +1,20 @@
+// Host interface of the tcgen05 dense product (dense_tc.cu).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+struct SolveDev;
+
+#define TC_NMAX 96          // 3 k padded to 16, k <= 32
+#define TC_MAXG 24          // solves per launch (tensor maps travel as kernel parameters)
+
+struct TcMaps {
+    CUtensorMap a[TC_MAXG];   // over the objective's n x n bf16 data
+    CUtensorMap b[TC_MAXG];   // over the split subspace block Wsp
+};
+
+cudaError_t tc_init();
+size_t tc_smem_bytes();
+bool tc_make_maps(const void* D, int n, const void* Wsp, int kpad, int npad, CUtensorMap* a, CUtensorMap* b);
+cudaError_t launch_dense_tc(const SolveDev* d_solves, int ns, int blocks, const TcMaps& maps, cudaStream_t st);

@@ -11,8 +11,10 @@
 //              last block: Rayleigh-Ritz on span W (final product), exp-map
 //              (Definition 2), certificate (Lemma 2), CholeskyQR factor
 //   orth1/2  : W <- CholeskyQR2(Z) (two passes), V_{t+1} = W Q_r; V^T W, W^T W
+#include <cuda_bf16.h>
 #include <math.h>
 
+#include "island_f32.cuh"
 #include "kxk.cuh"
 #include "meg_dev.cuh"
 
@@ -132,44 +134,276 @@ __global__ void k_begin(const SolveDev* sds, int ns) {
     if (si >= ns) return;
     const SolveDev& s = sds[si];
     double* sm = s.sm;
-    if (threadIdx.x != 0) return;
-    const int r = s.r;
+    const int r = s.r, lane = threadIdx.x;
     if (s.mode == 1) {
-        for (int l = 0; l < r; ++l) sm[SM_DCOEF + l] = 0.0;
-        sm[SM_C0] = 0.0;
-        sm[SM_ALPHA] = (s.kind == MEG_DENSE_QUAD) ? 1.0 : -1.0;
-        double g0;
-        if (s.kind == MEG_MEAS_STOCH) g0 = sm[SM_RESID_BOUND];
-        else if (s.kind == MEG_CSR_QUAD) g0 = sm[SM_RSS];
-        else g0 = sqrt(sm[SM_FROD2]);
-        sm[SM_SHIFT] = -1.0001 * g0 - 1e-300;
+        if (lane < r) sm[SM_DCOEF + lane] = 0.0;
+        if (lane == 0) {
+            sm[SM_C0] = 0.0;
+            sm[SM_ALPHA] = (s.kind == MEG_DENSE_QUAD) ? 1.0 : -1.0;
+            double g0;
+            if (s.kind == MEG_MEAS_STOCH) g0 = sm[SM_RESID_BOUND];
+            else if (s.kind == MEG_CSR_QUAD) g0 = sm[SM_RSS];
+            else g0 = sqrt(sm[SM_FROD2]);
+            sm[SM_SHIFT] = -1.0001 * g0 - 1e-300;
+        }
         return;
     }
     const double t = sm[SM_T];
-    const double eps = eps_of(s, t);
-    sm[SM_EPS] = eps;
     const double sv = sm[SM_S];
-    const double logs = log(sv);
-    sm[SM_LOGS] = logs;
     const double eta = s.eta;
-    double lmin = logs;
-    for (int l = 0; l < r; ++l) {
-        double mu = sm[SM_MU + l];
-        double d = log(mu) - logs;
-        lmin = fmin(lmin, log(mu));
+    // one logarithm per lane
+    const double logs = log(sv);
+    double lmu = logs;
+    if (lane < r) {
+        const double mu = sm[SM_MU + lane];
+        lmu = log(mu);
+        double d = lmu - logs;
         if (s.kind == MEG_DENSE_QUAD) d -= eta * (mu - sv);
-        sm[SM_DCOEF + l] = d;
+        sm[SM_DCOEF + lane] = d;
     }
-    sm[SM_C0] = (s.kind == MEG_DENSE_QUAD) ? logs - eta * sv : logs;
-    sm[SM_ALPHA] = (s.kind == MEG_DENSE_QUAD) ? eta : -eta;
-    double g;
-    switch (s.kind) {
-        case MEG_DENSE_QUAD: g = sm[SM_GNORM]; break;
-        case MEG_LINEAR: g = sqrt(sm[SM_FROD2]); break;
-        case MEG_CSR_QUAD: g = sm[SM_RSS]; break;
-        default: g = sm[SM_RESID_BOUND]; break;
+    double lmin = fmin(lmu, logs);
+    for (int o = 16; o > 0; o >>= 1) lmin = fmin(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+    if (lane == 0) {
+        // eps_t = a / (t + c + 1)^q; integer q by repeated multiplication
+        const double x = t + s.eps_c + 1.0;
+        double xp;
+        if (s.eps_pow == 2.0) xp = x * x;
+        else if (s.eps_pow == 1.0) xp = x;
+        else if (s.eps_pow == 3.0) xp = x * x * x;
+        else xp = pow(x, s.eps_pow);
+        sm[SM_EPS] = s.eps_a / xp;
+        sm[SM_LOGS] = logs;
+        sm[SM_C0] = (s.kind == MEG_DENSE_QUAD) ? logs - eta * sv : logs;
+        sm[SM_ALPHA] = (s.kind == MEG_DENSE_QUAD) ? eta : -eta;
+        double g;
+        switch (s.kind) {
+            case MEG_DENSE_QUAD: g = sm[SM_GNORM]; break;
+            case MEG_LINEAR: g = sqrt(sm[SM_FROD2]); break;
+            case MEG_CSR_QUAD: g = sm[SM_RSS]; break;
+            default: g = sm[SM_RESID_BOUND]; break;
+        }
+        sm[SM_SHIFT] = lmin - eta * g - 1e-12 * fabs(lmin);
     }
-    sm[SM_SHIFT] = lmin - eta * g - 1e-12 * fabs(lmin);
+}
+
+
+// ---------------------------------------------------------------------------
+// Rayleigh-Ritz for float storage (float64 results from float32 work).
+//   Ht = G^{-1/2} H G^{-1/2} = H - (E H + H E)/2 + O(E^2),  E = G - I (|E| < 1e-3,
+//        so the neglected terms are below 1e-6 |E| |H|; W is float32-orthonormal)
+//   float32 Jacobi on Ht -> Q
+//   theta_i = q_i^T Ht q_i / q_i^T q_i  with exact (Dot2) products
+//   top r vectors: q_i + sum_j q_j (q_j^T Ht q_i)/(theta_i - theta_j)  (first order;
+//        pairs closer than 100 |q_j^T Ht q_i| are left as they are),
+//        Lowdin re-orthonormalisation, map back x = (I - E/2) q
+// Scratch: F (4 float matrices), the double regions C, JB, Bm (G), H.
+// Writes sigma, mu, s, t, certificate, objective estimate, QV, M1 like the
+// float64 island.
+__device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, const double* P, double* G,
+                            double* H, double* C, double* JB, float* F, double* wv, double* pr, double* pdg,
+                            double* sig, double* mun, double shift) {
+    const int tid = threadIdx.x, nt = blockDim.x, k = s.k, r = s.r, n = s.n;
+    constexpr int FM = 32 * MEG_LDK;        // floats per float matrix
+    float* F0 = F;
+    float* F1 = F + FM;
+    float* F2 = F + 2 * FM;
+    float* F3 = F + 3 * FM;
+    float* Bh = (float*)G;                  // two float matrices in the G region
+    float* Bl = Bh + FM;
+    __shared__ int perm[MEG_KMAX];
+    __shared__ int flag2;
+    // 1. E, H in float; Ht = H - (E H + (E H)^T)/2 in float64
+    for (int e = tid; e < k * k; e += nt) {
+        const int i = e / k, j = e % k;
+        F0[i * MEG_LDK + j] = (float)(G[i * MEG_LDK + j] - (i == j ? 1.0 : 0.0));
+        F1[i * MEG_LDK + j] = (float)H[i * MEG_LDK + j];
+    }
+    __syncthreads();
+    mm_f32(F0, false, F1, F2, k, k, k);                       // T = E H
+    for (int e = tid; e < k * k; e += nt) {
+        const int i = e / k, j = e % k;
+        H[i * MEG_LDK + j] -= 0.5 * ((double)F2[i * MEG_LDK + j] + (double)F2[j * MEG_LDK + i]);
+    }
+    __syncthreads();
+    // 2. float32 Jacobi on Ht
+    for (int e = tid; e < k * k; e += nt) F1[(e / k) * MEG_LDK + e % k] = (float)H[(e / k) * MEG_LDK + e % k];
+    __syncthreads();
+    jacobi_f32(F1, F2, F3, (float*)pr, k, 16, 2e-7f);           // Q in F2
+    // 3. Ht as hi/lo floats; Tq = Ht Q exactly (Dot2), as hi/lo floats in F1/F3
+    for (int e = tid; e < k * k; e += nt) {
+        const int i = e / k, j = e % k;
+        float hi, lo;
+        dw_split(H[i * MEG_LDK + j], hi, lo);
+        Bh[i * MEG_LDK + j] = hi;
+        Bl[i * MEG_LDK + j] = lo;
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {
+        const int a = e / k, i = e % k;
+        dw acc = {0.f, 0.f};
+        for (int b = 0; b < k; ++b) {
+            const float q = F2[b * MEG_LDK + i];
+            dot2_acc(acc, Bh[a * MEG_LDK + b], q);
+            dot2_acc(acc, Bl[a * MEG_LDK + b], q);
+        }
+        F1[a * MEG_LDK + i] = acc.hi;
+        F3[a * MEG_LDK + i] = acc.lo;
+    }
+    __syncthreads();
+    // 4. Rayleigh quotients theta_i (exact products) and the descending order
+    if (tid < k) {
+        dw num = {0.f, 0.f}, den = {0.f, 0.f};
+        for (int a = 0; a < k; ++a) {
+            const float q = F2[a * MEG_LDK + tid];
+            dot2_acc(num, q, F1[a * MEG_LDK + tid]);
+            dot2_acc(num, q, F3[a * MEG_LDK + tid]);
+            dot2_acc(den, q, q);
+        }
+        wv[tid] = dw_value(num) / dw_value(den);
+    }
+    __syncthreads();
+    if (tid < k) {
+        int rank = 0;
+        const double v = wv[tid];
+        for (int j = 0; j < k; ++j) rank += (wv[j] > v) || (wv[j] == v && j < tid);
+        perm[rank] = tid;
+    }
+    __syncthreads();
+    if (tid < k) sig[tid] = wv[perm[tid]] + shift;
+    // 5. first-order correction of the top r vectors: coefficients in Bh (k x r)
+    for (int e = tid; e < k * r; e += nt) {
+        const int j = e / r, i = e % r, ci = perm[i];
+        float cf = 0.f;
+        if (j != ci) {
+            dw h = {0.f, 0.f};
+            for (int a = 0; a < k; ++a) {
+                const float q = F2[a * MEG_LDK + j];
+                dot2_acc(h, q, F1[a * MEG_LDK + ci]);
+                dot2_acc(h, q, F3[a * MEG_LDK + ci]);
+            }
+            const double hv = dw_value(h), gap = wv[ci] - wv[j];
+            if (fabs(gap) > 100.0 * fabs(hv)) cf = (float)(hv / gap);
+        }
+        Bh[j * MEG_LDK + i] = cf;
+    }
+    __syncthreads();
+    mm_f32(F2, false, Bh, Bl, k, k, r);                        // corr = Q coef  (k x r)
+    for (int e = tid; e < k * r; e += nt) {
+        const int a = e / r, i = e % r;
+        H[a * MEG_LDK + i] = (double)F2[a * MEG_LDK + perm[i]] + (double)Bl[a * MEG_LDK + i];
+    }
+    __syncthreads();
+    // 6. Lowdin: QV <- QV (I - (QV^T QV - I)/2), float64 (k r^2)
+    for (int e = tid; e < r * r; e += nt) {
+        const int i = e / r, j = e % r;
+        double g = 0.0;
+        for (int a = 0; a < k; ++a) g = fma(H[a * MEG_LDK + i], H[a * MEG_LDK + j], g);
+        C[i * MEG_LDK + j] = g - (i == j ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int e = tid; e < k * r; e += nt) {
+        const int a = e / r, i = e % r;
+        double v = H[a * MEG_LDK + i];
+        for (int j = 0; j < r; ++j) v -= 0.5 * H[a * MEG_LDK + j] * C[j * MEG_LDK + i];
+        JB[a * MEG_LDK + i] = v;
+        Bh[a * MEG_LDK + i] = (float)v;
+    }
+    __syncthreads();
+    // 7. back to the W basis: x = (I - E/2) q
+    mm_f32(F0, false, Bh, Bl, k, k, r);                        // E QV (k x r)
+    for (int e = tid; e < k * r; e += nt) {
+        const int a = e / r, i = e % r;
+        const double v = JB[a * MEG_LDK + i] - 0.5 * (double)Bl[a * MEG_LDK + i];
+        smw[SM_QV + a * 32 + i] = v;
+        Bh[a * MEG_LDK + i] = (float)v;
+    }
+    __syncthreads();
+    // 8. objective estimate v_i^T D v_i (float32 suffices: it only sets the shift bound)
+    for (int e = tid; e < k * k; e += nt) F3[(e / k) * MEG_LDK + e % k] = (float)P[(e / k) * MEG_LDK + e % k];
+    __syncthreads();
+    mm_f32(F3, false, Bh, Bl, k, k, r);                        // P QV
+    if (tid < r) {
+        float acc = 0.f;
+        for (int a = 0; a < k; ++a) acc = fmaf(Bh[a * MEG_LDK + tid], Bl[a * MEG_LDK + tid], acc);
+        pdg[tid] = acc;
+    }
+    // 9. scalars: exp-map (Definition 2), certificate (Lemma 2), objective estimate
+    if (tid < 32) {
+        const int lane = tid;
+        const double t = smw[SM_T];
+        double m = (lane <= r && lane < k) ? sig[lane] : -1e300;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const double ex = (lane <= r && lane < k) ? exp(sig[lane] - m) : 0.0;
+        double a_r = lane < r ? ex : 0.0, a_r1 = ex;
+        for (int o = 16; o > 0; o >>= 1) {
+            a_r += __shfl_xor_sync(0xffffffffu, a_r, o);
+            a_r1 += __shfl_xor_sync(0xffffffffu, a_r1, o);
+        }
+        const double lse_r = m + log(a_r), lse_r1 = m + log(a_r1);
+        if (s.mode == 1) {
+            if (lane == 0) {
+                for (int i = 0; i < r; ++i) mun[i] = sig[i];
+                simplex_project(mun, r);
+                const double eps0 = eps_of(s, 0.0);
+                for (int i = 0; i < r; ++i) smw[SM_MU + i] = (1.0 - eps0) * mun[i] + eps0 / n;
+                smw[SM_S] = eps0 / n;
+                smw[SM_T] = 1.0;
+                smw[SM_LAST_T] = 0.0;
+                smw[SM_CERT] = 0.0;
+                smw[SM_HOLDS] = 0.0;
+                smw[SM_FIRST_HOLD] = 0.0;
+            }
+        } else {
+            const double eps = smw[SM_EPS];
+            const double s_new = eps / (double)(n - r);
+            const double mu = lane < r ? (1.0 - eps) * exp(sig[lane] - lse_r) : 0.0;
+            double xd = lane < r ? (mu - s_new) * pdg[lane] : 0.0, x2 = mu * mu;
+            for (int o = 16; o > 0; o >>= 1) {
+                xd += __shfl_xor_sync(0xffffffffu, xd, o);
+                x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+            }
+            if (lane < r) smw[SM_MU + lane] = mu;
+            if (lane == 0) {
+                const double cert = log((double)(n - r)) + sig[r] - log(eps) - lse_r1;
+                const int holds = cert <= 2.0 * eps;
+                smw[SM_LSE] = lse_r;
+                smw[SM_CERT] = cert;
+                smw[SM_HOLDS] = holds;
+                if (holds && smw[SM_FIRST_HOLD] == 0.0) smw[SM_FIRST_HOLD] = t;
+                smw[SM_LAST_T] = t;
+                if (s.kind == MEG_DENSE_QUAD || s.kind == MEG_LINEAR) {
+                    xd += s_new * smw[SM_TRD];
+                    x2 += (double)(n - r) * s_new * s_new;
+                    if (s.kind == MEG_DENSE_QUAD) {
+                        const double f = 0.5 * x2 - xd + 0.5 * smw[SM_FROD2];
+                        smw[SM_FEST] = f;
+                        smw[SM_GNORM] = 1.25 * sqrt(fmax(2.0 * f, 0.0));
+                    } else {
+                        smw[SM_FEST] = xd;
+                    }
+                }
+                smw[SM_S] = s_new;
+                smw[SM_T] = t + 1.0;
+            }
+        }
+        if (lane < k) {
+            smw[SM_SIGMA + lane] = sig[lane];
+            if (!isfinite(sig[lane])) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+        }
+    }
+    __syncthreads();
+    // 10. next block: W' = Z Q L^{-T}, L = chol(Q^T S1 Q) (Ritz-ordered, float32)
+    for (int e = tid; e < k * k; e += nt) {
+        const int a = e / k, i = e % k;
+        F1[a * MEG_LDK + i] = F2[a * MEG_LDK + perm[i]];       // Q, sorted columns
+        F3[a * MEG_LDK + i] = (float)S1[a * MEG_LDK + i];
+    }
+    __syncthreads();
+    mm_f32(F3, false, F1, Bh, k, k, k);                        // S1 Q
+    mm_f32(F1, true, Bh, Bl, k, k, k);                         // Q^T S1 Q
+    if (!chol_inv_f32(Bl, F3, (float*)pr, k, &flag2) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+    mm_f32(F1, false, F3, Bh, k, k, k);                        // M1 = Q L^{-T}
+    for (int e = tid; e < k * k; e += nt) smw[SM_M1 + (e / k) * 32 + e % k] = (double)Bh[(e / k) * MEG_LDK + e % k];
 }
 
 // ==========================================================================
@@ -190,7 +424,11 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     T* sZ = sW + s.rows_red * k;
     T* sY = sZ + s.rows_red * k;
     dw* ent = (dw*)(((uintptr_t)(sY + s.rows_red * k) + 15) & ~(uintptr_t)15);
-    double* kx = (double*)(ent + 2 * 528);
+    // the k x k doubles start after the row-phase buffers, which the float island
+    // reuses as four float matrices once the reductions are unpacked
+    const uintptr_t rp_end = (uintptr_t)(ent + 2 * 528);
+    const uintptr_t f_end = (uintptr_t)smraw + 4 * 32 * MEG_LDK * sizeof(float);
+    double* kx = (double*)(((rp_end > f_end ? rp_end : f_end) + 15) & ~(uintptr_t)15);
     __shared__ Coef<T> c_id, c_al;
 
     const double* sm = s.sm;
@@ -211,6 +449,10 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     const double* V = s.V;
     T* Z = (T*)s.Z;
     const bool dense = (s.kind == MEG_DENSE_QUAD || s.kind == MEG_LINEAR);
+    __shared__ T sVt[16 * MEG_RMAX];           // this block's rows of V in storage precision
+    if (!init)
+        for (int e = tid; e < nr * r; e += NT) sVt[e] = (T)V[(size_t)(row0 + e / r) * r + e % r];
+    __syncthreads();
     for (int idx = tid; idx < nr * k; idx += NT) {
         const int i = row0 + idx / k, j = idx % k;
         const T w = W[(size_t)i * k + j];
@@ -226,7 +468,7 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
             }
             z = c_al.mul(y);
             z = c_id.fma_(w, z);
-            for (int l = 0; l < r; ++l) z = Bc[l * k + j].fma_((T)V[(size_t)i * r + l], z);
+            for (int l = 0; l < r; ++l) z = Bc[l * k + j].fma_(sVt[(idx / k) * r + l], z);
         }
         Z[(size_t)i * k + j] = z;
         sW[idx] = w;
@@ -268,11 +510,20 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     unpack_sym(ent, S1, k);
     if (!fin) {
         // W' = Z L^{-T}, L = chol(Z^T Z)
-        for (int e = tid; e < k * k; e += NT) A[(e / k) * MEG_LDK + e % k] = S1[(e / k) * MEG_LDK + e % k];
-        __syncthreads();
-        if (!kxk_chol(A, k, &flag) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
-        kxk_inv_lower_T(A, C, k);
-        store_kxk(smw + SM_M1, C, k, k);
+        if constexpr (sizeof(T) == 4) {
+            float* Af = (float*)A;
+            float* Mf = (float*)C;
+            for (int e = tid; e < k * k; e += NT) Af[(e / k) * MEG_LDK + e % k] = (float)S1[(e / k) * MEG_LDK + e % k];
+            __syncthreads();
+            if (!chol_inv_f32(Af, Mf, (float*)pr, k, &flag) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+            for (int e = tid; e < k * k; e += NT) smw[SM_M1 + (e / k) * 32 + e % k] = (double)Mf[(e / k) * MEG_LDK + e % k];
+        } else {
+            for (int e = tid; e < k * k; e += NT) A[(e / k) * MEG_LDK + e % k] = S1[(e / k) * MEG_LDK + e % k];
+            __syncthreads();
+            if (!kxk_chol(A, k, &flag) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+            kxk_inv_lower_T(A, C, k);
+            store_kxk(smw + SM_M1, C, k, k);
+        }
         return;
     }
     // ---- Rayleigh-Ritz on span W (Section 3, three steps):
@@ -286,13 +537,34 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     load_kxk(smw + SM_U, U, r, k);
     const double d_id = smw[SM_C0] - smw[SM_SHIFT], alpha = smw[SM_ALPHA], shift = smw[SM_SHIFT];
     double* H = Qg;
+    __shared__ double dco[MEG_RMAX];
+    if (tid < r) dco[tid] = smw[SM_DCOEF + tid];
+    __syncthreads();
     for (int e = tid; e < k * k; e += NT) {
         int i = e / k, j = e % k;
         double h = d_id * G[i * MEG_LDK + j] + alpha * P[i * MEG_LDK + j];
-        for (int l = 0; l < r; ++l) h += U[l * MEG_LDK + i] * smw[SM_DCOEF + l] * U[l * MEG_LDK + j];
+        for (int l = 0; l < r; ++l) h += U[l * MEG_LDK + i] * dco[l] * U[l * MEG_LDK + j];
         H[i * MEG_LDK + j] = h;
     }
     __syncthreads();
+    __shared__ double sig[MEG_KMAX];
+    __shared__ double mun[MEG_KMAX];
+    __shared__ int use_fast;
+    if constexpr (sizeof(T) == 4) {
+        // E = G - I; W is orthonormal to float32 accuracy after CholeskyQR2
+        if (tid < 32) {
+            float em = 0.f;
+            for (int e = tid; e < k * k; e += 32)
+                em = fmaxf(em, fabsf((float)(G[(e / k) * MEG_LDK + e % k] - ((e / k == e % k) ? 1.0 : 0.0))));
+            for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
+            if (tid == 0) use_fast = em < 1e-3f;
+        }
+        __syncthreads();
+        if (use_fast) {
+            rr_fast_f32(s, smw, S1, P, G, H, C, JB, (float*)smraw, wv, pr, pdg, sig, mun, shift);
+            return;
+        }
+    }
     // G = L L^T; Ht = L^{-1} H L^{-T}
     if (!kxk_chol(G, k, &flag) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
     double* Li = U;                       // U no longer needed (H is built)
@@ -313,8 +585,6 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     __syncthreads();
 
     // Ritz values sigma_i = theta_i + c, kept in shared memory
-    __shared__ double sig[MEG_KMAX];
-    __shared__ double mun[MEG_KMAX];
     if (tid < k) {
         sig[tid] = wv[tid] + shift;
         smw[SM_SIGMA + tid] = sig[tid];
@@ -450,10 +720,20 @@ __global__ void __launch_bounds__(NT) k_orth1(const SolveDev* sds, int ns, int p
     double* A = kx;
     double* C = A + 32 * MEG_LDK;
     __shared__ int flag;
+    __shared__ float dsc[MEG_KMAX];
     unpack_sym(ent, A, k);
-    if (!kxk_chol(A, k, &flag) && tid == 0) s.sm[SM_STATUS] = MEG_ERR_NUMERIC;
-    kxk_inv_lower_T(A, C, k);
-    store_kxk(s.sm + SM_M2, C, k, k);
+    if constexpr (sizeof(T) == 4) {
+        float* Af = (float*)C;
+        float* Mf = Af + 32 * MEG_LDK;
+        for (int e = tid; e < k * k; e += NT) Af[(e / k) * MEG_LDK + e % k] = (float)A[(e / k) * MEG_LDK + e % k];
+        __syncthreads();
+        if (!chol_inv_f32(Af, Mf, dsc, k, &flag) && tid == 0) s.sm[SM_STATUS] = MEG_ERR_NUMERIC;
+        for (int e = tid; e < k * k; e += NT) s.sm[SM_M2 + (e / k) * 32 + e % k] = (double)Mf[(e / k) * MEG_LDK + e % k];
+    } else {
+        if (!kxk_chol(A, k, &flag) && tid == 0) s.sm[SM_STATUS] = MEG_ERR_NUMERIC;
+        kxk_inv_lower_T(A, C, k);
+        store_kxk(s.sm + SM_M2, C, k, k);
+    }
 }
 
 // ==========================================================================
@@ -473,6 +753,7 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
     T* sW = M2 + MEG_KMAX * MEG_KMAX;
     double* sV = (double*)(((uintptr_t)(sW + s.rows_red * k) + 7) & ~(uintptr_t)7);
     dw* ent = (dw*)(((uintptr_t)(sV + s.rows_red * r) + 15) & ~(uintptr_t)15);
+    __shared__ float sVh[16 * MEG_RMAX], sVl[16 * MEG_RMAX];
     const double* sm = s.sm;
     const bool fin = (phase == PH_FINAL);
     for (int e = tid; e < k * k; e += NT) M2[e] = (T)sm[SM_M2 + (e / k) * 32 + e % k];
@@ -487,6 +768,19 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
         for (int l = 0; l < k; ++l) acc += Wp[(size_t)i * k + l] * M2[l * k + j];
         W[(size_t)i * k + j] = acc;
         sW[idx] = acc;
+        if (s.Wsp) {
+            // exact split for the tensor-core product: W = hi + mid + lo in bf16
+            const float w = (float)acc;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const float r1 = w - __bfloat162float(hi);
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(mid);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
+            const size_t kp = (size_t)s.tc_kpad;
+            s.Wsp[(size_t)j * kp + i] = __bfloat16_as_ushort(hi);
+            s.Wsp[(size_t)(k + j) * kp + i] = __bfloat16_as_ushort(mid);
+            s.Wsp[(size_t)(2 * k + j) * kp + i] = __bfloat16_as_ushort(lo);
+        }
     }
     for (int idx = tid; idx < nr * r; idx += NT) {
         const int i = row0 + idx / r, j = idx % r;
@@ -498,6 +792,9 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
             v = V[(size_t)i * r + j];
         }
         sV[idx] = v;
+        const float vh = (float)v;
+        sVh[idx] = vh;
+        sVl[idx] = (float)(v - (double)vh);
     }
     __syncthreads();
     const int nsym = k * (k + 1) / 2;
@@ -512,13 +809,11 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
         } else {
             int l = (e - nsym) / k, j = (e - nsym) % k;
             for (int q = 0; q < nr; ++q) {
-                const double v = sV[q * r + l];
                 if constexpr (sizeof(T) == 8) {
-                    a.add_prod(v, sW[q * k + j]);
-                } else {      // V is float64: split into two floats, both products exact in Dot2
-                    const float hi = (float)v, lo = (float)(v - (double)hi);
-                    a.add_prod(hi, sW[q * k + j]);
-                    a.add_prod(lo, sW[q * k + j]);
+                    a.add_prod(sV[q * r + l], sW[q * k + j]);
+                } else {      // V is float64: two floats per entry, both products exact in Dot2
+                    a.add_prod(sVh[q * r + l], sW[q * k + j]);
+                    a.add_prod(sVl[q * r + l], sW[q * k + j]);
                 }
             }
         }
@@ -936,7 +1231,9 @@ size_t combine_smem(int prec) {
     size_t rows = 3 * 16 * MEG_KMAX * tsz;          // rows_red <= 16
     size_t ent = 2 * 528 * sizeof(dw) + 16;
     size_t kx = (6 * 32 * MEG_LDK + 32 + 96 + 32) * sizeof(double);
-    return coef + rows + ent + kx;
+    size_t rowphase = coef + rows + ent;
+    size_t fl = 4 * 32 * MEG_LDK * sizeof(float);
+    return (rowphase > fl ? rowphase : fl) + 16 + kx;
 }
 size_t orth1_smem(int prec) {
     size_t tsz = prec == MEG_FP64 ? 8 : 4;
@@ -970,6 +1267,10 @@ cudaError_t launch_begin(const GroupLaunch& g) {
 }
 
 cudaError_t launch_dense(const GroupLaunch& g) {
+    for (int c = 0; c < g.tc_chunks; ++c) {
+        cudaError_t e = launch_dense_tc(g.tc_desc[c], g.tc_ns[c], g.tc_blocks[c], *g.tc_maps[c], g.stream);
+        if (e != cudaSuccess) return e;
+    }
     if (g.blocks[PK_DENSE] == 0) return cudaSuccess;
     if (g.prec == MEG_FP64) k_dense<double, double><<<g.blocks[PK_DENSE], NT, 0, g.stream>>>(g.d_solves, g.ns);
     else if (g.prec == MEG_FP32) k_dense<float, float><<<g.blocks[PK_DENSE], NT, 0, g.stream>>>(g.d_solves, g.ns);

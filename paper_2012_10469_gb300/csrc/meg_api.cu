@@ -34,10 +34,27 @@ meg_status fail(meg_status st, const std::string& msg) {
 
 std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
+bool g_tc_ok = false;        // tcgen05 product available (driver entry point for TMA maps found)
 
 cudaError_t ensure_attributes() {
-    std::call_once(g_attr_once, [] { g_attr_err = init_kernel_attributes(); });
+    std::call_once(g_attr_once, [] {
+        g_attr_err = init_kernel_attributes();
+        g_tc_ok = (tc_init() == cudaSuccess);
+        cudaGetLastError();
+    });
     return g_attr_err;
+}
+
+int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// K splits of the tensor-core product: multiples of 64, about two CTAs per SM for one solve
+void tc_partition(SolveDev& d) {
+    d.nb_tm = (d.n + 127) / 128;
+    int s = std::max(1, (2 * 152 + d.nb_tm - 1) / d.nb_tm);
+    s = std::min(s, std::max(1, (d.n + 63) / 64));
+    const int kl = (d.n + s - 1) / s;
+    d.ks_len = round_up(kl, 64);
+    d.nb_ds = (d.n + d.ks_len - 1) / d.ks_len;
 }
 
 constexpr int ROWS_RED = 16;
@@ -60,6 +77,8 @@ struct meg_solve_s {
     cudaStream_t stream = nullptr;
     // device buffers (owned)
     void *V = nullptr, *Vn = nullptr, *W = nullptr, *Wp = nullptr, *Z = nullptr, *Y = nullptr, *Ys = nullptr;
+    void* Wsp = nullptr;                   // split W for the tensor-core product (MEG_MIXED_BF16)
+    TcMaps* solo_maps = nullptr;           // this solve's TMA maps at index 0
     float* part = nullptr;
     unsigned* ctr = nullptr;
     double* sm = nullptr;
@@ -81,6 +100,8 @@ struct meg_solve_s {
 struct meg_group_s {
     std::vector<meg_solve_s*> solves;
     SolveDev* d_desc = nullptr;
+    SolveDev* d_tc_desc = nullptr;         // descriptors of the tensor-core solves, chunk by chunk
+    std::vector<TcMaps> tc_maps;           // one per chunk (addresses stable after creation)
     GroupLaunch gl{};
     bool has_dense = false, has_csr = false, has_meas = false;
     int q = 0;
@@ -104,10 +125,12 @@ void compute_partition(meg_solve_s* h, SolveDev& d) {
 }
 
 int blocks_of(const SolveDev& d, int kind) {
+    const bool dense = (d.kind == MEG_DENSE_QUAD || d.kind == MEG_LINEAR);
     switch (kind) {
         case PK_RED: return d.nb_red;
-        case PK_DENSE: return (d.kind == MEG_DENSE_QUAD || d.kind == MEG_LINEAR) ? d.nb_dm * d.nb_ds : 0;
+        case PK_DENSE: return (dense && !d.tc) ? d.nb_dm * d.nb_ds : 0;
         case PK_CSR: return d.kind == MEG_CSR_QUAD ? d.nb_csr : 0;
+        case PK_DTC: return (dense && d.tc) ? d.nb_tm * d.nb_ds : 0;
         default: return d.kind == MEG_MEAS_STOCH ? d.nb_meas : 0;
     }
 }
@@ -119,6 +142,13 @@ GroupLaunch solo_launch(meg_solve_s* h) {
     for (int p = 0; p < PK_COUNT; ++p) g.blocks[p] = blocks_of(h->desc, p);
     g.prec = h->prec;
     g.stream = h->stream;
+    if (g.blocks[PK_DTC] > 0) {
+        g.tc_chunks = 1;
+        g.tc_desc[0] = h->d_desc;
+        g.tc_ns[0] = 1;
+        g.tc_blocks[0] = g.blocks[PK_DTC];
+        g.tc_maps[0] = h->solo_maps;
+    }
     return g;
 }
 
@@ -242,7 +272,8 @@ int64_t meg_footprint(int n, int r, int p, int precision, int kind) {
     const int64_t groups = (nb_red + RED_GROUP - 1) / RED_GROUP;
     int64_t b = 0;
     b += ts * (int64_t)n * (2 * r + 4 * k);
-    if (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR) b += ts * (int64_t)dense_splits(n) * n * k;
+    if (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR) b += ts * (int64_t)std::max(dense_splits(n), 16) * n * k;
+    if (precision == MEG_MIXED_BF16 && n % 8 == 0) b += 2 * (int64_t)((3 * k + 15) / 16 * 16) * ((n + 63) / 64 * 64);
     b += 4 * (nb_red + groups) * 2 * RED_MAX_ENTRIES;
     b += 4 * (groups + 3) + 8 * SM_TOTAL + 8;
     return b;
@@ -312,6 +343,18 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
         meg_destroy(h);
         return fail(MEG_ERR_OOM, "meg_create: device allocation failed");
     }
+    if (h->prec == MEG_MIXED_BF16 && (n % 8) == 0) {
+        d.tc_npad = round_up(3 * k, 16);
+        d.tc_kpad = round_up(n, 64);
+        const size_t wsb = (size_t)2 * d.tc_npad * d.tc_kpad;
+        h->solo_maps = new TcMaps();
+        if (cudaMalloc(&h->Wsp, wsb) != cudaSuccess || cudaMemsetAsync(h->Wsp, 0, wsb, h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            meg_destroy(h);
+            return fail(MEG_ERR_OOM, "meg_create: split block");
+        }
+    }
+    d.Wsp = (unsigned short*)h->Wsp;
     d.V = (double*)h->V; d.Vn = (double*)h->Vn; d.W = h->W; d.Wp = h->Wp; d.Z = h->Z; d.Y = h->Y; d.Ys = nullptr;
     d.part = h->part; d.ctr = h->ctr; d.sm = h->sm; d.meas = nullptr; d.bidx = nullptr;
     meg_status st;
@@ -380,7 +423,17 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     d.D = o->dense; d.rowptr = o->rowptr; d.col = o->col; d.val = o->val; d.nnz = o->nnz;
     d.A = o->A; d.y = o->y; d.m = o->m; d.L = o->L;
     const size_t ts = tsize(h->prec);
-    if ((o->kind == MEG_DENSE_QUAD || o->kind == MEG_LINEAR) && !h->Ys) {
+    const bool dense_kind = (o->kind == MEG_DENSE_QUAD || o->kind == MEG_LINEAR);
+    d.tc = 0;
+    if (dense_kind && h->Wsp && g_tc_ok &&
+        tc_make_maps(o->dense, n, h->Wsp, d.tc_kpad, d.tc_npad, &h->solo_maps->a[0], &h->solo_maps->b[0])) {
+        d.tc = 1;
+        tc_partition(d);
+    } else {
+        compute_partition(h, d);
+    }
+    if (dense_kind) {
+        if (h->Ys) { cudaFree(h->Ys); h->Ys = nullptr; }
         if (cudaMalloc(&h->Ys, ts * (size_t)d.nb_ds * n * k) != cudaSuccess)
             return fail(MEG_ERR_OOM, "meg_set_objective: dense partials");
     }
@@ -606,7 +659,7 @@ meg_status meg_get_state(meg_handle h, void* buf, int64_t bytes) {
     if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
     int64_t* hdr = (int64_t*)buf;
     hdr[0] = STATE_MAGIC; hdr[1] = h->n; hdr[2] = h->r; hdr[3] = h->k; hdr[4] = h->prec;
-    hdr[5] = h->desc.kind; hdr[6] = h->has_x; hdr[7] = 0;
+    hdr[5] = h->desc.kind; hdr[6] = h->has_x; hdr[7] = h->desc.tc;
     char* p = (char*)buf + 8 * STATE_HDR;
     CU(cudaMemcpyAsync(p, h->sm, 8 * SM_TOTAL, cudaMemcpyDeviceToHost, h->stream));
     p += 8 * SM_TOTAL;
@@ -640,11 +693,12 @@ meg_status meg_destroy(meg_handle h) {
     cudaStreamSynchronize(h->stream);
     if (h->in_group) cudaStreamSynchronize(h->group_stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    void* bufs[] = {h->V, h->Vn, h->W, h->Wp, h->Z, h->Y, h->Ys, h->part, h->ctr,
+    void* bufs[] = {h->V, h->Vn, h->W, h->Wp, h->Z, h->Y, h->Ys, h->Wsp, h->part, h->ctr,
                     h->sm, h->meas, h->bidx, h->d_f, h->d_desc};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h->solo_maps;
     delete h;
     return MEG_OK;
 }
@@ -703,6 +757,47 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
     for (int p = 0; p < PK_COUNT; ++p) g->gl.blocks[p] = tot[p];
     g->gl.prec = prec;
     g->gl.stream = g->stream;
+    // tensor-core solves: contiguous descriptor copies, chunks of at most TC_MAXG
+    std::vector<SolveDev> tcd;
+    std::vector<meg_solve_s*> tcs;
+    for (int i = 0; i < count; ++i)
+        if (blocks_of(descs[i], PK_DTC) > 0) { tcd.push_back(descs[i]); tcs.push_back(solves[i]); }
+    const int nch = ((int)tcd.size() + TC_MAXG - 1) / TC_MAXG;
+    if (nch > TC_MAX_CHUNKS) {
+        cudaFree(g->d_desc);
+        if (g->own_stream) cudaStreamDestroy(g->stream);
+        delete g;
+        return fail(MEG_ERR_INVALID_ARG, "meg_group_create: too many tensor-core solves in one group");
+    }
+    g->tc_maps.resize(nch);
+    for (int c = 0; c < nch; ++c) {
+        int off = 0;
+        const int first = c * TC_MAXG, cnt = std::min(TC_MAXG, (int)tcd.size() - first);
+        for (int j = 0; j < cnt; ++j) {
+            tcd[first + j].off[PK_DTC] = off;
+            off += blocks_of(tcd[first + j], PK_DTC);
+            g->tc_maps[c].a[j] = tcs[first + j]->solo_maps->a[0];
+            g->tc_maps[c].b[j] = tcs[first + j]->solo_maps->b[0];
+        }
+        g->gl.tc_ns[c] = cnt;
+        g->gl.tc_blocks[c] = off;
+    }
+    if (!tcd.empty()) {
+        if (cudaMalloc((void**)&g->d_tc_desc, sizeof(SolveDev) * tcd.size()) != cudaSuccess ||
+            cudaMemcpy(g->d_tc_desc, tcd.data(), sizeof(SolveDev) * tcd.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+            cudaFree(g->d_desc);
+            if (g->d_tc_desc) cudaFree(g->d_tc_desc);
+            if (g->own_stream) cudaStreamDestroy(g->stream);
+            delete g;
+            return fail(MEG_ERR_CUDA, "meg_group_create: tensor-core descriptors");
+        }
+    }
+    g->gl.tc_chunks = nch;
+    for (int c = 0; c < nch; ++c) {
+        g->gl.tc_desc[c] = g->d_tc_desc + c * TC_MAXG;
+        g->gl.tc_maps[c] = &g->tc_maps[c];
+    }
     for (auto* h : g->solves) { h->in_group = true; h->group_stream = g->stream; }
     *out = g;
     return MEG_OK;
@@ -760,6 +855,7 @@ meg_status meg_group_destroy(meg_group g) {
     cudaStreamSynchronize(g->stream);
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
     if (g->d_desc) cudaFree(g->d_desc);
+    if (g->d_tc_desc) cudaFree(g->d_tc_desc);
     for (auto* h : g->solves) { h->in_group = false; h->group_stream = nullptr; }
     if (g->own_stream) cudaStreamDestroy(g->stream);
     delete g;

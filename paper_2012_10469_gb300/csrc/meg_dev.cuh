@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include "../../include/meg.h"
+#include "dense_tc.cuh"
 
 #define MEG_KMAX 32
 #define MEG_RMAX 30
@@ -54,7 +55,7 @@ enum SmallSlot : int {
 };
 
 // Work-partition kinds (one offset table per kind in a group).
-enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_COUNT = 4 };
+enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_DTC = 4, PK_COUNT = 5 };
 
 #define RED_GROUP 16            // blocks per first-level group of a reduction
 #define RED_MAX_ENTRIES 1536    // >= k(k+1)/2 + r k for k <= 32, r <= 30 (orth2: 528 + 960)
@@ -69,6 +70,9 @@ struct SolveDev {
     int nb_dm, nb_ds;    // dense product: row tiles, K splits
     int ks_len;          // K extent of one split (multiple of the K tile)
     int nb_csr, nb_meas; // blocks of the CSR / measurement kernels
+    int tc;              // 1: dense product on tcgen05 (bf16 data, n % 8 == 0)
+    int nb_tm;           // tensor-core path: 128-row tiles
+    int tc_npad, tc_kpad;// Wsp: (3k padded to 16) x (n padded to 64) bf16
     int off[PK_COUNT];   // first block of this solve in a grouped launch
     double* V;           // n x r   float64 in every mode: V of X_t
     double* Vn;          // n x r   float64: V of X_{t+1} being formed
@@ -77,6 +81,7 @@ struct SolveDev {
     void* Z;             // n x k   (T)  (M_t - c I) W
     void* Y;             // n x k   (T)  gradient-part product
     void* Ys;            // nb_ds x n x k (T) split-K partials of the dense product
+    unsigned short* Wsp; // bf16 bits of W = W_hi + W_mid + W_lo, K-major (tensor-core path)
     float* part;         // reduction partials: [nb_red + groups][2 * RED_MAX_ENTRIES]
     unsigned* ctr;       // reduction counters: [groups + 1]
     double* sm;          // SmallSlot state
@@ -188,12 +193,20 @@ __device__ __forceinline__ double eps_of(const SolveDev& s, double t) {
 
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers (defined in the kernel translation units).
+#define TC_MAX_CHUNKS 8
 struct GroupLaunch {
     const SolveDev* d_solves;   // device array of descriptors
     int ns;                     // number of solves
     int blocks[PK_COUNT];       // total blocks per partition kind
     int prec;                   // storage precision of the group
     cudaStream_t stream;
+    // tensor-core dense product: chunks of at most TC_MAXG solves, each with
+    // its own descriptor sub-array (PK_DTC offsets relative to the chunk)
+    int tc_chunks;
+    const SolveDev* tc_desc[TC_MAX_CHUNKS];
+    int tc_ns[TC_MAX_CHUNKS];
+    int tc_blocks[TC_MAX_CHUNKS];
+    const TcMaps* tc_maps[TC_MAX_CHUNKS];
 };
 
 // mode of a reduction-kernel launch within an iteration

@@ -108,6 +108,24 @@ def test_config1_scaled(prec):
     prob = synth.config(1, scale=384, storage="bf16" if prec == "bf16" else "f32")
     rows = run_pair("dense_quadratic", prob, 10, 6, 2, B.PRECISION[prec], 1.0, 30, {1, 5, 30})
     _check(rows, 10)
+    s = make_gpu_solve("dense_quadratic", prob, 10, 6, 2, B.PRECISION[prec], 1.0, 1)
+    assert np.frombuffer(s.meg_get_state()[:64], dtype=np.int64)[7] == (1 if prec == "bf16" else 0)
+    s.meg_destroy()
+
+
+@pytest.mark.parametrize("n", [392, 250])
+def test_bf16_ragged_sizes(n):
+    """bf16 dense product at sizes with partial 128-row tiles and 64-column K
+    blocks (n = 392, tensor-core path) and with n not a multiple of 8 (n = 250,
+    where the CUDA-core product is used)."""
+    from paper_2012_10469_gb300 import binding as B
+    prob = synth.dense_quadratic(n, 5, seed=80 + n, sigma=1e-5, storage="bf16")
+    rows = run_pair("dense_quadratic", prob, 5, 3, 2, B.MEG_MIXED_BF16, 1.0, 12, {1, 12})
+    _check(rows, 5)
+    s = make_gpu_solve("dense_quadratic", prob, 5, 3, 2, B.MEG_MIXED_BF16, 1.0, 1)
+    tc = np.frombuffer(s.meg_get_state()[:64], dtype=np.int64)[7]
+    assert tc == (1 if n % 8 == 0 else 0)      # tcgen05 product where TMA can address the rows
+    s.meg_destroy()
 
 
 def test_linear_fp64():
