@@ -2,21 +2,31 @@
 // for the mixed-precision path: D is the objective's n x n bfloat16 matrix,
 // W the float32 subspace block, split exactly into three bfloat16 pieces
 // W = W_hi + W_mid + W_lo (24 mantissa bits) by k_orth2 and stored K-major
-// as Wsp[3k padded to 16][n padded to 64].  One CTA computes a 128-row tile
-// of [D W_hi | D W_mid | D W_lo] over one K split:
-//   - warp 0, one lane: TMA producer, 64-column K blocks of D (128 x 64) and
-//     Wsp (N x 64), 128-byte swizzle, into a 3-stage mbarrier ring;
-//   - warp 1, one lane: issues tcgen05.mma kind::f16 (bf16 x bf16 -> fp32 in
-//     tensor memory), M = 128, N = 3k padded to 16, K = 16 per instruction;
-//   - all four warps: tcgen05.ld of the accumulator, sum of the three pieces,
-//     float32 partial of this K split written to Ys (summed in k_combine).
+// as Wsp[3k padded to 16][n padded to 64].
+//
+// Persistent stream-K schedule: the launch's work is the sequence of 64-wide
+// K chunks of every 128-row tile of every solve (solve by solve, tile by
+// tile); CTA c of G (one per SM) takes chunks [cT/G, (c+1)T/G).  Where a
+// CTA's range cuts a tile, each piece (segment) is written as its own
+// float32 partial (slot = the CTA's index among the tile's CTAs) and
+// k_combine sums the tile's slots in slot order, so the result does not
+// depend on timing.  Roles inside the CTA (192 threads):
+//   - warp 0, one lane: TMA producer, D tiles (128 x 64) and Wsp tiles
+//     (N x 64), 128-byte swizzle, into an S-stage mbarrier ring that runs on
+//     across segment and tile boundaries (D is streamed once: L2 evict-first);
+//   - warp 1, one lane: issues tcgen05.mma kind::f16 (bf16 x bf16 -> fp32),
+//     M = 128, N = 3k padded to 16, K = 16, into one of two tensor-memory
+//     accumulators (segment i uses accumulator i mod 2);
+//   - warps 2-5: epilogue of the other accumulator: tcgen05.ld, the sum
+//     hi + mid + lo per column, coalesced float32 stores of the partial.
 // Every mbarrier wait is bounded (about one second of globaltimer); on
-// timeout the CTA flags the solve with MEG_ERR_TIMEOUT, drains its own copies
-// and MMAs (again bounded), frees its tensor memory and returns.
+// timeout the CTA flags its solves with MEG_ERR_TIMEOUT, waits (bounded) for
+// its own copies and MMAs, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "dense_tc.cuh"
@@ -24,13 +34,15 @@
 
 namespace {
 
-constexpr int TC_THREADS = 128;
-constexpr int TC_STAGES = 3;
+constexpr int TC_THREADS = 192;
+constexpr int TC_STAGES_MAX = 8;
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;                       // bf16 elements per 128-byte row
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;   // 16 KB
-constexpr int TC_B_MAX = TC_NMAX * TC_BK * 2;   // 12 KB
-constexpr int TC_TMEM_COLS = 128;
+constexpr int TC_TMEM_COLS = 256;               // two accumulators, 128 columns apart
+constexpr int TC_EPI_LD = 33;                   // epilogue staging row (k <= 32 floats)
+constexpr int TC_EPI_BYTES = TC_BM * TC_EPI_LD * 4;
+constexpr int TC_SMEM_LIMIT = 227 * 1024;
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // 1 s
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -79,6 +91,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4}], [%2], %5;"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle,
 // 8-row groups 1024 bytes apart (stride byte offset), version bits 46-48 = 1.
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
@@ -123,37 +154,57 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// One segment of a CTA's chunk range: solve, tile, first chunk, chunk count,
+// partial slot.
+struct TcSeg {
+    int si, m0, kb0, len, slot;
+};
+
+// Segment of CTA c that starts at chunk g (g < end of the CTA's range).
+__device__ __forceinline__ TcSeg tc_segment(const SolveDev* sds, int ns, long long g, long long gend, long long T,
+                                            int G, int c) {
+    TcSeg q;
+    q.si = find_solve(sds, ns, PK_DTC, (int)g);
+    const SolveDev& s = sds[q.si];
+    const int nkb = s.tc_kpad / TC_BK;
+    const long long local = g - s.off[PK_DTC];
+    const int mt = (int)(local / nkb);
+    q.kb0 = (int)(local % nkb);
+    q.m0 = mt * TC_BM;
+    q.len = (int)min((long long)(nkb - q.kb0), gend - g);
+    q.slot = c - tc_cta_of(g - q.kb0, G, T);
+    return q;
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_dense_tc(const SolveDev* sds, int ns, const __grid_constant__ TcMaps maps) {
-    const int si = find_solve(sds, ns, PK_DTC, blockIdx.x);
-    const SolveDev& s = sds[si];
-    const int lb = blockIdx.x - s.off[PK_DTC];
-    const int nblk = s.nb_tm * s.nb_ds;
-    if (lb < 0 || lb >= nblk) return;
-    const int n = s.n, k = s.k, npad = s.tc_npad;
-    const int mt = lb % s.nb_tm, sp = lb / s.nb_tm;
-    const int m0 = mt * TC_BM;
-    const int k0 = sp * s.ks_len, k1 = min(n, k0 + s.ks_len);
-    const int nkb = (k1 - k0 + TC_BK - 1) / TC_BK;
+k_dense_tc(const SolveDev* sds, int ns, const __grid_constant__ TcMaps maps, long long T, int S, int b_stride) {
+    const int G = gridDim.x, c = blockIdx.x;
+    const long long g_begin = tc_chunk_start(c, G, T), g_end = tc_chunk_start(c + 1, G, T);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t b_bytes = (uint32_t)npad * TC_BK * 2;
 
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
-    unsigned char* sA = base;                                   // TC_STAGES x 16 KB
-    unsigned char* sB = base + TC_STAGES * TC_A_BYTES;          // TC_STAGES x 12 KB
-    uint64_t* full = (uint64_t*)(sB + TC_STAGES * TC_B_MAX);
-    uint64_t* empty = full + TC_STAGES;
-    uint64_t* accb = empty + TC_STAGES;
-    uint32_t* tslot = (uint32_t*)(accb + 1);
-    int* err = (int*)(tslot + 1);
+    unsigned char* sA = base;                                   // S x 16 KB
+    unsigned char* sB = base + (size_t)S * TC_A_BYTES;          // S x b_stride
+    float* stage = (float*)(sB + (size_t)S * b_stride);         // 128 x TC_EPI_LD
+    uint64_t* full = (uint64_t*)(stage + TC_BM * TC_EPI_LD);
+    uint64_t* empty = full + S;
+    uint64_t* tfull = empty + S;                                // accumulator ready [2]
+    uint64_t* tempty = tfull + 2;                               // accumulator drained [2]
+    uint64_t* mdone = tempty + 2;
+    uint32_t* tslot = (uint32_t*)(mdone + 1);
+    volatile int* err = (volatile int*)(tslot + 1);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) {
+        for (int i = 0; i < S; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
         }
-        mbar_init(accb, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 4);
+        }
+        mbar_init(mdone, 1);
         *err = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -167,69 +218,101 @@ k_dense_tc(const SolveDev* sds, int ns, const __grid_constant__ TcMaps maps) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const CUtensorMap* mapA = &maps.a[si];
-    const CUtensorMap* mapB = &maps.b[si];
 
-    if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer
-        int issued = 0;
-        for (int it = 0; it < nkb; ++it) {
-            const int st = it % TC_STAGES;
-            const uint32_t par = ((it / TC_STAGES) & 1) ^ 1;
-            if (!mbar_wait(&empty[st], par)) { *err = 1; break; }
-            mbar_arrive_expect_tx(&full[st], TC_A_BYTES + b_bytes);
-            const int kx = k0 + it * TC_BK;
-            tma_load_2d(sA + st * TC_A_BYTES, mapA, &full[st], kx, m0);
-            tma_load_2d(sB + st * TC_B_MAX, mapB, &full[st], kx, 0);
-            ++issued;
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer
+            const uint64_t pol = policy_evict_first();
+            int it = 0;
+            for (long long g = g_begin; g < g_end && !*err;) {
+                const TcSeg q = tc_segment(sds, ns, g, g_end, T, G, c);
+                const uint32_t bytes = TC_A_BYTES + (uint32_t)sds[q.si].tc_npad * TC_BK * 2;
+                for (int j = 0; j < q.len; ++j, ++it) {
+                    const int st = it % S;
+                    if (!mbar_wait(&empty[st], ((it / S) & 1) ^ 1)) { *err = 1; break; }
+                    mbar_arrive_expect_tx(&full[st], bytes);
+                    const int kx = (q.kb0 + j) * TC_BK;
+                    tma_load_2d_hint(sA + (size_t)st * TC_A_BYTES, &maps.a[q.si], &full[st], kx, q.m0, pol);
+                    tma_load_2d(sB + (size_t)st * b_stride, &maps.b[q.si], &full[st], kx, 0);
+                }
+                g += q.len;
+            }
+            if (*err) {
+                // drain: wait (bounded) for the copies that may still be in flight
+                for (int j = (it > S ? it - S : 0); j < it; ++j) mbar_wait(&full[j % S], (j / S) & 1);
+            }
         }
-        if (*err) {
-            // drain: wait (bounded) for the copies already in flight
-            for (int it = (issued > TC_STAGES ? issued - TC_STAGES : 0); it < issued; ++it)
-                mbar_wait(&full[it % TC_STAGES], (it / TC_STAGES) & 1);
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer
+            int it = 0, i = 0;
+            for (long long g = g_begin; g < g_end && !*err; ++i) {
+                const TcSeg q = tc_segment(sds, ns, g, g_end, T, G, c);
+                const int ab = i & 1;
+                if (!mbar_wait(&tempty[ab], ((i >> 1) & 1) ^ 1)) { *err = 1; break; }
+                tc_fence_after();
+                const uint32_t acc = tmem + (uint32_t)(ab * 128);
+                const uint32_t idesc = idesc_bf16(TC_BM, sds[q.si].tc_npad);
+                bool ok = true;
+                for (int j = 0; j < q.len; ++j, ++it) {
+                    const int st = it % S;
+                    if (!mbar_wait(&full[st], (it / S) & 1)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * b_stride);
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk)
+                        umma_bf16(acc, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                                  (j > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(&empty[st]);        // frees the stage once these MMAs have read it
+                }
+                if (!ok) { *err = 1; break; }
+                umma_commit(&tfull[ab]);            // accumulator ab complete
+                g += q.len;
+            }
+            umma_commit(mdone);                     // every MMA issued by this thread
+            mbar_wait(mdone, 0);
         }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------- MMA issuer
-        const uint32_t idesc = idesc_bf16(TC_BM, npad);
-        int done = 0;
-        for (int it = 0; it < nkb; ++it) {
-            const int st = it % TC_STAGES;
-            if (!mbar_wait(&full[st], (it / TC_STAGES) & 1)) { *err = 1; break; }
+    } else {
+        // ---------------- epilogue: warp w reads accumulator lanes 32 (w mod 4) ...
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        float* srow = stage + row * TC_EPI_LD;
+        int i = 0;
+        for (long long g = g_begin; g < g_end && !*err; ++i) {
+            const TcSeg q = tc_segment(sds, ns, g, g_end, T, G, c);
+            const SolveDev& s = sds[q.si];
+            const int n = s.n, k = s.k, npad = s.tc_npad;
+            const int ab = i & 1;
+            if (!mbar_wait(&tfull[ab], (i >> 1) & 1)) { *err = 1; break; }
             tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + st * TC_A_BYTES), b0 = smem_u32(sB + st * TC_B_MAX);
+            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 128);
+            for (int c0 = 0; c0 < npad; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(tb + (uint32_t)c0, v);
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk)
-                umma_bf16(tmem, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
-                          (it > 0 || kk > 0) ? 1u : 0u);
-            umma_commit(&empty[st]);        // frees the stage once these MMAs have read it
-            ++done;
+                for (int j = 0; j < 16; ++j) {
+                    const int col = c0 + j;
+                    const float x = __uint_as_float(v[j]);
+                    if (col < k) srow[col] = x;                       // W_hi piece
+                    else if (col < 2 * k) srow[col - k] += x;         // + W_mid piece
+                    else if (col < 3 * k) srow[col - 2 * k] += x;     // + W_lo piece
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[ab]);
+            // this warp's 32 rows are k * 32 consecutive floats of the partial
+            float* Ys = (float*)s.Ys + ((size_t)q.slot * n + q.m0 + quarter * 32) * k;
+            const int rows = min(32, n - (q.m0 + quarter * 32));
+            for (int e = lane; e < rows * k; e += 32) Ys[e] = stage[(quarter * 32 + e / k) * TC_EPI_LD + e % k];
+            __syncwarp();
+            g += q.len;
         }
-        umma_commit(accb);                  // accumulator complete (all MMAs issued so far)
-    }
-    __syncwarp();
-    // ---------------- epilogue: every thread owns one accumulator row
-    const bool ok_acc = mbar_wait(accb, 0);
-    tc_fence_after();
-    float* stage = (float*)sA;              // reuse the A ring: 128 rows x (npad + 1) floats
-    const int ld = npad + 1;
-    const int row = warp * 32 + lane;
-    if (ok_acc) {
-        for (int c0 = 0; c0 < npad; c0 += 16) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) stage[row * ld + c0 + j] = __uint_as_float(v[j]);
-        }
-    }
-    const int gi = m0 + row;
-    if (ok_acc && !*err && gi < n) {
-        float* Ys = (float*)s.Ys + ((size_t)sp * n + gi) * k;
-        for (int c = 0; c < k; ++c)
-            Ys[c] = stage[row * ld + c] + stage[row * ld + k + c] + stage[row * ld + 2 * k + c];
     }
     tc_fence_before();
     __syncthreads();
-    if ((!ok_acc || *err) && threadIdx.x == 0) s.sm[SM_STATUS] = MEG_ERR_TIMEOUT;
+    if (*err && threadIdx.x == 0)
+        for (int i = 0; i < ns; ++i) sds[i].sm[SM_STATUS] = MEG_ERR_TIMEOUT;
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
@@ -241,7 +324,15 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 }  // namespace
 
-size_t tc_smem_bytes() { return 1024 + TC_STAGES * (TC_A_BYTES + TC_B_MAX) + (2 * TC_STAGES + 1) * 8 + 16; }
+// stages of the ring for a B tile of b_stride bytes, and the dynamic shared memory
+int tc_stages(int b_stride) {
+    const int fixed = 1024 + TC_EPI_BYTES + 256;
+    return std::min(TC_STAGES_MAX, (TC_SMEM_LIMIT - fixed) / (TC_A_BYTES + b_stride));
+}
+
+size_t tc_smem_bytes(int S, int b_stride) {
+    return 1024 + (size_t)S * (TC_A_BYTES + b_stride) + TC_EPI_BYTES + (2 * S + 5) * 8 + 16;
+}
 
 cudaError_t tc_init() {
     if (!g_encode) {
@@ -252,7 +343,7 @@ cudaError_t tc_init() {
         if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
         g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    return cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+    return cudaFuncSetAttribute(k_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_LIMIT);
 }
 
 // Tensor maps of one solve: A over D (n x n bf16, rows of n elements), B over
@@ -277,8 +368,11 @@ bool tc_make_maps(const void* D, int n, const void* Wsp, int kpad, int npad, CUt
     return r == CUDA_SUCCESS;
 }
 
-cudaError_t launch_dense_tc(const SolveDev* d_solves, int ns, int blocks, const TcMaps& maps, cudaStream_t st) {
-    if (blocks == 0) return cudaSuccess;
-    k_dense_tc<<<blocks, TC_THREADS, tc_smem_bytes(), st>>>(d_solves, ns, maps);
+cudaError_t launch_dense_tc(const SolveDev* d_solves, int ns, long long T, int G, int npad_max, const TcMaps& maps,
+                            cudaStream_t st) {
+    if (T <= 0 || G <= 0) return cudaSuccess;
+    const int b_stride = npad_max * TC_BK * 2;      // a multiple of 2048: keeps 1024-byte tile alignment
+    const int S = tc_stages(b_stride);
+    k_dense_tc<<<G, TC_THREADS, tc_smem_bytes(S, b_stride), st>>>(d_solves, ns, maps, T, S, b_stride);
     return cudaGetLastError();
 }

@@ -14,7 +14,10 @@ struct TcMaps {
     CUtensorMap b[TC_MAXG];   // over the split subspace block Wsp
 };
 
+#define TC_YS_SLOTS 8       // partial slots per solve: a tile is cut into at most this many segments
+
 cudaError_t tc_init();
-size_t tc_smem_bytes();
 bool tc_make_maps(const void* D, int n, const void* Wsp, int kpad, int npad, CUtensorMap* a, CUtensorMap* b);
-cudaError_t launch_dense_tc(const SolveDev* d_solves, int ns, int blocks, const TcMaps& maps, cudaStream_t st);
+// T = chunks of the launch (sum over its solves of row tiles x K chunks), G = CTAs
+cudaError_t launch_dense_tc(const SolveDev* d_solves, int ns, long long T, int G, int npad_max, const TcMaps& maps,
+                            cudaStream_t st);

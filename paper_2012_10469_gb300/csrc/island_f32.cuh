@@ -13,55 +13,67 @@
 // ---------------------------------------------------------------------------
 // A (k x k SPD, float) -> M = L^{-T} with A = L L^T, computed on the
 // equilibrated matrix B = D A D (D = diag(A)^{-1/2}): B = Lb Lb^T,
-// L = D^{-1} Lb, L^{-T} = D Lb^{-T}.  Warp 0 only; returns false on a
-// non-positive pivot (M then holds the identity).  A is destroyed.
-__device__ inline bool chol_inv_f32(float* A, float* M, float* dsc, int k, int* flag) {
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid < 32) {
-        if (lane == 0) *flag = 0;
-        if (lane < k) {
-            const float d = A[lane * MEG_LDK + lane];
-            dsc[lane] = d > 0.f ? rsqrtf(d) : 0.f;
+// L = D^{-1} Lb, L^{-T} = D Lb^{-T}.  Warp 0 only, in registers: lane i
+// holds row i of B (then of Lb) and column i of X = Lb^{-1}; the entries
+// other lanes need travel by warp shuffles.  The order KP is k rounded up to
+// a multiple of 8 and fixed at compile time, B padded with the identity, so
+// every loop is straight-line code; pivots use the hardware reciprocal
+// square root (one or two units in the last place, removed by the second
+// CholeskyQR pass).  Returns false on a non-positive pivot (M then holds the
+// identity).  A is not modified.
+template <int KP>
+__device__ __forceinline__ void chol_inv_f32_k(const float* A, float* M, float* dsc, int k, int* flag) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const float dl = (lane < k) ? A[lane * MEG_LDK + lane] : 1.f;
+    const float sl = (lane < k && dl > 0.f) ? rsqrtf(dl) : 0.f;
+    if (lane < k) dsc[lane] = sl;
+    float a[KP];
+#pragma unroll
+    for (int c = 0; c < KP; ++c) {
+        const float sc = __shfl_sync(full, sl, c);
+        a[c] = (lane < k && c < k) ? A[lane * MEG_LDK + c] * sl * sc : (c == lane ? 1.f : 0.f);
+    }
+    int bad = 0;
+    // right-looking Cholesky: column j of Lb, then the trailing update
+#pragma unroll
+    for (int j = 0; j < KP; ++j) {
+        float d = __shfl_sync(full, a[j], j);
+        if (!(d > 0.f)) { bad = 1; d = 1.f; }
+        const float inv = rsqrtf(d), pj = d * inv;
+        a[j] = (lane == j) ? pj : (lane > j ? a[j] * inv : a[j]);
+#pragma unroll
+        for (int c = j + 1; c < KP; ++c) {
+            const float lcj = __shfl_sync(full, a[j], c);
+            a[c] = (lane > j) ? fmaf(-a[j], lcj, a[c]) : a[c];
         }
-        __syncwarp();
-        if (lane < k)
-            for (int c = 0; c < k; ++c) A[lane * MEG_LDK + c] *= dsc[lane] * dsc[c];
-        __syncwarp();
-        for (int j = 0; j < k; ++j) {
-            if (lane == j) {
-                float d = A[j * MEG_LDK + j];
-                if (!(d > 0.f)) { *flag = 1; d = 1.f; }
-                A[j * MEG_LDK + j] = sqrtf(d);
-            }
-            __syncwarp();
-            const float ljj = A[j * MEG_LDK + j];
-            if (lane > j && lane < k) A[lane * MEG_LDK + j] /= ljj;
-            __syncwarp();
-            if (lane > j && lane < k) {
-                const float lij = A[lane * MEG_LDK + j];
-                for (int c = j + 1; c <= lane; ++c) A[lane * MEG_LDK + c] -= lij * A[c * MEG_LDK + j];
-            }
-            __syncwarp();
+    }
+    // X = Lb^{-1}, lane = column: X_ic = (delta_ic - sum_{m<i} L_im X_mc) / L_ii
+    float x[KP];
+#pragma unroll
+    for (int i = 0; i < KP; ++i) {
+        float acc = (lane == i) ? 1.f : 0.f;
+#pragma unroll
+        for (int m = 0; m < i; ++m) acc = fmaf(-__shfl_sync(full, a[m], i), x[m], acc);
+        x[i] = acc * __frcp_rn(__shfl_sync(full, a[i], i));
+    }
+    // M = D X^T: lane c writes row c (zero left of the diagonal since X is lower)
+    if (lane < k) {
+#pragma unroll
+        for (int i = 0; i < KP; ++i)
+            if (i < k) M[lane * MEG_LDK + i] = bad ? (i == lane ? 1.f : 0.f) : sl * x[i];
+    }
+    if (lane == 0) *flag = bad;
+}
+
+__device__ inline bool chol_inv_f32(const float* A, float* M, float* dsc, int k, int* flag) {
+    if (threadIdx.x < 32) {
+        switch ((k + 7) >> 3) {
+            case 1: chol_inv_f32_k<8>(A, M, dsc, k, flag); break;
+            case 2: chol_inv_f32_k<16>(A, M, dsc, k, flag); break;
+            case 3: chol_inv_f32_k<24>(A, M, dsc, k, flag); break;
+            default: chol_inv_f32_k<32>(A, M, dsc, k, flag); break;
         }
-        // column c of Lb^{-1} by forward substitution in lane c; M_{c i} = d_c (Lb^{-1})_{i c}
-        if (lane < k) {
-            const int c = lane;
-            float x[MEG_KMAX];
-            for (int i = 0; i < k; ++i) x[i] = 0.f;
-            x[c] = 1.f / A[c * MEG_LDK + c];
-            for (int i = c + 1; i < k; ++i) {
-                float s = 0.f;
-                for (int m = c; m < i; ++m) s = fmaf(A[i * MEG_LDK + m], x[m], s);
-                x[i] = -s / A[i * MEG_LDK + i];
-            }
-            for (int i = 0; i < k; ++i) M[i * MEG_LDK + c] = 0.f;
-            for (int i = c; i < k; ++i) M[i * MEG_LDK + c] = 0.f;
-            __syncwarp(__activemask());
-            for (int i = c; i < k; ++i) M[c * MEG_LDK + i] = dsc[c] * x[i];
-        }
-        __syncwarp();
-        if (*flag && lane < k)
-            for (int i = 0; i < k; ++i) M[lane * MEG_LDK + i] = (i == lane) ? 1.f : 0.f;
     }
     __syncthreads();
     return *flag == 0;
@@ -79,74 +91,86 @@ __device__ inline void mm_f32(const float* A, bool transA, const float* B, float
 }
 
 // ---------------------------------------------------------------------------
-// Jacobi eigen-decomposition of a symmetric float matrix (parallel,
-// round-robin ordering of the k/2 disjoint rotations of a round; exact 2 x 2
-// symmetric Schur step, Golub & Van Loan Section 8.5).  A is overwritten by
-// a nearly diagonal matrix, Q accumulates the rotations (starts at I).
-// Stops when the off-diagonal norm falls below tol * ||diag|| or stalls.
-__device__ inline void jacobi_f32(float* A, float* Q, float* B, float* pr, int k, int max_sweeps, float tol) {
-    const int tid = threadIdx.x, nt = blockDim.x;
+// Jacobi eigen-decomposition of a symmetric float matrix by one warp (lane i
+// owns row i; k <= 32).  Round-robin ordering: the k/2 disjoint rotations of
+// a round are applied together, each an exact 2 x 2 symmetric Schur step
+// (Golub & Van Loan, Section 8.5).  Rows are double-buffered (A <-> B) so a
+// round needs only warp synchronisation.  On return *pA points at the nearly
+// diagonal matrix and Q holds the accumulated rotations.  Stops when the
+// off-diagonal norm is below tol times the diagonal norm or stops falling.
+__device__ inline int jacobi_warp_f32(float** pA, float* B, float* Q, float* pr, int k, int max_sweeps, float tol) {
+    __shared__ int nsw;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int kk = (k + 1) & ~1;
     int* partner = (int*)(pr + 2 * MEG_KMAX);
     float* cs = pr;
     float* sg = pr + MEG_KMAX;
-    __shared__ float s_off, s_dia;
-    for (int e = tid; e < k * k; e += nt) Q[(e / k) * MEG_LDK + e % k] = (e / k == e % k) ? 1.f : 0.f;
-    __syncthreads();
-    float prev_off = 3.4e38f;
-    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        if (tid < 32) {
+    if (tid < 32) {
+        float* A = *pA;
+        if (lane < k)
+            for (int j = 0; j < k; ++j) Q[lane * MEG_LDK + j] = (j == lane) ? 1.f : 0.f;
+        float prev_off = 3.4e38f;
+        int sweep = 0;
+        for (; sweep < max_sweeps; ++sweep) {
+            __syncwarp();
             float off = 0.f, dia = 0.f;
-            for (int e = tid; e < k * k; e += 32) {
-                const float v = A[(e / k) * MEG_LDK + e % k];
-                if (e / k == e % k) dia += v * v; else off += v * v;
-            }
+            if (lane < k)
+                for (int j = 0; j < k; ++j) {
+                    const float v = A[lane * MEG_LDK + j];
+                    if (j == lane) dia += v * v; else off += v * v;
+                }
             for (int o = 16; o > 0; o >>= 1) {
                 off += __shfl_xor_sync(0xffffffffu, off, o);
                 dia += __shfl_xor_sync(0xffffffffu, dia, o);
             }
-            if (tid == 0) { s_off = off; s_dia = dia; }
-        }
-        __syncthreads();
-        const float off = s_off;
-        if (off <= tol * tol * s_dia || off >= prev_off) break;
-        prev_off = off;
-        for (int round = 0; round < kk - 1; ++round) {
-            if (tid < kk / 2) {
-                const int a = tid == 0 ? 0 : 1 + (tid - 1 + round) % (kk - 1);
-                const int bpos = kk - 1 - tid;
-                const int b = bpos == 0 ? 0 : 1 + (bpos - 1 + round) % (kk - 1);
-                const int p = min(a, b), q = max(a, b);
-                float c = 1.f, s = 0.f;
-                if (q < k) {
-                    const float apq = A[p * MEG_LDK + q];
-                    if (apq != 0.f) {
-                        const float th = (A[q * MEG_LDK + q] - A[p * MEG_LDK + p]) / (2.f * apq);
-                        const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(1.f + th * th));
-                        c = rsqrtf(1.f + t * t);
-                        s = t * c;
+            if (off <= tol * tol * dia || off >= prev_off) break;
+            prev_off = off;
+            for (int round = 0; round < kk - 1; ++round) {
+                if (lane < kk / 2) {
+                    const int a = lane == 0 ? 0 : 1 + (lane - 1 + round) % (kk - 1);
+                    const int bpos = kk - 1 - lane;
+                    const int b = bpos == 0 ? 0 : 1 + (bpos - 1 + round) % (kk - 1);
+                    const int p = min(a, b), q = max(a, b);
+                    float c = 1.f, s = 0.f;
+                    if (q < k) {
+                        const float apq = A[p * MEG_LDK + q];
+                        if (apq != 0.f) {
+                            const float th = (A[q * MEG_LDK + q] - A[p * MEG_LDK + p]) / (2.f * apq);
+                            const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(1.f + th * th));
+                            c = rsqrtf(1.f + t * t);
+                            s = t * c;
+                        }
+                    }
+                    if (p < k) { partner[p] = q < k ? q : p; cs[p] = c; sg[p] = q < k ? -s : 0.f; }
+                    if (q < k) { partner[q] = p; cs[q] = c; sg[q] = s; }
+                }
+                __syncwarp();
+                if (lane < k) {
+                    const int i = lane, pi = partner[i];
+                    const float ci = cs[i], si = sg[i];
+                    for (int j = 0; j < k; ++j) {
+                        const int pj = partner[j];
+                        const float cj = cs[j], sj = sg[j];
+                        B[i * MEG_LDK + j] = ci * (cj * A[i * MEG_LDK + j] + sj * A[i * MEG_LDK + pj]) +
+                                             si * (cj * A[pi * MEG_LDK + j] + sj * A[pi * MEG_LDK + pj]);
+                    }
+                    // Q <- Q J on row i: columns j and partner(j) mix; process each pair once
+                    for (int j = 0; j < k; ++j) {
+                        const int pj = partner[j];
+                        if (pj < j) continue;
+                        const float qj = Q[i * MEG_LDK + j], qp = Q[i * MEG_LDK + pj];
+                        Q[i * MEG_LDK + j] = cs[j] * qj + sg[j] * qp;
+                        if (pj != j) Q[i * MEG_LDK + pj] = cs[pj] * qp + sg[pj] * qj;
                     }
                 }
-                if (p < k) { partner[p] = q < k ? q : p; cs[p] = c; sg[p] = q < k ? -s : 0.f; }
-                if (q < k) { partner[q] = p; cs[q] = c; sg[q] = s; }
+                __syncwarp();
+                float* t = A; A = B; B = t;
             }
-            __syncthreads();
-            for (int e = tid; e < k * k; e += nt) {
-                const int i = e / k, j = e % k, pi = partner[i], pj = partner[j];
-                B[i * MEG_LDK + j] = cs[i] * (cs[j] * A[i * MEG_LDK + j] + sg[j] * A[i * MEG_LDK + pj]) +
-                                     sg[i] * (cs[j] * A[pi * MEG_LDK + j] + sg[j] * A[pi * MEG_LDK + pj]);
-            }
-            __syncthreads();
-            for (int e = tid; e < k * k; e += nt) {
-                const int i = e / k, j = e % k;
-                A[i * MEG_LDK + j] = B[i * MEG_LDK + j];
-                B[i * MEG_LDK + j] = cs[j] * Q[i * MEG_LDK + j] + sg[j] * Q[i * MEG_LDK + partner[j]];
-            }
-            __syncthreads();
-            for (int e = tid; e < k * k; e += nt) Q[(e / k) * MEG_LDK + e % k] = B[(e / k) * MEG_LDK + e % k];
-            __syncthreads();
         }
+        if (lane == 0) { *pA = A; nsw = sweep; }
     }
+    __syncthreads();
+    return nsw;
 }
 
 // ---------------------------------------------------------------------------

@@ -11,8 +11,11 @@
 //              last block: Rayleigh-Ritz on span W (final product), exp-map
 //              (Definition 2), certificate (Lemma 2), CholeskyQR factor
 //   orth1/2  : W <- CholeskyQR2(Z) (two passes), V_{t+1} = W Q_r; V^T W, W^T W
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <math.h>
+
+namespace cg = cooperative_groups;
 
 #include "island_f32.cuh"
 #include "kxk.cuh"
@@ -21,6 +24,25 @@
 namespace {
 
 constexpr int NT = 256;              // threads of every row kernel
+
+// sum of entry e over the partials of blocks [b0, b1), in block order; loads are
+// issued eight at a time so that a chain of L2 round trips is not serialised
+__device__ __forceinline__ dw sum_partials(const float* part, size_t stride, int e, int b0, int b1) {
+    dw acc = {0.f, 0.f};
+    int b = b0;
+    for (; b + 8 <= b1; b += 8) {
+        float hv[8], lv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            hv[u] = __ldcg(part + (size_t)(b + u) * stride + 2 * e);
+            lv[u] = __ldcg(part + (size_t)(b + u) * stride + 2 * e + 1);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) dw_add(acc, dw{hv[u], lv[u]});
+    }
+    for (; b < b1; ++b) dw_add(acc, dw{__ldcg(part + (size_t)b * stride + 2 * e), __ldcg(part + (size_t)b * stride + 2 * e + 1)});
+    return acc;
+}
 
 // --------------------------------------------------------------------------
 // Two-level deterministic last-block reduction of per-block double-word
@@ -40,6 +62,16 @@ __device__ bool red_two_level(const SolveDev& s, int lb, const dw* mine, dw* out
     }
     __threadfence();
     __syncthreads();
+    if (s.nb_red <= 128) {
+        // one level: the last block sums every block's partial in block order
+        if (tid == 0) am_last = (atomicAdd(&s.ctr[ngroups], 1u) == (unsigned)(s.nb_red - 1));
+        __syncthreads();
+        if (!am_last) return false;
+        if (tid == 0) s.ctr[ngroups] = 0u;
+        for (int e = tid; e < E; e += blockDim.x) out[e] = sum_partials(part, stride, e, 0, s.nb_red);
+        __syncthreads();
+        return true;
+    }
     const int g = lb / RED_GROUP;
     const int g0 = g * RED_GROUP, gsz = min(RED_GROUP, s.nb_red - g0);
     if (tid == 0) am_last = (atomicAdd(&s.ctr[g], 1u) == (unsigned)(gsz - 1));
@@ -47,11 +79,7 @@ __device__ bool red_two_level(const SolveDev& s, int lb, const dw* mine, dw* out
     if (!am_last) return false;
     if (tid == 0) s.ctr[g] = 0u;
     for (int e = tid; e < E; e += blockDim.x) {
-        dw acc = {0.f, 0.f};
-        for (int b = g0; b < g0 + gsz; ++b) {
-            dw v = {__ldcg(part + (size_t)b * stride + 2 * e), __ldcg(part + (size_t)b * stride + 2 * e + 1)};
-            dw_add(acc, v);
-        }
+        const dw acc = sum_partials(part, stride, e, g0, g0 + gsz);
         part[(size_t)(s.nb_red + g) * stride + 2 * e] = acc.hi;
         part[(size_t)(s.nb_red + g) * stride + 2 * e + 1] = acc.lo;
     }
@@ -61,17 +89,52 @@ __device__ bool red_two_level(const SolveDev& s, int lb, const dw* mine, dw* out
     __syncthreads();
     if (!am_last) return false;
     if (tid == 0) s.ctr[ngroups] = 0u;
-    for (int e = tid; e < E; e += blockDim.x) {
-        dw acc = {0.f, 0.f};
-        for (int gg = 0; gg < ngroups; ++gg) {
-            size_t o = (size_t)(s.nb_red + gg) * stride + 2 * e;
-            dw v = {__ldcg(part + o), __ldcg(part + o + 1)};
-            dw_add(acc, v);
+    for (int e = tid; e < E; e += blockDim.x) out[e] = sum_partials(part, stride, e, s.nb_red, s.nb_red + ngroups);
+    __syncthreads();
+    return true;
+}
+
+// The RED_CLUSTER blocks of a cluster add their E double-word entries through
+// distributed shared memory (in rank order) and rank 0 writes one partial per
+// cluster to the solve's partial buffer.  Every block of the cluster must call
+// this (blocks past the solve's rows contribute zeros).
+__device__ __forceinline__ void write_partial(const SolveDev& s, int lb, dw* ent, int E) {
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();
+    if (cluster.block_rank() == 0) {
+        float* p = s.part + (size_t)(lb / RED_CLUSTER) * 2 * RED_MAX_ENTRIES;
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+            dw acc = ent[e];
+            for (int rk = 1; rk < RED_CLUSTER; ++rk) dw_add(acc, cluster.map_shared_rank(ent, rk)[e]);
+            p[2 * e] = acc.hi;
+            p[2 * e + 1] = acc.lo;
         }
+    }
+    cluster.sync();    // the other blocks' shared memory must stay until rank 0 has read it
+}
+
+// Island kernels: sum the nb_red partials of every entry in a fixed order.
+// Items (entry, chunk of blocks) are spread over the threads, each chunk
+// summed with batched loads; chunks are then added in chunk order.  The
+// result does not depend on timing (deterministic).
+__device__ void reduce_partials(const SolveDev& s, dw* out, int E, dw* scratch, int scratch_cap) {
+    const int nb = (s.nb_red + RED_CLUSTER - 1) / RED_CLUSTER;     // one partial per cluster
+    int C = scratch_cap / E;
+    const int cmax = (nb + 15) / 16;               // at least 16 partials per chunk
+    C = C < 1 ? 1 : (C > cmax ? cmax : C);
+    const size_t stride = 2 * RED_MAX_ENTRIES;
+    for (int it = threadIdx.x; it < C * E; it += blockDim.x) {
+        const int e = it % E, c = it / E;
+        const int b0 = (int)((long long)nb * c / C), b1 = (int)((long long)nb * (c + 1) / C);
+        scratch[c * E + e] = sum_partials(s.part, stride, e, b0, b1);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        dw acc = scratch[e];
+        for (int c = 1; c < C; ++c) dw_add(acc, scratch[c * E + e]);
         out[e] = acc;
     }
     __syncthreads();
-    return true;
 }
 
 // index e of the packed upper triangle (column by column) -> (i, j), i <= j
@@ -228,7 +291,13 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
     // 2. float32 Jacobi on Ht
     for (int e = tid; e < k * k; e += nt) F1[(e / k) * MEG_LDK + e % k] = (float)H[(e / k) * MEG_LDK + e % k];
     __syncthreads();
-    jacobi_f32(F1, F2, F3, (float*)pr, k, 16, 2e-7f);           // Q in F2
+    // the double-word refinement below corrects the remaining rotations to first
+    // order, so Jacobi only has to reach about 1e-5 relative off-diagonal size
+    __shared__ float* jA;
+    if (tid == 0) jA = F1;
+    __syncthreads();
+    const int nsw = jacobi_warp_f32(&jA, F3, F2, (float*)pr, k, 4, 1e-5f);   // Q in F2; F1/F3 free
+    if (tid == 0) smw[SM_JSWEEPS] = nsw;
     // 3. Ht as hi/lo floats; Tq = Ht Q exactly (Dot2), as hi/lo floats in F1/F3
     for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e % k;
@@ -327,10 +396,12 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
         for (int a = 0; a < k; ++a) acc = fmaf(Bh[a * MEG_LDK + tid], Bl[a * MEG_LDK + tid], acc);
         pdg[tid] = acc;
     }
-    // 9. scalars: exp-map (Definition 2), certificate (Lemma 2), objective estimate
+    // 9. scalars: exp-map (Definition 2), certificate (Lemma 2), objective estimate.
+    //    The transcendental functions run side by side on different lanes.
     if (tid < 32) {
         const int lane = tid;
         const double t = smw[SM_T];
+        const double eps = smw[SM_EPS];
         double m = (lane <= r && lane < k) ? sig[lane] : -1e300;
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         const double ex = (lane <= r && lane < k) ? exp(sig[lane] - m) : 0.0;
@@ -339,7 +410,11 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
             a_r += __shfl_xor_sync(0xffffffffu, a_r, o);
             a_r1 += __shfl_xor_sync(0xffffffffu, a_r1, o);
         }
-        const double lse_r = m + log(a_r), lse_r1 = m + log(a_r1);
+        // lane 0: log a_r, lane 1: log a_{r+1}, lane 2: log eps
+        const double lg = log(lane == 0 ? a_r : (lane == 1 ? a_r1 : (lane == 2 ? eps : 1.0)));
+        const double lse_r = m + __shfl_sync(0xffffffffu, lg, 0);
+        const double lse_r1 = m + __shfl_sync(0xffffffffu, lg, 1);
+        const double log_eps = __shfl_sync(0xffffffffu, lg, 2);
         if (s.mode == 1) {
             if (lane == 0) {
                 for (int i = 0; i < r; ++i) mun[i] = sig[i];
@@ -354,7 +429,6 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
                 smw[SM_FIRST_HOLD] = 0.0;
             }
         } else {
-            const double eps = smw[SM_EPS];
             const double s_new = eps / (double)(n - r);
             const double mu = lane < r ? (1.0 - eps) * exp(sig[lane] - lse_r) : 0.0;
             double xd = lane < r ? (mu - s_new) * pdg[lane] : 0.0, x2 = mu * mu;
@@ -364,7 +438,7 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
             }
             if (lane < r) smw[SM_MU + lane] = mu;
             if (lane == 0) {
-                const double cert = log((double)(n - r)) + sig[r] - log(eps) - lse_r1;
+                const double cert = s.log_nr + sig[r] - log_eps - lse_r1;
                 const int holds = cert <= 2.0 * eps;
                 smw[SM_LSE] = lse_r;
                 smw[SM_CERT] = cert;
@@ -412,10 +486,9 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int phase) {
     const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
     const SolveDev& s = sds[si];
-    const int lb = blockIdx.x - s.off[PK_RED];
-    if (lb < 0 || lb >= s.nb_red) return;
+    const int lb = blockIdx.x - s.off[PK_RED];     // blocks past nb_red pad the last cluster
     const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
-    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    const int row0 = min(n, lb * s.rows_red), row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
 
     extern __shared__ __align__(16) unsigned char smraw[];
     // layout: Bc[r*k] Coef, sW/sZ/sY [rows_red*k] T, ent dw[2*528], then k x k doubles
@@ -424,11 +497,6 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     T* sZ = sW + s.rows_red * k;
     T* sY = sZ + s.rows_red * k;
     dw* ent = (dw*)(((uintptr_t)(sY + s.rows_red * k) + 15) & ~(uintptr_t)15);
-    // the k x k doubles start after the row-phase buffers, which the float island
-    // reuses as four float matrices once the reductions are unpacked
-    const uintptr_t rp_end = (uintptr_t)(ent + 2 * 528);
-    const uintptr_t f_end = (uintptr_t)smraw + 4 * 32 * MEG_LDK * sizeof(float);
-    double* kx = (double*)(((rp_end > f_end ? rp_end : f_end) + 15) & ~(uintptr_t)15);
     __shared__ Coef<T> c_id, c_al;
 
     const double* sm = s.sm;
@@ -449,7 +517,7 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     const double* V = s.V;
     T* Z = (T*)s.Z;
     const bool dense = (s.kind == MEG_DENSE_QUAD || s.kind == MEG_LINEAR);
-    __shared__ T sVt[16 * MEG_RMAX];           // this block's rows of V in storage precision
+    __shared__ T sVt[ROWS_MAX * MEG_RMAX];     // this block's rows of V in storage precision
     if (!init)
         for (int e = tid; e < nr * r; e += NT) sVt[e] = (T)V[(size_t)(row0 + e / r) * r + e % r];
     __syncthreads();
@@ -462,7 +530,8 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
         } else {
             if (dense) {
                 const T* Ys = (const T*)s.Ys;
-                for (int p = 0; p < s.nb_ds; ++p) y += Ys[((size_t)p * n + i) * k + j];
+                const int np = s.tc ? tc_tile_slots(s, i / 128) : s.nb_ds;   // slots in order
+                for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
             } else {
                 y = ((const T*)s.Y)[(size_t)i * k + j];
             }
@@ -483,18 +552,44 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     for (int e = tid; e < E; e += NT) {
         int m = e / nsym, i, j;
         tri_decode(e % nsym, i, j);
-        Acc<T> a;
+        Acc<T> a, b;
         a.zero();
-        if (m == 0) {
-            for (int q = 0; q < nr; ++q) a.add_prod(sZ[q * k + i], sZ[q * k + j]);
-        } else {
-            for (int q = 0; q < nr; ++q) a.add_prod(sW[q * k + i], sY[q * k + j]);
+        b.zero();
+        const T* X = (m == 0) ? sZ : sW;
+        const T* Yv = (m == 0) ? sZ : sY;
+        int q = 0;
+        for (; q + 1 < nr; q += 2) {          // two independent chains for ILP
+            a.add_prod(X[q * k + i], Yv[q * k + j]);
+            b.add_prod(X[(q + 1) * k + i], Yv[(q + 1) * k + j]);
         }
-        ent[e] = a.as_dw();
+        if (q < nr) a.add_prod(X[q * k + i], Yv[q * k + j]);
+        dw r0 = a.as_dw();
+        dw_add(r0, b.as_dw());
+        ent[e] = r0;
     }
     __syncthreads();
-    if (!red_two_level(s, lb, ent, ent, E)) return;
+    write_partial(s, lb, ent, E);
+}
 
+// ==========================================================================
+// island after combine (one block per solve): Z^T Z (and W^T Y) from the
+// partials; CholeskyQR factor, and on the final product the Rayleigh-Ritz
+// step, exp-map (Definition 2) and certificate (Lemma 2).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, int phase) {
+    const int si = blockIdx.x;
+    if (si >= ns) return;
+    const SolveDev& s = sds[si];
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    // four float matrices (the reduction's scratch first), the entries, the k x k doubles
+    constexpr int FBYTES = 4 * 32 * MEG_LDK * (int)sizeof(float);
+    dw* ent = (dw*)(smraw + FBYTES);
+    double* kx = (double*)(ent + RED_MAX_ENTRIES);
+    const int nsym = k * (k + 1) / 2;
+    const bool fin = (phase == PH_FINAL);
+    const int E = fin ? 2 * nsym : nsym;
+    reduce_partials(s, ent, E, (dw*)smraw, FBYTES / (int)sizeof(dw));
     // ---------------- last block of this solve: k x k island (float64)
     double* S1 = kx;
     double* A = S1 + 32 * MEG_LDK;
@@ -659,16 +754,14 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_orth1(const SolveDev* sds, int ns, int phase) {
     const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
     const SolveDev& s = sds[si];
-    const int lb = blockIdx.x - s.off[PK_RED];
-    if (lb < 0 || lb >= s.nb_red) return;
+    const int lb = blockIdx.x - s.off[PK_RED];     // blocks past nb_red pad the last cluster
     const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
-    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    const int row0 = min(n, lb * s.rows_red), row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* M1 = (T*)smraw;                                  // k x k
     Coef<T>* Qv = (Coef<T>*)(M1 + MEG_KMAX * MEG_KMAX); // k x r
     T* sW = (T*)(Qv + MEG_KMAX * MEG_RMAX);
     dw* ent = (dw*)(((uintptr_t)(sW + s.rows_red * k) + 15) & ~(uintptr_t)15);
-    double* kx = (double*)(ent + 528);
     const double* sm = s.sm;
     const bool fin = (phase == PH_FINAL);
     for (int e = tid; e < k * k; e += NT) M1[e] = (T)sm[SM_M1 + (e / k) * 32 + e % k];
@@ -710,13 +803,37 @@ __global__ void __launch_bounds__(NT) k_orth1(const SolveDev* sds, int ns, int p
     for (int e = tid; e < nsym; e += NT) {
         int i, j;
         tri_decode(e, i, j);
-        Acc<T> a;
+        Acc<T> a, b;
         a.zero();
-        for (int q = 0; q < nr; ++q) a.add_prod(sW[q * k + i], sW[q * k + j]);
-        ent[e] = a.as_dw();
+        b.zero();
+        int q = 0;
+        for (; q + 1 < nr; q += 2) {
+            a.add_prod(sW[q * k + i], sW[q * k + j]);
+            b.add_prod(sW[(q + 1) * k + i], sW[(q + 1) * k + j]);
+        }
+        if (q < nr) a.add_prod(sW[q * k + i], sW[q * k + j]);
+        dw r0 = a.as_dw();
+        dw_add(r0, b.as_dw());
+        ent[e] = r0;
     }
     __syncthreads();
-    if (!red_two_level(s, lb, ent, ent, nsym)) return;
+    write_partial(s, lb, ent, nsym);
+}
+
+// ==========================================================================
+// island after orth1: W'^T W' from the partials -> second CholeskyQR factor.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_island_o1(const SolveDev* sds, int ns, int phase) {
+    const int si = blockIdx.x;
+    if (si >= ns) return;
+    const SolveDev& s = sds[si];
+    const int k = s.k, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int FBYTES = 4 * 32 * MEG_LDK * (int)sizeof(float);
+    dw* ent = (dw*)(smraw + FBYTES);
+    double* kx = (double*)(ent + RED_MAX_ENTRIES);
+    const int nsym = k * (k + 1) / 2;
+    reduce_partials(s, ent, nsym, (dw*)smraw, FBYTES / (int)sizeof(dw));
     double* A = kx;
     double* C = A + 32 * MEG_LDK;
     __shared__ int flag;
@@ -744,16 +861,15 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int phase) {
     const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
     const SolveDev& s = sds[si];
-    const int lb = blockIdx.x - s.off[PK_RED];
-    if (lb < 0 || lb >= s.nb_red) return;
+    const int lb = blockIdx.x - s.off[PK_RED];     // blocks past nb_red pad the last cluster
     const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
-    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    const int row0 = min(n, lb * s.rows_red), row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
     extern __shared__ __align__(16) unsigned char smraw[];
     T* M2 = (T*)smraw;
     T* sW = M2 + MEG_KMAX * MEG_KMAX;
     double* sV = (double*)(((uintptr_t)(sW + s.rows_red * k) + 7) & ~(uintptr_t)7);
     dw* ent = (dw*)(((uintptr_t)(sV + s.rows_red * r) + 15) & ~(uintptr_t)15);
-    __shared__ float sVh[16 * MEG_RMAX], sVl[16 * MEG_RMAX];
+    __shared__ float sVh[ROWS_MAX * MEG_RMAX], sVl[ROWS_MAX * MEG_RMAX];
     const double* sm = s.sm;
     const bool fin = (phase == PH_FINAL);
     for (int e = tid; e < k * k; e += NT) M2[e] = (T)sm[SM_M2 + (e / k) * 32 + e % k];
@@ -800,12 +916,18 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
     const int nsym = k * (k + 1) / 2;
     const int E = nsym + r * k;
     for (int e = tid; e < E; e += NT) {
-        Acc<T> a;
+        Acc<T> a, b;
         a.zero();
+        b.zero();
         if (e < nsym) {
             int i, j;
             tri_decode(e, i, j);
-            for (int q = 0; q < nr; ++q) a.add_prod(sW[q * k + i], sW[q * k + j]);
+            int q = 0;
+            for (; q + 1 < nr; q += 2) {
+                a.add_prod(sW[q * k + i], sW[q * k + j]);
+                b.add_prod(sW[(q + 1) * k + i], sW[(q + 1) * k + j]);
+            }
+            if (q < nr) a.add_prod(sW[q * k + i], sW[q * k + j]);
         } else {
             int l = (e - nsym) / k, j = (e - nsym) % k;
             for (int q = 0; q < nr; ++q) {
@@ -813,14 +935,32 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
                     a.add_prod(sV[q * r + l], sW[q * k + j]);
                 } else {      // V is float64: two floats per entry, both products exact in Dot2
                     a.add_prod(sVh[q * r + l], sW[q * k + j]);
-                    a.add_prod(sVl[q * r + l], sW[q * k + j]);
+                    b.add_prod(sVl[q * r + l], sW[q * k + j]);
                 }
             }
         }
-        ent[e] = a.as_dw();
+        dw r0 = a.as_dw();
+        dw_add(r0, b.as_dw());
+        ent[e] = r0;
     }
     __syncthreads();
-    if (!red_two_level(s, lb, ent, ent, E)) return;
+    write_partial(s, lb, ent, E);
+}
+
+// ==========================================================================
+// island after orth2: G = W^T W and U = V^T W from the partials.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_island_o2(const SolveDev* sds, int ns, int phase) {
+    const int si = blockIdx.x;
+    if (si >= ns) return;
+    const SolveDev& s = sds[si];
+    const int k = s.k, r = s.r, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int FBYTES = 4 * 32 * MEG_LDK * (int)sizeof(float);
+    dw* ent = (dw*)(smraw + FBYTES);
+    const int nsym = k * (k + 1) / 2;
+    const int E = nsym + r * k;
+    reduce_partials(s, ent, E, (dw*)smraw, FBYTES / (int)sizeof(dw));
     double* smw = s.sm;
     for (int e = tid; e < nsym; e += NT) {
         int i, j;
@@ -1077,7 +1217,7 @@ __global__ void __launch_bounds__(NT) k_meas_apply(const SolveDev* sds, int ns) 
     const double scale = 2.0 / (double)Lb;
     const double* sc = s.meas;
     __shared__ T Sb[64][MEG_KMAX];
-    T acc[4] = {0, 0, 0, 0};
+    T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int nout = nr * k;
     for (int b0 = 0; b0 < Lb; b0 += 64) {
         const int bn = min(64, Lb - b0);
@@ -1087,7 +1227,7 @@ __global__ void __launch_bounds__(NT) k_meas_apply(const SolveDev* sds, int ns) 
             Sb[bb][c] = (T)(scale * sc[b0 + bb] * sc[2 * (size_t)Lb + (size_t)(b0 + bb) * MEG_KMAX + c]);
         }
         __syncthreads();
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 8; ++q) {
             int o = tid + q * NT;
             if (o >= nout) break;
             int i = row0 + o / k, c = o % k;
@@ -1099,7 +1239,7 @@ __global__ void __launch_bounds__(NT) k_meas_apply(const SolveDev* sds, int ns) 
             acc[q] = a2;
         }
     }
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
         int o = tid + q * NT;
         if (o >= nout) break;
         int i = row0 + o / k, c = o % k;
@@ -1227,28 +1367,42 @@ __global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, d
 namespace {
 size_t combine_smem(int prec) {
     size_t tsz = prec == MEG_FP64 ? 8 : 4;
-    size_t coef = (prec == MEG_FP64 ? 8 : 8) * MEG_RMAX * MEG_KMAX;
-    size_t rows = 3 * 16 * MEG_KMAX * tsz;          // rows_red <= 16
-    size_t ent = 2 * 528 * sizeof(dw) + 16;
-    size_t kx = (6 * 32 * MEG_LDK + 32 + 96 + 32) * sizeof(double);
-    size_t rowphase = coef + rows + ent;
-    size_t fl = 4 * 32 * MEG_LDK * sizeof(float);
-    return (rowphase > fl ? rowphase : fl) + 16 + kx;
+    return 8 * MEG_RMAX * MEG_KMAX + 3 * ROWS_MAX * MEG_KMAX * tsz + 2 * 528 * sizeof(dw) + 16;
 }
 size_t orth1_smem(int prec) {
     size_t tsz = prec == MEG_FP64 ? 8 : 4;
-    return MEG_KMAX * MEG_KMAX * tsz + 8 * MEG_KMAX * MEG_RMAX + 16 * MEG_KMAX * tsz + 528 * sizeof(dw) + 16 +
-           2 * 32 * MEG_LDK * sizeof(double);
+    return MEG_KMAX * MEG_KMAX * tsz + 8 * MEG_KMAX * MEG_RMAX + ROWS_MAX * MEG_KMAX * tsz + 528 * sizeof(dw) + 16;
 }
 size_t orth2_smem(int prec) {
     size_t tsz = prec == MEG_FP64 ? 8 : 4;
-    return MEG_KMAX * MEG_KMAX * tsz + 16 * MEG_KMAX * tsz + 8 + 16 * MEG_RMAX * 8 + RED_MAX_ENTRIES * sizeof(dw) + 16;
+    return MEG_KMAX * MEG_KMAX * tsz + ROWS_MAX * MEG_KMAX * tsz + 8 + ROWS_MAX * MEG_RMAX * 8 + RED_MAX_ENTRIES * sizeof(dw) + 16;
+}
+size_t island_smem() {
+    return 4 * 32 * MEG_LDK * sizeof(float) + RED_MAX_ENTRIES * sizeof(dw) + (6 * 32 * MEG_LDK + 32 + 96 + 32) * sizeof(double);
 }
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 }  // namespace
+
+// row-reduction kernels run in clusters of RED_CLUSTER blocks (grid padded per solve)
+template <typename K>
+cudaError_t launch_clustered(K kern, const GroupLaunch& g, size_t smem, int phase) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g.blocks[PK_RED], 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = g.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = RED_CLUSTER;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, g.d_solves, g.ns, phase);
+}
 
 cudaError_t init_kernel_attributes() {
     cudaError_t e;
@@ -1258,6 +1412,12 @@ cudaError_t init_kernel_attributes() {
     if ((e = set_smem(k_orth1<float>, orth1_smem(MEG_FP32))) != cudaSuccess) return e;
     if ((e = set_smem(k_orth2<double>, orth2_smem(MEG_FP64))) != cudaSuccess) return e;
     if ((e = set_smem(k_orth2<float>, orth2_smem(MEG_FP32))) != cudaSuccess) return e;
+    if ((e = set_smem(k_island_c<double>, island_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_island_c<float>, island_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_island_o1<double>, island_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_island_o1<float>, island_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_island_o2<double>, island_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_island_o2<float>, island_smem())) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1268,7 +1428,8 @@ cudaError_t launch_begin(const GroupLaunch& g) {
 
 cudaError_t launch_dense(const GroupLaunch& g) {
     for (int c = 0; c < g.tc_chunks; ++c) {
-        cudaError_t e = launch_dense_tc(g.tc_desc[c], g.tc_ns[c], g.tc_blocks[c], *g.tc_maps[c], g.stream);
+        cudaError_t e = launch_dense_tc(g.tc_desc[c], g.tc_ns[c], g.tc_T[c], g.tc_G[c], g.tc_npad[c], *g.tc_maps[c],
+                                        g.stream);
         if (e != cudaSuccess) return e;
     }
     if (g.blocks[PK_DENSE] == 0) return cudaSuccess;
@@ -1301,30 +1462,39 @@ cudaError_t launch_meas_apply(const GroupLaunch& g) {
 
 cudaError_t launch_combine(const GroupLaunch& g, int phase) {
     size_t sm = combine_smem(g.prec);
+    cudaError_t e;
     if (g.prec == MEG_FP64) {
-        k_combine<double><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+        if ((e = launch_clustered(k_combine<double>, g, sm, phase)) != cudaSuccess) return e;
+        k_island_c<double><<<g.ns, NT, island_smem(), g.stream>>>(g.d_solves, g.ns, phase);
     } else {
-        k_combine<float><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+        if ((e = launch_clustered(k_combine<float>, g, sm, phase)) != cudaSuccess) return e;
+        k_island_c<float><<<g.ns, NT, island_smem(), g.stream>>>(g.d_solves, g.ns, phase);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_orth1(const GroupLaunch& g, int phase) {
     size_t sm = orth1_smem(g.prec);
+    cudaError_t e;
     if (g.prec == MEG_FP64) {
-        k_orth1<double><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+        if ((e = launch_clustered(k_orth1<double>, g, sm, phase)) != cudaSuccess) return e;
+        k_island_o1<double><<<g.ns, NT, island_smem(), g.stream>>>(g.d_solves, g.ns, phase);
     } else {
-        k_orth1<float><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+        if ((e = launch_clustered(k_orth1<float>, g, sm, phase)) != cudaSuccess) return e;
+        k_island_o1<float><<<g.ns, NT, island_smem(), g.stream>>>(g.d_solves, g.ns, phase);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_orth2(const GroupLaunch& g, int phase) {
     size_t sm = orth2_smem(g.prec);
+    cudaError_t e;
     if (g.prec == MEG_FP64) {
-        k_orth2<double><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+        if ((e = launch_clustered(k_orth2<double>, g, sm, phase)) != cudaSuccess) return e;
+        k_island_o2<double><<<g.ns, NT, island_smem(), g.stream>>>(g.d_solves, g.ns, phase);
     } else {
-        k_orth2<float><<<g.blocks[PK_RED], NT, sm, g.stream>>>(g.d_solves, g.ns, phase);
+        if ((e = launch_clustered(k_orth2<float>, g, sm, phase)) != cudaSuccess) return e;
+        k_island_o2<float><<<g.ns, NT, island_smem(), g.stream>>>(g.d_solves, g.ns, phase);
     }
     return cudaGetLastError();
 }

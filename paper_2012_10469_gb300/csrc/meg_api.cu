@@ -47,17 +47,46 @@ cudaError_t ensure_attributes() {
 
 int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-// K splits of the tensor-core product: multiples of 64, about two CTAs per SM for one solve
-void tc_partition(SolveDev& d) {
-    d.nb_tm = (d.n + 127) / 128;
-    int s = std::max(1, (2 * 152 + d.nb_tm - 1) / d.nb_tm);
-    s = std::min(s, std::max(1, (d.n + 63) / 64));
-    const int kl = (d.n + s - 1) / s;
-    d.ks_len = round_up(kl, 64);
-    d.nb_ds = (d.n + d.ks_len - 1) / d.ks_len;
+int g_num_sms = 0;           // SMs of the device the first solve was created on
+
+int num_sms() {
+    if (g_num_sms <= 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+            g_num_sms = v;
+        else
+            g_num_sms = 1;
+    }
+    return g_num_sms;
 }
 
-constexpr int ROWS_RED = 16;
+// K chunks (64 wide) of one tensor-core solve: 128-row tiles x chunks per tile
+long long tc_chunks_of(const SolveDev& d) { return (long long)d.nb_tm * (d.tc_kpad / 64); }
+
+// CTAs of a stream-K launch over T chunks whose tiles have at most nkb_max
+// chunks: one per SM, fewer when a CTA's share would be so short that a tile
+// could be cut into more than TC_YS_SLOTS segments (a share of at least
+// ceil(nkb_max / (slots - 1)) chunks meets at most `slots` CTAs per tile).
+int tc_grid(long long T, int nkb_max) {
+    const long long need = (nkb_max + TC_YS_SLOTS - 2) / (TC_YS_SLOTS - 1);
+    const long long G = std::min<long long>(num_sms(), T / std::max<long long>(1, need));
+    return (int)std::max<long long>(1, G);
+}
+
+void tc_partition(SolveDev& d) {
+    d.nb_tm = (d.n + 127) / 128;
+    d.nb_ds = TC_YS_SLOTS;                 // partial slots of Ys
+    d.ks_len = d.tc_kpad;
+    d.off[PK_DTC] = 0;                     // stand-alone launch: this solve only
+    d.tc_T = tc_chunks_of(d);
+    d.tc_G = tc_grid(d.tc_T, d.tc_kpad / 64);
+}
+
+// rows per reduction block: many small blocks for small n, up to ROWS_MAX for
+// large n (fewer waves of the row kernels, whose last block needs the island's
+// shared memory)
+int rows_red_for(int n) { return n >= 4096 ? ROWS_MAX : (n >= 2048 ? 32 : 16); }
 
 size_t tsize(int prec) { return prec == MEG_FP64 ? 8 : 4; }
 
@@ -113,8 +142,8 @@ struct meg_group_s {
 namespace {
 
 void compute_partition(meg_solve_s* h, SolveDev& d) {
-    d.rows_red = ROWS_RED;
-    d.nb_red = (h->n + ROWS_RED - 1) / ROWS_RED;
+    d.rows_red = rows_red_for(h->n);
+    d.nb_red = (h->n + d.rows_red - 1) / d.rows_red;
     d.nb_dm = (h->n + 63) / 64;
     d.nb_ds = dense_splits(h->n);
     int kl = (h->n + d.nb_ds - 1) / d.nb_ds;
@@ -127,10 +156,10 @@ void compute_partition(meg_solve_s* h, SolveDev& d) {
 int blocks_of(const SolveDev& d, int kind) {
     const bool dense = (d.kind == MEG_DENSE_QUAD || d.kind == MEG_LINEAR);
     switch (kind) {
-        case PK_RED: return d.nb_red;
+        case PK_RED: return (d.nb_red + RED_CLUSTER - 1) / RED_CLUSTER * RED_CLUSTER;
         case PK_DENSE: return (dense && !d.tc) ? d.nb_dm * d.nb_ds : 0;
         case PK_CSR: return d.kind == MEG_CSR_QUAD ? d.nb_csr : 0;
-        case PK_DTC: return (dense && d.tc) ? d.nb_tm * d.nb_ds : 0;
+        case PK_DTC: return (dense && d.tc) ? (int)tc_chunks_of(d) : 0;
         default: return d.kind == MEG_MEAS_STOCH ? d.nb_meas : 0;
     }
 }
@@ -146,7 +175,9 @@ GroupLaunch solo_launch(meg_solve_s* h) {
         g.tc_chunks = 1;
         g.tc_desc[0] = h->d_desc;
         g.tc_ns[0] = 1;
-        g.tc_blocks[0] = g.blocks[PK_DTC];
+        g.tc_T[0] = h->desc.tc_T;
+        g.tc_G[0] = h->desc.tc_G;
+        g.tc_npad[0] = h->desc.tc_npad;
         g.tc_maps[0] = h->solo_maps;
     }
     return g;
@@ -268,7 +299,7 @@ int64_t meg_footprint(int n, int r, int p, int precision, int kind) {
     if (n <= 0 || r <= 0 || p <= 0) return -1;
     const int64_t k = r + p;
     const int64_t ts = precision == MEG_FP64 ? 8 : 4;
-    const int64_t nb_red = (n + ROWS_RED - 1) / ROWS_RED;
+    const int64_t nb_red = (n + rows_red_for(n) - 1) / rows_red_for(n);
     const int64_t groups = (nb_red + RED_GROUP - 1) / RED_GROUP;
     int64_t b = 0;
     b += ts * (int64_t)n * (2 * r + 4 * k);
@@ -325,6 +356,7 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
     SolveDev& d = h->desc;
     d.n = n; d.r = r; d.k = h->k; d.kind = -1; d.prec = h->prec; d.q = q; d.mode = 0;
     d.eta = opt->eta; d.eps_a = opt->eps_a; d.eps_c = opt->eps_c; d.eps_pow = opt->eps_pow; d.seed = opt->seed;
+    d.log_nr = std::log((double)(n - r));
     compute_partition(h, d);
     const size_t ts = tsize(h->prec);
     const int k = h->k;
@@ -740,6 +772,44 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
         g->has_csr |= kind == MEG_CSR_QUAD;
         g->has_meas |= kind == MEG_MEAS_STOCH;
     }
+    // tensor-core solves: chunks of at most TC_MAXG solves, one stream-K launch
+    // each; offsets, chunk totals and grids go into both descriptor copies
+    // (the product reads the chunk's copy, k_combine the group's)
+    std::vector<int> tc_idx;
+    for (int i = 0; i < count; ++i)
+        if (blocks_of(descs[i], PK_DTC) > 0) tc_idx.push_back(i);
+    const int nch = ((int)tc_idx.size() + TC_MAXG - 1) / TC_MAXG;
+    if (nch > TC_MAX_CHUNKS) {
+        if (g->own_stream) cudaStreamDestroy(g->stream);
+        delete g;
+        return fail(MEG_ERR_INVALID_ARG, "meg_group_create: too many tensor-core solves in one group");
+    }
+    g->tc_maps.resize(nch);
+    for (int c = 0; c < nch; ++c) {
+        long long off = 0;
+        int nkb_max = 1, npad_max = 16;
+        const int first = c * TC_MAXG, cnt = std::min(TC_MAXG, (int)tc_idx.size() - first);
+        for (int j = 0; j < cnt; ++j) {
+            SolveDev& d = descs[tc_idx[first + j]];
+            d.off[PK_DTC] = (int)off;
+            off += tc_chunks_of(d);
+            nkb_max = std::max(nkb_max, d.tc_kpad / 64);
+            npad_max = std::max(npad_max, d.tc_npad);
+            g->tc_maps[c].a[j] = solves[tc_idx[first + j]]->solo_maps->a[0];
+            g->tc_maps[c].b[j] = solves[tc_idx[first + j]]->solo_maps->b[0];
+        }
+        const int G = tc_grid(off, nkb_max);
+        for (int j = 0; j < cnt; ++j) {
+            descs[tc_idx[first + j]].tc_T = off;
+            descs[tc_idx[first + j]].tc_G = G;
+        }
+        g->gl.tc_ns[c] = cnt;
+        g->gl.tc_T[c] = off;
+        g->gl.tc_G[c] = G;
+        g->gl.tc_npad[c] = npad_max;
+    }
+    std::vector<SolveDev> tcd;
+    for (int i : tc_idx) tcd.push_back(descs[i]);
     if (cudaMalloc((void**)&g->d_desc, sizeof(SolveDev) * count) != cudaSuccess) {
         if (g->own_stream) cudaStreamDestroy(g->stream);
         delete g;
@@ -757,31 +827,6 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
     for (int p = 0; p < PK_COUNT; ++p) g->gl.blocks[p] = tot[p];
     g->gl.prec = prec;
     g->gl.stream = g->stream;
-    // tensor-core solves: contiguous descriptor copies, chunks of at most TC_MAXG
-    std::vector<SolveDev> tcd;
-    std::vector<meg_solve_s*> tcs;
-    for (int i = 0; i < count; ++i)
-        if (blocks_of(descs[i], PK_DTC) > 0) { tcd.push_back(descs[i]); tcs.push_back(solves[i]); }
-    const int nch = ((int)tcd.size() + TC_MAXG - 1) / TC_MAXG;
-    if (nch > TC_MAX_CHUNKS) {
-        cudaFree(g->d_desc);
-        if (g->own_stream) cudaStreamDestroy(g->stream);
-        delete g;
-        return fail(MEG_ERR_INVALID_ARG, "meg_group_create: too many tensor-core solves in one group");
-    }
-    g->tc_maps.resize(nch);
-    for (int c = 0; c < nch; ++c) {
-        int off = 0;
-        const int first = c * TC_MAXG, cnt = std::min(TC_MAXG, (int)tcd.size() - first);
-        for (int j = 0; j < cnt; ++j) {
-            tcd[first + j].off[PK_DTC] = off;
-            off += blocks_of(tcd[first + j], PK_DTC);
-            g->tc_maps[c].a[j] = tcs[first + j]->solo_maps->a[0];
-            g->tc_maps[c].b[j] = tcs[first + j]->solo_maps->b[0];
-        }
-        g->gl.tc_ns[c] = cnt;
-        g->gl.tc_blocks[c] = off;
-    }
     if (!tcd.empty()) {
         if (cudaMalloc((void**)&g->d_tc_desc, sizeof(SolveDev) * tcd.size()) != cudaSuccess ||
             cudaMemcpy(g->d_tc_desc, tcd.data(), sizeof(SolveDev) * tcd.size(), cudaMemcpyHostToDevice) !=
@@ -845,8 +890,12 @@ meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch) {
 
 int meg_group_kernels_per_step(meg_group g) {
     if (!g) return -1;
-    // per product: gradient-part kernel(s) + combine + orth1 + orth2 (+ minibatch pass); plus begin
-    const int per = (g->has_dense ? 1 : 0) + (g->has_csr ? 1 : 0) + (g->has_meas ? 2 : 0) + 3;
+    // per product: the gradient-part kernels (one tensor-core launch per chunk of
+    // tensor-core solves, one FFMA launch for the other dense solves), CSR,
+    // the two minibatch passes, and combine / orth1 / orth2, each a row kernel
+    // followed by an island kernel; plus the begin kernel once per iteration
+    const int dense = g->gl.tc_chunks + (g->gl.blocks[PK_DENSE] > 0 ? 1 : 0);
+    const int per = dense + (g->has_csr ? 1 : 0) + (g->has_meas ? 2 : 0) + 6;
     return g->q * per + 1;
 }
 

@@ -41,6 +41,7 @@ enum SmallSlot : int {
     SM_RSS,            // CSR: max_i sum_j |R_ij| of the last gradient pass (bounds ||grad f||_2)
     SM_RESID_BOUND,    // MEAS: spectral estimate of the minibatch gradient (see k_meas_batch)
     SM_ETA,            // eta
+    SM_JSWEEPS,        // Jacobi sweeps of the last Rayleigh-Ritz step (diagnostic)
     SM_MU = 32,        // [32] mu of X_t
     SM_DCOEF = 64,     // [32] coefficients of V diag(.) V^T in M_t
     SM_SIGMA = 96,     // [32] Ritz values of the last Rayleigh-Ritz, unshifted
@@ -58,6 +59,8 @@ enum SmallSlot : int {
 enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_DTC = 4, PK_COUNT = 5 };
 
 #define RED_GROUP 16            // blocks per first-level group of a reduction
+#define ROWS_MAX 64             // rows per block of the row-reduction kernels, at most
+#define RED_CLUSTER 8           // row blocks of a thread-block cluster; one partial per cluster
 #define RED_MAX_ENTRIES 1536    // >= k(k+1)/2 + r k for k <= 32, r <= 30 (orth2: 528 + 960)
 
 // Device descriptor of one solve.  Read-only for kernels (state lives in the
@@ -73,6 +76,8 @@ struct SolveDev {
     int tc;              // 1: dense product on tcgen05 (bf16 data, n % 8 == 0)
     int nb_tm;           // tensor-core path: 128-row tiles
     int tc_npad, tc_kpad;// Wsp: (3k padded to 16) x (n padded to 64) bf16
+    int tc_G;            // tensor-core launch holding this solve: CTAs
+    long long tc_T;      //   and total K chunks (this solve's first chunk is off[PK_DTC])
     int off[PK_COUNT];   // first block of this solve in a grouped launch
     double* V;           // n x r   float64 in every mode: V of X_t
     double* Vn;          // n x r   float64: V of X_{t+1} being formed
@@ -99,6 +104,7 @@ struct SolveDev {
     int L;
     // schedule
     double eta, eps_a, eps_c, eps_pow;
+    double log_nr;       // log(n - r), used by the certificate
     uint64_t seed;
 };
 
@@ -111,6 +117,23 @@ __device__ __forceinline__ int find_solve(const SolveDev* sd, int ns, int kind, 
         if (sd[mid].off[kind] <= b) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Stream-K split of T work chunks over G CTAs: CTA c owns [start(c), start(c+1)),
+// start(c) = floor(c T / G); tc_cta_of(g) is the CTA owning chunk g (the last c
+// with start(c) <= g, i.e. ceil((g + 1) G / T) - 1).
+__host__ __device__ __forceinline__ long long tc_chunk_start(int c, int G, long long T) {
+    return (long long)c * T / G;
+}
+__host__ __device__ __forceinline__ int tc_cta_of(long long g, int G, long long T) {
+    return (int)(((g + 1) * G + T - 1) / T) - 1;
+}
+// partial slots of the 128-row tile mt of a tensor-core solve (one per CTA that touches it)
+__device__ __forceinline__ int tc_tile_slots(const SolveDev& s, int mt) {
+    const int nkb = s.tc_kpad / 64;
+    const long long t0 = s.off[PK_DTC] + (long long)mt * nkb;
+    return tc_cta_of(t0 + nkb - 1, s.tc_G, s.tc_T) - tc_cta_of(t0, s.tc_G, s.tc_T) + 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -205,7 +228,9 @@ struct GroupLaunch {
     int tc_chunks;
     const SolveDev* tc_desc[TC_MAX_CHUNKS];
     int tc_ns[TC_MAX_CHUNKS];
-    int tc_blocks[TC_MAX_CHUNKS];
+    long long tc_T[TC_MAX_CHUNKS];   // K chunks of the launch
+    int tc_G[TC_MAX_CHUNKS];         // CTAs of the launch
+    int tc_npad[TC_MAX_CHUNKS];      // largest N tile of the launch
     const TcMaps* tc_maps[TC_MAX_CHUNKS];
 };
 
