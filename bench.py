@@ -129,6 +129,13 @@ def gpu_solves(probs, device, stream):
     return solves, dense
 
 
+# DRAM bytes (read + write) of one k_dense_tc launch on this workload, from one
+# ncu capture of it (dram__bytes_read.sum + dram__bytes_write.sum; the summary
+# is kept with the other ncu summaries).  None whenever the kernel has changed
+# since that capture.
+DENSE_TC_TRAFFIC_BYTES = 272.804864e6 + 3.506944e6
+
+
 def algorithmic_bytes_dense_product():
     """Minimum HBM traffic of one grouped dense product Y = M W over the batch:
     M once (n^2 bf16) + W read + Y written (n k float32 each)."""
@@ -347,7 +354,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": kps * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
+                         "frac": achieved / hbm_peak, "traffic": DENSE_TC_TRAFFIC_BYTES,
                          "kernel": "grouped dense product k_dense_tc (bf16 tcgen05, TMA)",
                          "peak_kind": f"{peak_kind} burst copy bandwidth", "ms_per_launch": prod_ms,
                          "bytes_per_launch": alg},
