@@ -212,6 +212,180 @@ def torch_fp32_form(prob, device, iters: int):
     return iters / (e0.elapsed_time(e1) / 1e3)
 
 
+# --------------------------------------------------------------------------- serving
+SERVE_P, SERVE_Q, SERVE_TOL, SERVE_MAX_ITERS = 4, 2, 1e-6, 5000
+
+
+def serve_request_args(B, q):
+    """Server request for one trace entry (config-0 type: float64 dense, f* unknown,
+    plateau rule; config-3 type: bf16 measurements, f* = 0)."""
+    common = dict(n=q.n, r=q.r, p=SERVE_P, q=SERVE_Q, seed=17 + q.n, warm_start_products=40,
+                  tol=SERVE_TOL, max_iters=SERVE_MAX_ITERS)
+    if q.kind == 0:
+        return dict(kind=B.MEG_DENSE_QUAD, data=q.M, precision=B.MEG_FP64, eta=1.0, **common)
+    return dict(kind=B.MEG_MEAS_STOCH, data=q.A_bits, y=q.y, L=q.L, precision=B.MEG_MIXED_BF16,
+                eta=1.0 / (4.0 * (1.0 + q.n / q.L)), fstar=0.0, **common)
+
+
+def run_serving(trace, budget_bytes: int, max_active: int = 1024):
+    """Replay the trace's Poisson arrivals into meg_server; returns the summary."""
+    import threading
+    from paper_2012_10469_gb300 import binding as B
+    srv = B.Server(budget_bytes, max_active=max_active, check_every=10, meas_check_every=50)
+    results, errors = [], []
+
+    def submitter():
+        try:
+            base = srv.meg_server_now()
+            for q in trace:
+                delay = base + q.t - srv.meg_server_now()
+                if delay > 0:
+                    time.sleep(delay)
+                srv.meg_server_submit(**serve_request_args(B, q))
+        except Exception as ex:  # surfaced below
+            errors.append(ex)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    deadline = time.time() + 900
+    while len(results) < len(trace) and time.time() < deadline and not errors:
+        for rec, _V, _mu, _s in srv.meg_server_poll(max_out=512, timeout_ms=20):
+            results.append(rec)
+    th.join()
+    srv.meg_server_destroy()
+    if errors:
+        raise errors[0]
+    lat = np.array([r["t_done"] - r["t_submit"] for r in results])
+    t_first = min(r["t_submit"] for r in results)
+    t_last = max(r["t_done"] for r in results)
+    st = [r["status"] for r in results]
+    its = np.array([r["iters"] for r in results])
+    return {
+        "requests": len(trace), "finished": len(results),
+        "solves_per_s": len(results) / (t_last - t_first),
+        "latency_p50_ms": 1e3 * float(np.percentile(lat, 50)),
+        "latency_p99_ms": 1e3 * float(np.percentile(lat, 99)),
+        "iters_p50": float(np.percentile(its, 50)), "iters_p99": float(np.percentile(its, 99)),
+        "converged": int(sum(1 for x in st if x == 0)),
+        "hit_max_iters": int(sum(1 for x in st if x == 5)),
+        "failed": int(sum(1 for x in st if x not in (0, 5))),
+        "makespan_s": t_last - t_first,
+    }
+
+
+def torch_fp32_solve(q, device, max_iters=SERVE_MAX_ITERS, tol=SERVE_TOL):
+    """One serving request with plain float32 torch ops (cuBLAS/cuSOLVER), the
+    same algorithm, warm start and stopping rule, no batching, no graphs."""
+    import torch
+    n, r, k = q.n, q.r, q.r + SERVE_P
+    gen = torch.Generator(device="cpu").manual_seed(q.n)
+    dense = q.kind == 0
+    if dense:
+        M = torch.from_numpy(q.M.astype(np.float32)).to(device)
+        G0 = M
+        eta, check = 1.0, 10
+    else:
+        A = torch.from_numpy(q.A.astype(np.float32)).to(device)
+        y = torch.from_numpy(q.y.astype(np.float32)).to(device)
+        G0 = (2.0 / A.shape[0]) * (A.T @ (y[:, None] * A))
+        eta, check = 1.0 / (4.0 * (1.0 + n / q.L)), 50
+    lam, U = torch.linalg.eigh(0.5 * (G0 + G0.T))
+    lam, V = lam.flip(0)[:r], U.flip(1)[:, :r]
+    srt, _ = torch.sort(lam, descending=True)           # simplex projection of lam
+    css = torch.cumsum(srt, 0) - 1.0
+    ind = torch.arange(1, r + 1, device=device, dtype=torch.float32)
+    rho = int(torch.nonzero(srt - css / ind > 0).max()) + 1
+    lam = torch.clamp(lam - css[rho - 1] / rho, min=0.0)
+    eps0 = 0.8 / 121.0
+    mu = (1 - eps0) * lam + eps0 / n
+    s = eps0 / n
+
+    def fval(V, mu, s):
+        if dense:
+            X = (V * (mu - s)) @ V.T + s * torch.eye(n, device=device)
+            return 0.5 * float(((X - M) ** 2).sum())
+        P = A @ V
+        qv = (P * P) @ (mu - s) + s * (A * A).sum(1)
+        return float(((qv - y) ** 2).mean())
+
+    def grad_apply(V, mu, s, W):
+        if dense:
+            return V @ ((mu - s)[:, None] * (V.T @ W)) + s * W - M @ W, None
+        idx = torch.randint(0, A.shape[0], (q.L,), device=device)
+        Ab = A[idx]
+        P = Ab @ V
+        res = (P * P) @ (mu - s) + s * (Ab * Ab).sum(1) - y[idx]
+        return (2.0 / q.L) * (Ab.T @ (res[:, None] * (Ab @ W))), res
+
+    f1 = fval(V, mu, s)
+    f_prev, f = f1, f1
+    W, _ = torch.linalg.qr(torch.cat([V, torch.randn(n, SERVE_P, generator=gen).to(device)], 1))
+    gb = 1.25 * math.sqrt(2 * f1) if dense else 1.0
+    it = 0
+    while it < max_iters:
+        for _ in range(check):
+            it += 1
+            eps = 0.8 / (it + 11.0) ** 2
+            logs = math.log(s)
+            dlog = torch.log(mu) - logs
+            shift = min(logs, float(torch.log(mu).min())) - eta * gb
+            for j in range(SERVE_Q):
+                GW, res = grad_apply(V, mu, s, W)
+                Z = V @ (dlog[:, None] * (V.T @ W)) + (logs - shift) * W - eta * GW
+                if j < SERVE_Q - 1:
+                    W, _ = torch.linalg.qr(Z)
+            if res is not None:
+                gb = float((2.0 / q.L) * res.abs().max() * (A[:1] * A[:1]).sum() * (1 + math.sqrt(q.L / n)) ** 2)
+            H = W.T @ Z
+            th, Qm = torch.linalg.eigh(0.5 * (H + H.T))
+            th, Qm = th.flip(0), Qm.flip(1)
+            sig = th + shift
+            mu = (1 - eps) * torch.exp(sig[:r] - torch.logsumexp(sig[:r], 0))
+            s = eps / (n - r)
+            V = W @ Qm[:, :r]
+            W, _ = torch.linalg.qr(Z @ Qm)
+            if it >= max_iters:
+                break
+        f_prev, f = f, fval(V, mu, s)
+        if dense:
+            gb = 1.25 * math.sqrt(2 * max(f, 0.0))
+            if f1 - f > 0 and f_prev - f <= tol * (f1 - f):
+                return it, True
+        elif f <= tol * f1:
+            return it, True
+    return it, False
+
+
+def torch_fp32_serve_sample(trace, device, seconds: float):
+    """The plain float32 form on the trace's first requests, one at a time, for
+    about `seconds`; latency from a FIFO replay of the arrivals with the measured
+    service times."""
+    import torch
+    torch_fp32_solve(trace[0], device, max_iters=20)        # load cuBLAS/cuSOLVER
+    torch.cuda.synchronize()
+    serv, its, t_all = [], [], time.perf_counter()
+    for q in trace:
+        t0 = time.perf_counter()
+        it, _ok = torch_fp32_solve(q, device)
+        torch.cuda.synchronize()
+        serv.append(time.perf_counter() - t0)
+        its.append(it)
+        if time.perf_counter() - t_all > seconds:
+            break
+    done, lat = 0.0, []
+    for q, sv in zip(trace, serv):
+        done = max(done, q.t) + sv
+        lat.append(done - q.t)
+    return {"requests": len(serv), "solves_per_s": len(serv) / sum(serv),
+            "service_p50_ms": 1e3 * float(np.percentile(serv, 50)),
+            "service_p99_ms": 1e3 * float(np.percentile(serv, 99)),
+            "latency_p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "latency_p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "iters_p50": float(np.percentile(its, 50)),
+            "what": "same algorithm and stopping rule in plain float32 torch ops, one request at a time "
+                    "(FIFO replay of the same arrivals for latency), on the trace's first requests"}
+
+
 # --------------------------------------------------------------------------- main
 def run_reference(args):
     """The oracle on the workload: each step is one float64 low-rank MEG
@@ -341,6 +515,20 @@ def run_gpu(args):
         except Exception as ex:  # reported, never fatal
             single = {"error": repr(ex)}
         cpu_rate, cores, it, el = oracle_sample(args.cpu_seconds)
+        serving = None
+        if args.serve_requests > 0:
+            try:
+                import synth
+                trace = synth.serving_trace(args.serve_requests, args.serve_rate, 2000)
+                free, _tot = torch.cuda.mem_get_info()
+                serving = run_serving(trace, budget_bytes=int(free * 0.6))
+                serving["arrival_rate_per_s"] = args.serve_rate
+                serving["workload"] = ("Poisson arrivals, n log-uniform [64, 1024], r uniform 1..8, 50/50 "
+                                       "dense quadratic (float64, noise 1e-4, plateau rule) / measurements "
+                                       "(bf16 A, m=50000, L=256, f*=0), tol 1e-6, max_iters 5000, p=4, q=2")
+                serving["plain_fp32_form"] = torch_fp32_serve_sample(trace, device, args.serve_fp32_seconds)
+            except Exception as ex:  # reported, never fatal
+                serving = {"error": repr(ex)[:300]}
         line = {
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -363,6 +551,7 @@ def run_gpu(args):
                                        f"n={N} instance in {el:.1f} s"},
             "fp32_torch_form": fp32_form,
             "single_solve": single,
+            "serving": serving,
         }
     group.meg_group_destroy()
     for s_ in solves:
@@ -401,6 +590,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-requests", type=int, default=2000, help="serving trace length (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=500.0, help="mean arrivals per second")
+    ap.add_argument("--serve-fp32-seconds", type=float, default=30.0,
+                    help="time spent on the plain float32 form's sample of the trace")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -221,6 +221,91 @@ meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch);
 /* Number of kernels one meg_group_step iteration launches. */
 int meg_group_kernels_per_step(meg_group g);
 
+/* meg_group_launch -- enqueue `nsteps` iterations of every member like
+ * meg_group_step, but as plain kernel launches (no graph capture), for
+ * groups that live only a few steps.  Same results. */
+meg_status meg_group_launch(meg_group g, int nsteps);
+
+/* meg_group_objective -- f(X_t) of every member (meg_objective's accurate
+ * pass, one launch for the group), written to host f[count] in member
+ * order.  Synchronises the group's stream. */
+meg_status meg_group_objective(meg_group g, double* f);
+
+/*
+ * Serving: continuous batching of independent solves on one GPU.  The
+ * paper has no counterpart (it runs one solve at a time); each request
+ * is an ordinary run of Algorithm 2 from X_1 until its stopping rule.
+ * A worker thread of the library admits requests in submission order
+ * when a slot is free and their device footprint -- meg_footprint plus a
+ * copy of the request's objective data -- fits the memory budget, groups
+ * the admitted solves by (precision, q, objective family), runs each
+ * group `check_every` iterations at a time on its own stream (groups
+ * overlap on the device), evaluates every member's f after each such
+ * tick, and retires members whose stopping rule holds:
+ *   f* known (finite): (f(X_t) - f*) <= tol (f(X_1) - f*)   (relative gap);
+ *   f* unknown (NaN):  f(X_{t-c}) - f(X_t) <= tol (f(X_1) - f(X_t)), c the
+ *                      check interval (the iteration's progress has stalled
+ *                      at tol of the progress made);
+ *   t = max_iters:     status MEG_ERR_NOT_CONVERGED.
+ * Results do not depend on which other requests share the GPU: grouped
+ * kernels compute each member exactly as it would run alone.
+ */
+typedef struct meg_server_s* meg_server;
+
+typedef struct {
+    int64_t hbm_budget;       /* device bytes the admitted requests may hold */
+    int max_active;           /* most requests admitted at once, >= 1 */
+    int check_every;          /* iterations per tick (objective check), dense */
+    int meas_check_every;     /* same for MEAS_STOCH requests (the full
+                                 objective reads all m measurements) */
+} meg_server_options;
+
+/* One request.  Host pointers (data, y, V0, lam0) are copied when the
+ * request is admitted and must stay valid until its result is returned;
+ * out_V (n x r), out_mu (r) and out_s (1) are written before the result
+ * is returned (each may be NULL). */
+typedef struct {
+    meg_options opt;          /* sizes, precision, schedule, seed; stream ignored */
+    int kind;                 /* MEG_DENSE_QUAD, MEG_LINEAR or MEG_MEAS_STOCH */
+    const void* data;         /* host: dense n x n, or A m x n (MEAS_STOCH); element
+                                 type by precision as in meg_objective_desc */
+    const double* y;          /* host: y[m] (MEAS_STOCH) */
+    int64_t m;
+    int L;
+    int warm_start_products;  /* > 0: X_0 by meg_warm_start(products); 0: V0, lam0 */
+    const double* V0;
+    const double* lam0;
+    double fstar;             /* optimal value, or NaN when unknown */
+    double tol;               /* > 0 */
+    int max_iters;            /* >= 1 */
+    double* out_V;
+    double* out_mu;
+    double* out_s;
+} meg_request;
+
+typedef struct {
+    uint64_t id;
+    meg_status status;        /* MEG_OK, MEG_ERR_NOT_CONVERGED, or the failure */
+    int iters;                /* iterations run */
+    double f1, f;             /* f(X_1) and f at the last check */
+    double t_submit, t_admit, t_done;   /* seconds on the server clock */
+} meg_result;
+
+/* Errors: MEG_ERR_INVALID_ARG (non-positive budget, slots or intervals). */
+meg_status meg_server_create(const meg_server_options* opt, meg_server* out);
+/* Queue a request; *id receives its id.  MEG_ERR_OOM when the request
+ * alone exceeds the budget, MEG_ERR_INVALID_ARG for a malformed one. */
+meg_status meg_server_submit(meg_server s, const meg_request* rq, uint64_t* id);
+/* Move up to max_out finished results into out (oldest first), waiting up
+ * to timeout_ms for at least one; *n_out receives the count. */
+meg_status meg_server_poll(meg_server s, meg_result* out, int max_out, int* n_out, int timeout_ms);
+/* Requests submitted and finished so far. */
+meg_status meg_server_counts(meg_server s, int64_t* submitted, int64_t* finished);
+/* The server clock (seconds since meg_server_create). */
+double meg_server_now(meg_server s);
+/* Stop the worker and free everything; unfinished requests are dropped. */
+meg_status meg_server_destroy(meg_server s);
+
 /*
  * meg_objective_dense_noalloc -- f(X) = 1/2 ||X - M||_F^2 for
  * X = V diag(mu) V^T + s (I - V V^T), computed without allocating any

@@ -41,6 +41,23 @@ class meg_objective_desc(C.Structure):
                 ("A", C.c_void_p), ("y", C.c_void_p), ("m", C.c_int64), ("L", C.c_int)]
 
 
+class meg_server_options(C.Structure):
+    _fields_ = [("hbm_budget", C.c_int64), ("max_active", C.c_int), ("check_every", C.c_int),
+                ("meas_check_every", C.c_int)]
+
+
+class meg_request(C.Structure):
+    _fields_ = [("opt", meg_options), ("kind", C.c_int), ("data", C.c_void_p), ("y", C.c_void_p),
+                ("m", C.c_int64), ("L", C.c_int), ("warm_start_products", C.c_int), ("V0", C.c_void_p),
+                ("lam0", C.c_void_p), ("fstar", C.c_double), ("tol", C.c_double), ("max_iters", C.c_int),
+                ("out_V", C.c_void_p), ("out_mu", C.c_void_p), ("out_s", C.c_void_p)]
+
+
+class meg_result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int), ("iters", C.c_int), ("f1", C.c_double),
+                ("f", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
 class MegError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"status {status}: {msg}")
@@ -81,6 +98,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_group_kernels_per_step": (C.c_int, [H]),
         "meg_objective_dense_noalloc": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_double, C.c_int, C.c_int,
                                                   C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+        "meg_group_launch": (C.c_int, [H, C.c_int]),
+        "meg_group_objective": (C.c_int, [H, _P(C.c_double)]),
+        "meg_server_create": (C.c_int, [_P(meg_server_options), _P(H)]),
+        "meg_server_submit": (C.c_int, [H, _P(meg_request), _P(C.c_uint64)]),
+        "meg_server_poll": (C.c_int, [H, _P(meg_result), C.c_int, _P(C.c_int), C.c_int]),
+        "meg_server_counts": (C.c_int, [H, _P(C.c_int64), _P(C.c_int64)]),
+        "meg_server_now": (C.c_double, [H]),
+        "meg_server_destroy": (C.c_int, [H]),
         "meg_state_size": (C.c_int64, [H]),
         "meg_get_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
         "meg_set_state": (C.c_int, [H, C.c_void_p, C.c_int64]),
@@ -99,7 +124,7 @@ def exported_symbols():
     hdr = os.path.join(os.path.dirname(HERE), "include", "meg.h")
     with open(hdr) as f:
         text = f.read()
-    return sorted(set(re.findall(r"^\s*(?:meg_status|const char\*|int64_t|int)\s+(meg_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:meg_status|const char\*|int64_t|int|double)\s+(meg_\w+)\s*\(", text, re.M)))
 
 
 def _check(status: int, what: str):
@@ -248,6 +273,14 @@ class Group:
     def meg_group_kernels_per_step(self) -> int:
         return int(load().meg_group_kernels_per_step(self.g))
 
+    def meg_group_launch(self, nsteps: int = 1):
+        _check(load().meg_group_launch(self.g, nsteps), "meg_group_launch")
+
+    def meg_group_objective(self) -> np.ndarray:
+        f = np.empty(len(self.solves), dtype=np.float64)
+        _check(load().meg_group_objective(self.g, _f64p(f)), "meg_group_objective")
+        return f
+
     def meg_group_destroy(self):
         if getattr(self, "g", None):
             load().meg_group_destroy(self.g)
@@ -256,5 +289,86 @@ class Group:
     def __del__(self):
         try:
             self.meg_group_destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (meg_server).  Host arrays of a
+    request are kept alive here until its result has been polled."""
+
+    def __init__(self, hbm_budget: int, max_active: int = 256, check_every: int = 10,
+                 meas_check_every: int = 50):
+        lib = load()
+        opt = meg_server_options(hbm_budget=int(hbm_budget), max_active=max_active, check_every=check_every,
+                                 meas_check_every=meas_check_every)
+        h = C.c_void_p()
+        _check(lib.meg_server_create(C.byref(opt), C.byref(h)), "meg_server_create")
+        self.h = h
+        self._live = {}
+
+    def meg_server_submit(self, kind: int, n: int, r: int, data: np.ndarray, p: int = 4, q: int = 2,
+                          precision: int = MEG_FP64, eta: float = 1.0, eps=(0.8, 10.0, 2.0), seed: int = 1,
+                          y: Optional[np.ndarray] = None, L: int = 0, warm_start_products: int = 40,
+                          V0=None, lam0=None, fstar: float = float("nan"), tol: float = 1e-6,
+                          max_iters: int = 5000) -> int:
+        """data: host array (dense n x n, or A m x n) in the precision's storage
+        type (float64, float32, or uint16 bfloat16 bits); y: float64 (m)."""
+        data = np.ascontiguousarray(data)
+        keep = [data]
+        opt = meg_options(n=n, r=r, p=p, q=q, precision=precision, eta=eta, eps_a=eps[0], eps_c=eps[1],
+                          eps_pow=eps[2], max_iters=max_iters, tol=tol, seed=seed, stream=None)
+        outV = np.zeros((n, r), dtype=np.float64)
+        outmu = np.zeros(r, dtype=np.float64)
+        outs = np.zeros(1, dtype=np.float64)
+        keep += [outV, outmu, outs]
+        rq = meg_request(opt=opt, kind=kind, data=data.ctypes.data, y=None, m=0, L=L,
+                         warm_start_products=warm_start_products, V0=None, lam0=None, fstar=fstar, tol=tol,
+                         max_iters=max_iters, out_V=outV.ctypes.data, out_mu=outmu.ctypes.data,
+                         out_s=outs.ctypes.data)
+        if y is not None:
+            y = np.ascontiguousarray(y, dtype=np.float64)
+            keep.append(y)
+            rq.y = y.ctypes.data
+            rq.m = int(data.shape[0])
+        if V0 is not None:
+            V0 = np.ascontiguousarray(V0, dtype=np.float64)
+            lam0 = np.ascontiguousarray(lam0, dtype=np.float64)
+            keep += [V0, lam0]
+            rq.V0, rq.lam0 = V0.ctypes.data, lam0.ctypes.data
+        rid = C.c_uint64()
+        _check(load().meg_server_submit(self.h, C.byref(rq), C.byref(rid)), "meg_server_submit")
+        self._live[rid.value] = (keep, outV, outmu, outs)
+        return rid.value
+
+    def meg_server_poll(self, max_out: int = 256, timeout_ms: int = 0):
+        """Finished requests: list of (meg_result fields as a dict, V, mu, s)."""
+        buf = (meg_result * max_out)()
+        cnt = C.c_int()
+        _check(load().meg_server_poll(self.h, buf, max_out, C.byref(cnt), timeout_ms), "meg_server_poll")
+        out = []
+        for i in range(cnt.value):
+            r = buf[i]
+            rec = {f: getattr(r, f) for f, _ in meg_result._fields_}
+            _, V, mu, s = self._live.pop(r.id)
+            out.append((rec, V, mu, float(s[0])))
+        return out
+
+    def meg_server_counts(self):
+        a, b = C.c_int64(), C.c_int64()
+        _check(load().meg_server_counts(self.h, C.byref(a), C.byref(b)), "meg_server_counts")
+        return a.value, b.value
+
+    def meg_server_now(self) -> float:
+        return float(load().meg_server_now(self.h))
+
+    def meg_server_destroy(self):
+        if getattr(self, "h", None):
+            load().meg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.meg_server_destroy()
         except Exception:
             pass

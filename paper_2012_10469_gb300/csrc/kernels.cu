@@ -532,6 +532,10 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
                 const T* Ys = (const T*)s.Ys;
                 const int np = s.tc ? tc_tile_slots(s, i / 128) : s.nb_ds;   // slots in order
                 for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
+            } else if (s.kind == MEG_MEAS_STOCH) {
+                const T* Ys = (const T*)s.Ys;
+                const int np = meas_chunks(s.nb_meas);                      // chunks in order
+                for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
             } else {
                 y = ((const T*)s.Y)[(size_t)i * k + j];
             }
@@ -1125,125 +1129,192 @@ template <> __device__ __forceinline__ float load_a<float>(const void* A, size_t
     return __uint_as_float(((unsigned)b) << 16);
 }
 
-// one block per batch element b: r_b = a^T X a - y (mode 0) or -y (mode 1),
-// ||a||^2 and T_b = a^T W (k values)
+// Minibatch pass, one warp per batch row b (MB_ROWS rows per block):
+// r_b = a^T X a - y (mode 0) or -y (mode 1, the warm start's -grad f(0)),
+// ||a||^2 and T_b = a^T W (k values).  V and W are staged MB_TILE rows at a
+// time in shared memory in the storage type (padded rows: no bank
+// conflicts) and shared by the block's rows; lanes stride the row's
+// elements, so each load of a is coalesced.  The last block of the solve
+// turns the per-block partial bounds into the shift bound.
+// one warp's batch row: products of a with the B staged columns of V (zero
+// beyond r) and of W (zero beyond k); B = k_bucket(k) >= k > r
+template <typename T, int B>
+__device__ __forceinline__ void meas_batch_row(const SolveDev& s, int64_t idx, bool active, bool warm, T* sV, T* sW,
+                                               T (&av)[MEG_KMAX], T (&aw)[MEG_KMAX], T& aa) {
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x, lane = tid & 31;
+    const double* V = s.V;
+    const T* W = (const T*)s.W;
+    for (int i0 = 0; i0 < n; i0 += MB_TILE) {
+        const int tn = min(MB_TILE, n - i0);
+        __syncthreads();
+        if (!warm)
+            for (int e = tid; e < tn * B; e += NT) {
+                const int j = e / B, l = e % B;
+                sV[j * (B + 1) + l] = l < r ? (T)V[(size_t)(i0 + j) * r + l] : (T)0;
+            }
+        for (int e = tid; e < tn * B; e += NT) {
+            const int j = e / B, c = e % B;
+            sW[j * (B + 1) + c] = c < k ? W[(size_t)(i0 + j) * k + c] : (T)0;
+        }
+        __syncthreads();
+        if (active) {
+            for (int ii = lane; ii < tn; ii += 32) {
+                const T a = load_a<T>(s.A, (size_t)idx * n + i0 + ii);
+                aa += a * a;
+                if (!warm) {
+#pragma unroll
+                    for (int l = 0; l < B; ++l) av[l] += a * sV[ii * (B + 1) + l];
+                }
+#pragma unroll
+                for (int c = 0; c < B; ++c) aw[c] += a * sW[ii * (B + 1) + c];
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) aa += __shfl_xor_sync(0xffffffffu, aa, o);
+#pragma unroll
+    for (int c = 0; c < B; ++c)
+        for (int o = 16; o > 0; o >>= 1) {
+            aw[c] += __shfl_xor_sync(0xffffffffu, aw[c], o);
+            if (!warm) av[c] += __shfl_xor_sync(0xffffffffu, av[c], o);
+        }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) {
     const int si = find_solve(sds, ns, PK_MEAS, blockIdx.x);
     const SolveDev& s = sds[si];
-    const int b = blockIdx.x - s.off[PK_MEAS];
-    if (b < 0 || b >= s.nb_meas) return;
-    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const int lb = blockIdx.x - s.off[PK_MEAS];
+    const int Lb = s.nb_meas, nblk = (Lb + MB_ROWS - 1) / MB_ROWS;
+    if (lb < 0 || lb >= nblk) return;
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool warm = (s.mode == 1);
-    const int64_t idx = warm ? (int64_t)b
-        : (int64_t)(splitmix64(s.seed + ((uint64_t)s.sm[SM_T] * (uint64_t)s.L + (uint64_t)b + 1ull) *
-                               0x9E3779B97F4A7C15ull) % (uint64_t)s.m);
-    const double* V = s.V;
-    const T* W = (const T*)s.W;
-    T acc[MEG_RMAX + 1 + MEG_KMAX];
-    const int nacc = r + 1 + k;
-    for (int c = 0; c < nacc; ++c) acc[c] = 0;
-    for (int i = tid; i < n; i += NT) {
-        T a = load_a<T>(s.A, (size_t)idx * n + i);
-        if (!warm)
-            for (int l = 0; l < r; ++l) acc[l] += a * (T)V[(size_t)i * r + l];
-        acc[r] += a * a;
-        for (int c = 0; c < k; ++c) acc[r + 1 + c] += a * W[(size_t)i * k + c];
+    const int b = lb * MB_ROWS + warp;
+    const bool active = b < Lb;
+    int64_t idx = 0;
+    if (active)
+        idx = warm ? (int64_t)b
+                   : (int64_t)(splitmix64(s.seed + ((uint64_t)s.sm[SM_T] * (uint64_t)s.L + (uint64_t)b + 1ull) *
+                                                       0x9E3779B97F4A7C15ull) %
+                               (uint64_t)s.m);
+    __shared__ T sV[MB_TILE * (MEG_KMAX + 1)];
+    __shared__ T sW[MB_TILE * (MEG_KMAX + 1)];
+    T av[MEG_KMAX], aw[MEG_KMAX], aa = 0;
+#pragma unroll
+    for (int c = 0; c < MEG_KMAX; ++c) { av[c] = 0; aw[c] = 0; }
+    switch (k_bucket(k)) {
+        case 8: meas_batch_row<T, 8>(s, idx, active, warm, sV, sW, av, aw, aa); break;
+        case 16: meas_batch_row<T, 16>(s, idx, active, warm, sV, sW, av, aw, aa); break;
+        default: meas_batch_row<T, 32>(s, idx, active, warm, sV, sW, av, aw, aa); break;
     }
-    __shared__ double red[NT / 32][MEG_RMAX + 1 + MEG_KMAX];
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int c = 0; c < nacc; ++c) {
-        double v = (double)acc[c];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) red[warp][c] = v;
-    }
-    __syncthreads();
-    if (tid < nacc) {
-        double v = 0.0;
-        for (int w = 0; w < NT / 32; ++w) v += red[w][tid];
-        red[0][tid] = v;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const double sv = warm ? 0.0 : s.sm[SM_S];
-        double q = sv * red[0][r];
-        if (!warm)
-            for (int l = 0; l < r; ++l) q += (s.sm[SM_MU + l] - sv) * red[0][l] * red[0][l];
-        const double res = q - s.y[idx];
-        const int Lb = s.nb_meas;
-        double* sc = s.meas;              // [Lb] residual, [Lb] ||a||^2, [Lb x 32] T_b
-        sc[b] = res;
-        sc[Lb + b] = red[0][r];
-        if (!warm) s.bidx[b] = (int)idx;
-        __threadfence();
-        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
-        unsigned prev = atomicAdd(c, 1u);
-        if (prev == (unsigned)(Lb - 1)) {
-            *c = 0u;
+    double* sc = s.meas;              // [Lb] residual, [Lb] ||a||^2, [Lb x 32] T_b, [nblk] bounds
+    __shared__ double bpart[MB_ROWS];
+    if (lane == 0) {
+        double contrib = 0.0;
+        if (active) {
+            const double sv = warm ? 0.0 : s.sm[SM_S];
+            double q = sv * (double)aa;
+            if (!warm)
+#pragma unroll
+                for (int l = 0; l < MEG_RMAX; ++l)
+                    if (l < r) q += (s.sm[SM_MU + l] - sv) * (double)av[l] * (double)av[l];
+            const double res = q - s.y[idx];
+            sc[b] = res;
+            sc[Lb + b] = (double)aa;
+#pragma unroll
+            for (int c = 0; c < MEG_KMAX; ++c)
+                if (c < k) sc[2 * (size_t)Lb + (size_t)b * MEG_KMAX + c] = (double)aw[c];
+            if (!warm) s.bidx[b] = (int)idx;
             // Minibatch (mode 0): the L vectors a_b are nearly orthogonal, so the
             // eigenvalues of (2/L) sum r_b a_b a_b^T are close to (2/L) r_b ||a_b||^2;
-            // estimate ||grad||_2 by (2/L) max_b |r_b| ||a_b||^2 (1 + sqrt(L/n))^2.
-            // The estimate only sets the shift (convergence speed); Rayleigh-Ritz is exact.
+            // ||grad||_2 is estimated by (2/L) max_b |r_b| ||a_b||^2 (1 + sqrt(L/n))^2.
             // Warm start (mode 1, r_b = -y_b): lambda_min(-grad f(0)) >= -(2/m) sum_{y<0} |y| ||a||^2.
-            double bound = 0.0;
-            if (warm) {
-                for (int q2 = 0; q2 < Lb; ++q2) {
-                    double rb = __ldcg(sc + q2);
-                    if (rb > 0.0) bound += rb * __ldcg(sc + Lb + q2);
-                }
-                bound *= 2.0 / (double)Lb;
-            } else {
-                for (int q2 = 0; q2 < Lb; ++q2) bound = fmax(bound, fabs(__ldcg(sc + q2)) * __ldcg(sc + Lb + q2));
-                const double f = 1.0 + sqrt((double)Lb / (double)n);
-                bound *= 2.0 / (double)Lb * f * f;
-            }
-            s.sm[SM_RESID_BOUND] = bound;
+            contrib = warm ? (res > 0.0 ? res * (double)aa : 0.0) : fabs(res) * (double)aa;
         }
+        bpart[warp] = contrib;
     }
-    if (tid < k) s.meas[2 * (size_t)s.nb_meas + (size_t)b * MEG_KMAX + tid] = red[0][r + 1 + tid];
+    __syncthreads();
+    __shared__ int am_last;
+    if (tid == 0) {
+        double v = 0.0;
+        for (int w = 0; w < MB_ROWS; ++w) v = warm ? v + bpart[w] : fmax(v, bpart[w]);
+        sc[(size_t)Lb * (2 + MEG_KMAX) + lb] = v;
+        __threadfence();
+        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
+        am_last = (atomicAdd(c, 1u) == (unsigned)(nblk - 1));
+        if (am_last) *c = 0u;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    // last block: combine the per-block bounds (fixed order per thread, then a fixed tree)
+    __shared__ double red[NT];
+    const double* bp = sc + (size_t)Lb * (2 + MEG_KMAX);
+    double v = 0.0;
+    for (int q2 = tid; q2 < nblk; q2 += NT) v = warm ? v + __ldcg(bp + q2) : fmax(v, __ldcg(bp + q2));
+    red[tid] = v;
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+        if (tid < h) red[tid] = warm ? red[tid] + red[tid + h] : fmax(red[tid], red[tid + h]);
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double bound = red[0];
+        if (warm) {
+            bound *= 2.0 / (double)Lb;
+        } else {
+            const double f = 1.0 + sqrt((double)Lb / (double)n);
+            bound *= 2.0 / (double)Lb * f * f;
+        }
+        s.sm[SM_RESID_BOUND] = bound;
+    }
 }
 
-// Y = (2/L) sum_b r_b a_b (a_b^T W): one block per 64 rows of Y.
+// Y = (2/Lb) sum_b r_b a_b (a_b^T W): block = MA_ROWS rows of Y times one chunk
+// of the batch.  Thread (row i, column group of 8) accumulates over the
+// chunk's rows; a warp reads 32 consecutive elements of a row of A per step,
+// and the scaled r_b T_b are staged in shared memory (broadcast reads).
+// Chunk c's partial goes to slot c of Ys; k_combine sums the slots in order.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_meas_apply(const SolveDev* sds, int ns) {
-    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    constexpr int CH = sizeof(T) == 8 ? 128 : 256;        // staged batch rows (shared memory)
+    const int si = find_solve(sds, ns, PK_MAP, blockIdx.x);
     const SolveDev& s = sds[si];
-    const int lb = blockIdx.x - s.off[PK_RED];
-    if (lb < 0 || lb >= s.nb_red || s.kind != MEG_MEAS_STOCH) return;
+    const int lb = blockIdx.x - s.off[PK_MAP];
     const int n = s.n, k = s.k, tid = threadIdx.x;
-    const int row0 = lb * s.rows_red, row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    const int Lb = s.nb_meas, nch = meas_chunks(Lb);
+    const int ntile = (n + MA_ROWS - 1) / MA_ROWS;
+    if (lb < 0 || lb >= ntile * nch || s.kind != MEG_MEAS_STOCH) return;
+    const int tile = lb % ntile, ch = lb / ntile;
+    const int b_lo = (int)((int64_t)ch * Lb / nch), b_hi = (int)((int64_t)(ch + 1) * Lb / nch);
     const bool warm = (s.mode == 1);
-    const int Lb = s.nb_meas;
     const double scale = 2.0 / (double)Lb;
     const double* sc = s.meas;
-    __shared__ T Sb[64][MEG_KMAX];
+    const int i = tile * MA_ROWS + (tid & (MA_ROWS - 1)), cg = tid / MA_ROWS;     // 4 groups x 8 columns
+    __shared__ T S[CH][MEG_KMAX + 1];
+    __shared__ int sidx[CH];
     T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const int nout = nr * k;
-    for (int b0 = 0; b0 < Lb; b0 += 64) {
-        const int bn = min(64, Lb - b0);
+    for (int b0 = b_lo; b0 < b_hi; b0 += CH) {
+        const int bn = min(CH, b_hi - b0);
         __syncthreads();
         for (int e = tid; e < bn * k; e += NT) {
-            int bb = e / k, c = e % k;
-            Sb[bb][c] = (T)(scale * sc[b0 + bb] * sc[2 * (size_t)Lb + (size_t)(b0 + bb) * MEG_KMAX + c]);
+            const int bb = e / k, c = e % k;
+            S[bb][c] = (T)(scale * sc[b0 + bb] * sc[2 * (size_t)Lb + (size_t)(b0 + bb) * MEG_KMAX + c]);
         }
+        for (int e = tid; e < bn; e += NT) sidx[e] = warm ? b0 + e : s.bidx[b0 + e];
         __syncthreads();
-        for (int q = 0; q < 8; ++q) {
-            int o = tid + q * NT;
-            if (o >= nout) break;
-            int i = row0 + o / k, c = o % k;
-            T a2 = acc[q];
+        if (i < n) {
             for (int bb = 0; bb < bn; ++bb) {
-                int64_t idx = warm ? (int64_t)(b0 + bb) : (int64_t)s.bidx[b0 + bb];
-                a2 += load_a<T>(s.A, (size_t)idx * n + i) * Sb[bb][c];
+                const T a = load_a<T>(s.A, (size_t)sidx[bb] * n + i);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if (cg * 8 + q < k) acc[q] += a * S[bb][cg * 8 + q];
             }
-            acc[q] = a2;
         }
     }
-    for (int q = 0; q < 8; ++q) {
-        int o = tid + q * NT;
-        if (o >= nout) break;
-        int i = row0 + o / k, c = o % k;
-        ((T*)s.Y)[(size_t)i * k + c] = acc[q];
+    if (i < n) {
+        T* Ys = (T*)s.Ys + ((size_t)ch * n + i) * k;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (cg * 8 + q < k) Ys[cg * 8 + q] = acc[q];
     }
 }
 
@@ -1267,8 +1338,70 @@ struct XdotDw {
 template <typename T>
 __device__ __forceinline__ double load_val(const void* val, int64_t p) { return (double)((const T*)val)[p]; }
 
+// Measurement part of the objective for bf16 A (exact in float), the block's
+// slice of the m measurements, one warp per row.  V is split once per block
+// into hi/lo floats in shared memory (RB columns, zero beyond r, rows padded
+// to RB + 1 floats: conflict-free); a^T v_l = Dot2(a, v_hi) + sum a v_lo, the
+// second sum in plain float (its terms are 2^-24 of the first), ||a||^2 exact.
+template <int RB, typename A>
+__device__ void obj_meas_rows(const SolveDev& s, int lb, float* vsm, const double* coef, A& acc) {
+    const int n = s.n, r = s.r, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int rp = RB + 1;
+    float* vhi = vsm;
+    float* vlo = vsm + (size_t)n * rp;
+    for (int e = tid; e < n * RB; e += NT) {
+        const int j = e / RB, l = e % RB;
+        const double v = l < r ? s.V[(size_t)j * r + l] : 0.0;
+        const float h = (float)v;
+        vhi[j * rp + l] = h;
+        vlo[j * rp + l] = (float)(v - (double)h);
+    }
+    __syncthreads();
+    const int64_t per = (s.m + s.nb_red - 1) / s.nb_red;
+    const int64_t i0 = (int64_t)lb * per, i1 = min((int64_t)s.m, i0 + per);
+    for (int64_t i = i0 + warp; i < i1; i += NT / 32) {
+        dw ph[RB], paa = {0.f, 0.f};
+        float pl[RB];
+#pragma unroll
+        for (int l = 0; l < RB; ++l) { ph[l] = {0.f, 0.f}; pl[l] = 0.f; }
+        for (int j = lane; j < n; j += 32) {
+            const float a = load_a<float>(s.A, (size_t)i * n + j);
+#pragma unroll
+            for (int l = 0; l < RB; ++l) {
+                dot2_acc(ph[l], a, vhi[j * rp + l]);
+                pl[l] = fmaf(a, vlo[j * rp + l], pl[l]);
+            }
+            dot2_acc(paa, a, a);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int l = 0; l < RB; ++l) {
+                dw t = {__shfl_xor_sync(0xffffffffu, ph[l].hi, o), __shfl_xor_sync(0xffffffffu, ph[l].lo, o)};
+                dw_add(ph[l], t);
+                pl[l] += __shfl_xor_sync(0xffffffffu, pl[l], o);
+            }
+            dw t = {__shfl_xor_sync(0xffffffffu, paa.hi, o), __shfl_xor_sync(0xffffffffu, paa.lo, o)};
+            dw_add(paa, t);
+        }
+        if (lane == 0) {
+            double q = coef[MEG_RMAX] * dw_value(paa);
+#pragma unroll
+            for (int l = 0; l < RB; ++l)
+                if (l < r) {
+                    const double pv = dw_value(ph[l]) + (double)pl[l];
+                    q += coef[l] * pv * pv;
+                }
+            const double R = q - s.y[i];
+            const double w = R * R / (double)s.m;
+            const float wh = (float)w;
+            acc.add_prod(wh, 1.f);
+            acc.add_prod((float)(w - (double)wh), 1.f);
+        }
+    }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, double* out) {
+__global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, double* out, int vcap) {
     const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
     const SolveDev& s = sds[si];
     const int lb = blockIdx.x - s.off[PK_RED];
@@ -1310,6 +1443,16 @@ __global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, d
                     }
                 }
             }
+        }
+    } else if (sizeof(T) == 4 && vcap >= 2 * n * (rank_bucket(r) + 1)) {
+        // measurements, bf16 A: see obj_meas_rows
+        extern __shared__ __align__(16) unsigned char dsm[];
+        switch (rank_bucket(r)) {
+            case 2: obj_meas_rows<2>(s, lb, (float*)dsm, coef, acc); break;
+            case 4: obj_meas_rows<4>(s, lb, (float*)dsm, coef, acc); break;
+            case 8: obj_meas_rows<8>(s, lb, (float*)dsm, coef, acc); break;
+            case 16: obj_meas_rows<16>(s, lb, (float*)dsm, coef, acc); break;
+            default: obj_meas_rows<32>(s, lb, (float*)dsm, coef, acc); break;
         }
     } else {
         // measurements: rows of this block index measurement blocks over m
@@ -1365,6 +1508,7 @@ __global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, d
 // ==========================================================================
 // host launch wrappers
 namespace {
+constexpr size_t OBJ_SMEM_MAX = 200 * 1024;   // k_objective: V hi/lo of measurement members
 size_t combine_smem(int prec) {
     size_t tsz = prec == MEG_FP64 ? 8 : 4;
     return 8 * MEG_RMAX * MEG_KMAX + 3 * ROWS_MAX * MEG_KMAX * tsz + 2 * 528 * sizeof(dw) + 16;
@@ -1418,6 +1562,7 @@ cudaError_t init_kernel_attributes() {
     if ((e = set_smem(k_island_o1<float>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_o2<double>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_o2<float>, island_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_objective<float>, OBJ_SMEM_MAX)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1455,8 +1600,8 @@ cudaError_t launch_meas_batch(const GroupLaunch& g) {
 
 cudaError_t launch_meas_apply(const GroupLaunch& g) {
     if (g.blocks[PK_MEAS] == 0) return cudaSuccess;
-    if (g.prec == MEG_FP64) k_meas_apply<double><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns);
-    else k_meas_apply<float><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    if (g.prec == MEG_FP64) k_meas_apply<double><<<g.blocks[PK_MAP], NT, 0, g.stream>>>(g.d_solves, g.ns);
+    else k_meas_apply<float><<<g.blocks[PK_MAP], NT, 0, g.stream>>>(g.d_solves, g.ns);
     return cudaGetLastError();
 }
 
@@ -1500,7 +1645,14 @@ cudaError_t launch_orth2(const GroupLaunch& g, int phase) {
 }
 
 cudaError_t launch_objective(const GroupLaunch& g, double* out_f) {
-    if (g.prec == MEG_FP64) k_objective<double><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns, out_f);
-    else k_objective<float><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns, out_f);
+    if (g.prec == MEG_FP64) {
+        k_objective<double><<<g.blocks[PK_RED], NT, 0, g.stream>>>(g.d_solves, g.ns, out_f, 0);
+    } else {
+        // measurement members stage V as hi/lo floats: 2 n (r | 1) floats when they fit
+        const size_t need = g.meas_vr > 0 ? (size_t)g.meas_vr * 8 : 0;
+        const bool fits = need > 0 && need <= OBJ_SMEM_MAX;
+        k_objective<float><<<g.blocks[PK_RED], NT, fits ? need : 0, g.stream>>>(g.d_solves, g.ns, out_f,
+                                                                                  fits ? (int)(need / 4) : 0);
+    }
     return cudaGetLastError();
 }

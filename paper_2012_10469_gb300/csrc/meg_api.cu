@@ -130,6 +130,7 @@ struct meg_group_s {
     std::vector<meg_solve_s*> solves;
     SolveDev* d_desc = nullptr;
     SolveDev* d_tc_desc = nullptr;         // descriptors of the tensor-core solves, chunk by chunk
+    double* d_f = nullptr;                 // objective of each member (meg_group_objective)
     std::vector<TcMaps> tc_maps;           // one per chunk (addresses stable after creation)
     GroupLaunch gl{};
     bool has_dense = false, has_csr = false, has_meas = false;
@@ -160,7 +161,10 @@ int blocks_of(const SolveDev& d, int kind) {
         case PK_DENSE: return (dense && !d.tc) ? d.nb_dm * d.nb_ds : 0;
         case PK_CSR: return d.kind == MEG_CSR_QUAD ? d.nb_csr : 0;
         case PK_DTC: return (dense && d.tc) ? (int)tc_chunks_of(d) : 0;
-        default: return d.kind == MEG_MEAS_STOCH ? d.nb_meas : 0;
+        case PK_MEAS: return d.kind == MEG_MEAS_STOCH ? (d.nb_meas + MB_ROWS - 1) / MB_ROWS : 0;
+        case PK_MAP:
+            return d.kind == MEG_MEAS_STOCH ? (d.n + MA_ROWS - 1) / MA_ROWS * meas_chunks(d.nb_meas) : 0;
+        default: return 0;
     }
 }
 
@@ -171,6 +175,7 @@ GroupLaunch solo_launch(meg_solve_s* h) {
     for (int p = 0; p < PK_COUNT; ++p) g.blocks[p] = blocks_of(h->desc, p);
     g.prec = h->prec;
     g.stream = h->stream;
+    g.meas_vr = h->desc.kind == MEG_MEAS_STOCH ? h->n * (rank_bucket(h->r) + 1) : 0;
     if (g.blocks[PK_DTC] > 0) {
         g.tc_chunks = 1;
         g.tc_desc[0] = h->d_desc;
@@ -288,6 +293,21 @@ meg_status refresh_bounds(meg_solve_s* h) {
 
 namespace meg_internal {
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+cudaStream_t group_stream(meg_group g) { return g->stream; }
+cudaStream_t solve_stream(meg_handle h) { return h->stream; }
+
+// every member's f(X_t) (meg_objective's accurate pass, one launch for the
+// group) copied to host memory f[count]; enqueued on the group's stream
+meg_status group_objective_enqueue(meg_group g, double* f) {
+    CU(launch_objective(g->gl, g->d_f));
+    CU(cudaMemcpyAsync(f, g->d_f, sizeof(double) * g->gl.ns, cudaMemcpyDeviceToHost, g->stream));
+    return MEG_OK;
+}
+
+// device status of a member (MEG_OK or the error a kernel recorded); the
+// group's stream must be idle
+meg_status solve_status(meg_handle h) { return check_device_status(h); }
 }
 
 // ============================================================================
@@ -304,6 +324,7 @@ int64_t meg_footprint(int n, int r, int p, int precision, int kind) {
     int64_t b = 0;
     b += ts * (int64_t)n * (2 * r + 4 * k);
     if (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR) b += ts * (int64_t)std::max(dense_splits(n), 16) * n * k;
+    if (kind == MEG_MEAS_STOCH) b += ts * (int64_t)MEAS_CHUNKS * n * k;   // (+ scratch of 8 (34 m + m/8) bytes)
     if (precision == MEG_MIXED_BF16 && n % 8 == 0) b += 2 * (int64_t)((3 * k + 15) / 16 * 16) * ((n + 63) / 64 * 64);
     b += 4 * (nb_red + groups) * 2 * RED_MAX_ENTRIES;
     b += 4 * (groups + 3) + 8 * SM_TOTAL + 8;
@@ -361,8 +382,10 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
     const size_t ts = tsize(h->prec);
     const int k = h->k;
     const int groups = (d.nb_red + RED_GROUP - 1) / RED_GROUP;
+    // stream-ordered allocations: creating or destroying a solve never
+    // synchronises the device, so other solves' work keeps running
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
-        return cudaMalloc(ptr, std::max<size_t>(bytes, 16)) == cudaSuccess;
+        return cudaMallocAsync(ptr, std::max<size_t>(bytes, 16), h->stream) == cudaSuccess;
     };
     bool ok = alloc(&h->V, 8 * n * r) && alloc(&h->Vn, 8 * n * r) && alloc(&h->W, ts * n * k) &&
               alloc(&h->Wp, ts * n * k) && alloc(&h->Z, ts * n * k) && alloc(&h->Y, ts * n * k) &&
@@ -380,7 +403,8 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
         d.tc_kpad = round_up(n, 64);
         const size_t wsb = (size_t)2 * d.tc_npad * d.tc_kpad;
         h->solo_maps = new TcMaps();
-        if (cudaMalloc(&h->Wsp, wsb) != cudaSuccess || cudaMemsetAsync(h->Wsp, 0, wsb, h->stream) != cudaSuccess) {
+        if (cudaMallocAsync(&h->Wsp, wsb, h->stream) != cudaSuccess ||
+            cudaMemsetAsync(h->Wsp, 0, wsb, h->stream) != cudaSuccess) {
             cudaGetLastError();
             meg_destroy(h);
             return fail(MEG_ERR_OOM, "meg_create: split block");
@@ -464,20 +488,23 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     } else {
         compute_partition(h, d);
     }
-    if (dense_kind) {
-        if (h->Ys) { cudaFree(h->Ys); h->Ys = nullptr; }
-        if (cudaMalloc(&h->Ys, ts * (size_t)d.nb_ds * n * k) != cudaSuccess)
-            return fail(MEG_ERR_OOM, "meg_set_objective: dense partials");
+    if (dense_kind || o->kind == MEG_MEAS_STOCH) {
+        // partial products: K splits of the dense product, or batch chunks of the minibatch product
+        const size_t slots = dense_kind ? (size_t)d.nb_ds : (size_t)MEAS_CHUNKS;
+        if (h->Ys) { cudaFreeAsync(h->Ys, h->stream); h->Ys = nullptr; }
+        if (cudaMallocAsync(&h->Ys, ts * slots * n * k, h->stream) != cudaSuccess)
+            return fail(MEG_ERR_OOM, "meg_set_objective: partial products");
     }
     d.Ys = h->Ys;
     if (o->kind == MEG_MEAS_STOCH || o->kind == MEG_CSR_QUAD) {
-        size_t cnt = o->kind == MEG_MEAS_STOCH ? (size_t)std::max<int64_t>(o->m, o->L) * (2 + MEG_KMAX)
-                                               : (size_t)d.nb_csr;
-        if (h->meas) cudaFree(h->meas);
-        if (h->bidx) cudaFree(h->bidx);
+        // minibatch scratch: [Lb] residuals, [Lb] ||a||^2, [Lb x 32] a^T W, one partial bound per block
+        const size_t lbm = (size_t)std::max<int64_t>(o->m, o->L);
+        size_t cnt = o->kind == MEG_MEAS_STOCH ? lbm * (2 + MEG_KMAX) + lbm / MB_ROWS + 1 : (size_t)d.nb_csr;
+        if (h->meas) cudaFreeAsync(h->meas, h->stream);
+        if (h->bidx) cudaFreeAsync(h->bidx, h->stream);
         h->meas = nullptr; h->bidx = nullptr;
-        if (cudaMalloc((void**)&h->meas, sizeof(double) * cnt) != cudaSuccess ||
-            cudaMalloc((void**)&h->bidx, sizeof(int) * std::max(1, o->L)) != cudaSuccess)
+        if (cudaMallocAsync((void**)&h->meas, sizeof(double) * cnt, h->stream) != cudaSuccess ||
+            cudaMallocAsync((void**)&h->bidx, sizeof(int) * std::max(1, o->L), h->stream) != cudaSuccess)
             return fail(MEG_ERR_OOM, "meg_set_objective: scratch");
     }
     d.meas = h->meas; d.bidx = h->bidx;
@@ -552,6 +579,7 @@ meg_status meg_warm_start(meg_handle h, int products) {
     for (int p = 0; p < PK_COUNT; ++p) g.blocks[p] = blocks_of(dw, p);
     g.prec = h->prec;
     g.stream = h->stream;
+    g.meas_vr = dw.kind == MEG_MEAS_STOCH ? n * (rank_bucket(r) + 1) : 0;
     if ((st = enqueue_init_orth(g)) != MEG_OK) return st;
     if (dw.kind == MEG_CSR_QUAD) CU(launch_csr(g));   // bound max_i sum_j |M_ij| for the shift
     const bool dense = dw.kind == MEG_DENSE_QUAD || dw.kind == MEG_LINEAR;
@@ -728,7 +756,7 @@ meg_status meg_destroy(meg_handle h) {
     void* bufs[] = {h->V, h->Vn, h->W, h->Wp, h->Z, h->Y, h->Ys, h->Wsp, h->part, h->ctr,
                     h->sm, h->meas, h->bidx, h->d_f, h->d_desc};
     for (void* b : bufs)
-        if (b) cudaFree(b);
+        if (b) cudaFreeAsync(b, h->stream);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h->solo_maps;
     delete h;
@@ -758,7 +786,7 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
     }
     g->q = q;
     std::vector<SolveDev> descs(count);
-    int tot[PK_COUNT] = {0, 0, 0, 0};
+    int tot[PK_COUNT] = {};
     for (int i = 0; i < count; ++i) {
         meg_solve_s* h = solves[i];
         g->solves.push_back(h);
@@ -810,34 +838,49 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
     }
     std::vector<SolveDev> tcd;
     for (int i : tc_idx) tcd.push_back(descs[i]);
-    if (cudaMalloc((void**)&g->d_desc, sizeof(SolveDev) * count) != cudaSuccess) {
+    // the group's stream waits (on the device) for each member's queued work
+    cudaEvent_t ready = nullptr;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) {
         if (g->own_stream) cudaStreamDestroy(g->stream);
         delete g;
-        return fail(MEG_ERR_OOM, "meg_group_create: descriptors");
+        return fail(MEG_ERR_CUDA, "meg_group_create: event");
     }
-    for (auto* h : g->solves) cudaStreamSynchronize(h->stream);
-    if (cudaMemcpy(g->d_desc, descs.data(), sizeof(SolveDev) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
-        cudaFree(g->d_desc);
+    for (auto* h : g->solves) {
+        cudaEventRecord(ready, h->stream);
+        cudaStreamWaitEvent(g->stream, ready, 0);
+    }
+    cudaEventDestroy(ready);
+    auto undo = [&](meg_status st, const char* msg) {
+        if (g->d_desc) cudaFreeAsync(g->d_desc, g->stream);
+        if (g->d_tc_desc) cudaFreeAsync(g->d_tc_desc, g->stream);
+        if (g->d_f) cudaFreeAsync(g->d_f, g->stream);
+        cudaStreamSynchronize(g->stream);
         if (g->own_stream) cudaStreamDestroy(g->stream);
         delete g;
-        return fail(MEG_ERR_CUDA, "meg_group_create: descriptor copy");
-    }
+        return fail(st, msg);
+    };
+    if (cudaMallocAsync((void**)&g->d_desc, sizeof(SolveDev) * count, g->stream) != cudaSuccess ||
+        cudaMallocAsync((void**)&g->d_f, sizeof(double) * count, g->stream) != cudaSuccess)
+        return undo(MEG_ERR_OOM, "meg_group_create: descriptors");
+    if (cudaMemcpyAsync(g->d_desc, descs.data(), sizeof(SolveDev) * count, cudaMemcpyHostToDevice, g->stream) !=
+        cudaSuccess)
+        return undo(MEG_ERR_CUDA, "meg_group_create: descriptor copy");
     g->gl.d_solves = g->d_desc;
     g->gl.ns = count;
     for (int p = 0; p < PK_COUNT; ++p) g->gl.blocks[p] = tot[p];
     g->gl.prec = prec;
     g->gl.stream = g->stream;
+    g->gl.meas_vr = 0;
+    for (auto* h : g->solves)
+        if (h->desc.kind == MEG_MEAS_STOCH) g->gl.meas_vr = std::max(g->gl.meas_vr, h->n * (rank_bucket(h->r) + 1));
     if (!tcd.empty()) {
-        if (cudaMalloc((void**)&g->d_tc_desc, sizeof(SolveDev) * tcd.size()) != cudaSuccess ||
-            cudaMemcpy(g->d_tc_desc, tcd.data(), sizeof(SolveDev) * tcd.size(), cudaMemcpyHostToDevice) !=
-                cudaSuccess) {
-            cudaFree(g->d_desc);
-            if (g->d_tc_desc) cudaFree(g->d_tc_desc);
-            if (g->own_stream) cudaStreamDestroy(g->stream);
-            delete g;
-            return fail(MEG_ERR_CUDA, "meg_group_create: tensor-core descriptors");
-        }
+        if (cudaMallocAsync((void**)&g->d_tc_desc, sizeof(SolveDev) * tcd.size(), g->stream) != cudaSuccess ||
+            cudaMemcpyAsync(g->d_tc_desc, tcd.data(), sizeof(SolveDev) * tcd.size(), cudaMemcpyHostToDevice,
+                            g->stream) != cudaSuccess)
+            return undo(MEG_ERR_CUDA, "meg_group_create: tensor-core descriptors");
     }
+    // the host vectors above go out of scope: finish the copies first
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return undo(MEG_ERR_CUDA, "meg_group_create: copies");
     g->gl.tc_chunks = nch;
     for (int c = 0; c < nch; ++c) {
         g->gl.tc_desc[c] = g->d_tc_desc + c * TC_MAXG;
@@ -862,6 +905,23 @@ meg_status meg_group_step(meg_group g, int nsteps) {
         if (ce != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
     }
     for (int i = 0; i < nsteps; ++i) CU(cudaGraphLaunch(g->gexec, g->stream));
+    return MEG_OK;
+}
+
+meg_status meg_group_launch(meg_group g, int nsteps) {
+    if (!g || nsteps < 0) return fail(MEG_ERR_INVALID_ARG, "meg_group_launch: arguments");
+    for (int i = 0; i < nsteps; ++i) {
+        meg_status st = enqueue_iteration(g->gl, g->has_dense, g->has_csr, g->has_meas, g->q);
+        if (st != MEG_OK) return st;
+    }
+    return MEG_OK;
+}
+
+meg_status meg_group_objective(meg_group g, double* f) {
+    if (!g || !f) return fail(MEG_ERR_INVALID_ARG, "meg_group_objective: arguments");
+    meg_status st = meg_internal::group_objective_enqueue(g, f);
+    if (st != MEG_OK) return st;
+    CU(cudaStreamSynchronize(g->stream));
     return MEG_OK;
 }
 
@@ -901,10 +961,19 @@ int meg_group_kernels_per_step(meg_group g) {
 
 meg_status meg_group_destroy(meg_group g) {
     if (!g) return MEG_OK;
-    cudaStreamSynchronize(g->stream);
+    // members' later work (and frees) on their own streams follows the group's
+    cudaEvent_t done = nullptr;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(done, g->stream);
+        for (auto* h : g->solves) cudaStreamWaitEvent(h->stream, done, 0);
+    } else {
+        cudaStreamSynchronize(g->stream);
+    }
     if (g->gexec) cudaGraphExecDestroy(g->gexec);
-    if (g->d_desc) cudaFree(g->d_desc);
-    if (g->d_tc_desc) cudaFree(g->d_tc_desc);
+    if (g->d_desc) cudaFreeAsync(g->d_desc, g->stream);
+    if (g->d_tc_desc) cudaFreeAsync(g->d_tc_desc, g->stream);
+    if (g->d_f) cudaFreeAsync(g->d_f, g->stream);
+    if (done) cudaEventDestroy(done);
     for (auto* h : g->solves) { h->in_group = false; h->group_stream = nullptr; }
     if (g->own_stream) cudaStreamDestroy(g->stream);
     delete g;

@@ -56,7 +56,26 @@ enum SmallSlot : int {
 };
 
 // Work-partition kinds (one offset table per kind in a group).
-enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_DTC = 4, PK_COUNT = 5 };
+enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_DTC = 4, PK_MAP = 5, PK_COUNT = 6 };
+
+// Minibatch kernels (MEAS_STOCH).  k_meas_batch: one warp per batch row,
+// MB_ROWS rows per block, V and W staged MB_TILE rows at a time.
+// k_meas_apply: MA_ROWS rows of Y per block times one chunk of the batch;
+// a batch of more than MA_CHUNK rows (the warm start's full set of m
+// measurements) is split into up to MEAS_CHUNKS chunks whose partial
+// products k_combine sums in chunk order.
+#define MB_ROWS 8
+#define MB_TILE 64
+#define MA_ROWS 64
+#define MA_CHUNK 256
+#define MEAS_CHUNKS 16
+// compile-time widths the minibatch and objective kernels specialise on
+__host__ __device__ __forceinline__ int rank_bucket(int r) { return r <= 2 ? 2 : r <= 4 ? 4 : r <= 8 ? 8 : r <= 16 ? 16 : 32; }
+__host__ __device__ __forceinline__ int k_bucket(int k) { return k <= 8 ? 8 : k <= 16 ? 16 : 32; }
+__host__ __device__ __forceinline__ int meas_chunks(int Lb) {
+    const int c = (Lb + MA_CHUNK - 1) / MA_CHUNK;
+    return c < MEAS_CHUNKS ? (c > 0 ? c : 1) : MEAS_CHUNKS;
+}
 
 #define RED_GROUP 16            // blocks per first-level group of a reduction
 #define ROWS_MAX 64             // rows per block of the row-reduction kernels, at most
@@ -225,6 +244,7 @@ struct GroupLaunch {
     cudaStream_t stream;
     // tensor-core dense product: chunks of at most TC_MAXG solves, each with
     // its own descriptor sub-array (PK_DTC offsets relative to the chunk)
+    int meas_vr;                // largest n*(rank_bucket(r)+1) of a MEAS_STOCH member (objective staging), 0 if none
     int tc_chunks;
     const SolveDev* tc_desc[TC_MAX_CHUNKS];
     int tc_ns[TC_MAX_CHUNKS];

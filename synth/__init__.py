@@ -35,7 +35,8 @@ import numpy as np
 
 __all__ = [
     "bf16_round", "bf16_bits", "sym_noise", "orthonormal", "dense_quadratic",
-    "completion", "measurements", "linear", "arrival_trace", "DenseQuadratic",
+    "completion", "measurements", "linear", "arrival_trace", "serving_trace", "ServingRequest",
+    "DenseQuadratic",
     "Completion", "Measurements", "Linear", "config",
 ]
 
@@ -228,6 +229,60 @@ def arrival_trace(count: int, rate: float, seed: int, n_lo: int = 64, n_hi: int 
     r = rng.integers(1, r_max + 1, size=count)
     kind = rng.integers(0, 2, size=count)   # 0: dense quadratic, 1: measurements
     return [(float(times[i]), int(n[i]), int(r[i]), int(kind[i])) for i in range(count)]
+
+
+@dataclasses.dataclass
+class ServingRequest:
+    """One request of the serving trace (host data)."""
+    t: float                 # arrival time, seconds from the start of the trace
+    n: int
+    r: int
+    kind: int                # 0: dense quadratic (float64), 1: measurements (bf16)
+    M: Optional[np.ndarray] = None       # dense: n x n float64
+    A_bits: Optional[np.ndarray] = None  # measurements: m x n bf16 bits (a view of the pool)
+    A: Optional[np.ndarray] = None       # the same values as float64 (a view of the pool)
+    y: Optional[np.ndarray] = None       # m float64
+    L: int = 256
+
+
+def serving_trace(count: int, rate: float, seed: int, m: int = 50000, L: int = 256,
+                  sigma: float = 1e-4, n_lo: int = 64, n_hi: int = 1024, r_max: int = 8):
+    """Poisson trace of config-0-type and config-3-type requests.
+
+    Dense requests: M = U diag(w) U^T + E, w ~ Dirichlet(1_r), U orthonormal
+    of the request's own seed, E the leading n x n block of one seeded
+    symmetric N(0, sigma^2) matrix (a block of a symmetric matrix with i.i.d.
+    upper triangle has the same distribution).  Measurement requests: m
+    vectors a_i ~ N(0, I_n) rounded to bf16, taken as a contiguous window of
+    one seeded pool of i.i.d. values at a request-specific offset, and
+    y_i = a_i^T X* a_i (float64) for the request's own trace-1 rank-r X*.
+    Sharing the pools keeps the trace's host memory and generation time
+    bounded; every request still has its own planted solution.
+    """
+    arr = arrival_trace(count, rate, seed, n_lo, n_hi, r_max)
+    rng = np.random.default_rng(seed + 1)
+    E = sym_noise(rng, n_hi, sigma)
+    need_meas = any(k == 1 for _, _, _, k in arr)
+    pool_len = m * n_hi + 64 * 1024
+    if need_meas:
+        pool_bits = bf16_bits(rng.standard_normal(pool_len))
+        pool = (pool_bits.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
+    out = []
+    for j, (t, n, r, kind) in enumerate(arr):
+        rj = np.random.default_rng([seed, j])
+        U = orthonormal(rj, n, r)
+        w = rj.dirichlet(np.ones(r))
+        if kind == 0:
+            M = (U * w) @ U.T + E[:n, :n]
+            out.append(ServingRequest(t=t, n=n, r=r, kind=0, M=0.5 * (M + M.T)))
+        else:
+            off = int(rj.integers(0, (pool_len - m * n) // 8 + 1)) * 8
+            A = pool[off:off + m * n].reshape(m, n)
+            p = A @ U
+            y = (p * p) @ w
+            out.append(ServingRequest(t=t, n=n, r=r, kind=1, A_bits=pool_bits[off:off + m * n].reshape(m, n),
+                                      A=A, y=y, L=L))
+    return out
 
 
 # ---------------------------------------------------------------- named workloads

@@ -1,0 +1,124 @@
+"""Serving loop (meg_server: continuous batching) through the C ABI.
+
+* every request's result is the same alone and in a mix of requests of
+  different n, r, objective and precision that share the GPU;
+* a served request matches the float64 oracle run for the same number of
+  iterations;
+* admission respects the memory budget, and with room for several
+  requests their work overlaps.
+"""
+import math
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import meg
+
+from meg_cases import rel_frob
+
+pytestmark = pytest.mark.gpu
+
+
+def _B():
+    from paper_2012_10469_gb300 import binding as B
+    B.load()
+    return B
+
+
+def _requests(B):
+    """Config-0-type dense quadratics (float64) and config-3-type measurements (bf16)."""
+    reqs = []
+    for i, (n, r) in enumerate([(64, 1), (96, 3), (150, 2), (200, 5), (256, 4)]):
+        p = synth.dense_quadratic(n, r, 3000 + i, sigma=1e-4, storage="f64")
+        reqs.append(dict(kind=B.MEG_DENSE_QUAD, n=n, r=r, data=p.M, precision=B.MEG_FP64, p=4, q=2, eta=1.0,
+                         seed=10 + i, warm_start_products=40, tol=1e-6, max_iters=300))
+    for i, (n, r) in enumerate([(64, 2), (128, 3)]):
+        p = synth.measurements(n, r, 20 * n, 64, 3100 + i)
+        reqs.append(dict(kind=B.MEG_MEAS_STOCH, n=n, r=r, data=p.bits(), y=p.y, L=64,
+                         precision=B.MEG_MIXED_BF16, p=4, q=2, eta=1.0 / (4 * (1 + n / 64)), seed=20 + i,
+                         warm_start_products=40, fstar=0.0, tol=1e-6, max_iters=120))
+    return reqs
+
+
+def _serve(B, reqs, budget=8 << 30, max_active=64, one_at_a_time=False, timeout=120.0):
+    srv = B.Server(budget, max_active=max_active)
+    out = {}
+    try:
+        ids = []
+        for rq in reqs:
+            ids.append(srv.meg_server_submit(**rq))
+            if one_at_a_time:
+                while ids[-1] not in out:
+                    for rec, V, mu, s in srv.meg_server_poll(timeout_ms=50):
+                        out[rec["id"]] = (rec, V, mu, s)
+        t0 = time.time()
+        while len(out) < len(ids):
+            assert time.time() - t0 < timeout, "serving loop did not finish"
+            for rec, V, mu, s in srv.meg_server_poll(timeout_ms=50):
+                out[rec["id"]] = (rec, V, mu, s)
+    finally:
+        srv.meg_server_destroy()
+    return [out[i] for i in ids]
+
+
+def _X(V, mu, s):
+    return meg.Factored(V=V, mu=mu, s=s)
+
+
+def test_result_same_alone_and_in_mix():
+    B = _B()
+    reqs = _requests(B)
+    alone = _serve(B, reqs, one_at_a_time=True)
+    mix = _serve(B, reqs)
+    for rq, a, m in zip(reqs, alone, mix):
+        ra, rm = a[0], m[0]
+        assert ra["status"] in (B.MEG_OK, B.MEG_ERR_NOT_CONVERGED), ra
+        assert ra["status"] == rm["status"] and ra["iters"] == rm["iters"], (rq["n"], ra, rm)
+        e = rel_frob(_X(*a[1:]), _X(*m[1:]))
+        assert e <= 1e-5, (rq["n"], rq["r"], e)
+        assert abs(ra["f"] - rm["f"]) <= 1e-6 * max(abs(ra["f1"]), 1e-300)
+    # the mix really ran concurrently: some request was admitted before another finished
+    spans = sorted((m[0]["t_admit"], m[0]["t_done"]) for m in mix)
+    assert any(spans[i + 1][0] < spans[i][1] for i in range(len(spans) - 1))
+
+
+def test_served_request_matches_oracle():
+    B = _B()
+    n, r = 120, 3
+    p = synth.dense_quadratic(n, r, 3200, sigma=1e-4, storage="f64")
+    obj = meg.DenseQuadratic(p.M)
+    V0, lam0 = meg.warm_start(obj, r)
+    rq = dict(kind=B.MEG_DENSE_QUAD, n=n, r=r, data=p.M, precision=B.MEG_FP64, p=4, q=3, eta=1.0, seed=5,
+              warm_start_products=0, V0=V0, lam0=lam0, tol=1e-6, max_iters=60)
+    (rec, V, mu, s), = _serve(B, [rq])
+    assert rec["status"] in (B.MEG_OK, B.MEG_ERR_NOT_CONVERGED)
+    Xo, _ = meg.lowrank_meg(obj, V0, lam0, rec["iters"], 1.0, method="exact")
+    assert rel_frob(_X(V, mu, s), Xo) <= 1e-5
+    assert abs(rec["f"] - obj.value(Xo)) <= 1e-6 * obj.value(meg.init_X1(V0, lam0, meg.eps_schedule(0)))
+    # the plateau rule: the last check interval's decrease is below tol of the total
+    assert rec["iters"] == 60 or rec["f1"] > rec["f"]
+
+
+def test_admission_by_memory_budget():
+    B = _B()
+    reqs = _requests(B)[:5]
+    foot = [B.meg_footprint(q["n"], q["r"], q["p"], q["precision"], q["kind"]) + q["data"].nbytes for q in reqs]
+    budget = int(max(foot) * 1.5)
+    res = _serve(B, reqs, budget=budget)
+    spans = [(r[0]["t_admit"], r[0]["t_done"]) for r in res]
+    # at every admission, the requests then on the device fit the budget (a request's
+    # memory is released after its t_done, so intervals are [t_admit, t_done))
+    for ta, _ in spans:
+        held = sum(f for f, (a, d) in zip(foot, spans) if a <= ta < d)
+        assert held <= budget, (held, budget)
+    # and the budget made someone wait for another request to finish
+    assert any(spans[j][0] >= spans[i][1] for i in range(len(spans)) for j in range(len(spans)) if i != j)
+    srv = B.Server(1 << 20, max_active=4)
+    try:
+        with pytest.raises(B.MegError) as ei:
+            srv.meg_server_submit(**reqs[-1])
+        assert ei.value.status == B.MEG_ERR_OOM
+    finally:
+        srv.meg_server_destroy()
