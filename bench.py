@@ -217,12 +217,12 @@ SERVE_P, SERVE_Q, SERVE_TOL, SERVE_MAX_ITERS = 4, 2, 1e-6, 5000
 
 
 def serve_request_args(B, q):
-    """Server request for one trace entry (config-0 type: float64 dense, f* unknown,
-    plateau rule; config-3 type: bf16 measurements, f* = 0)."""
+    """Server request for one trace entry (config-0 type: float32 dense data, f*
+    unknown, plateau rule; config-3 type: bf16 measurements, f* = 0)."""
     common = dict(n=q.n, r=q.r, p=SERVE_P, q=SERVE_Q, seed=17 + q.n, warm_start_products=40,
                   tol=SERVE_TOL, max_iters=SERVE_MAX_ITERS)
     if q.kind == 0:
-        return dict(kind=B.MEG_DENSE_QUAD, data=q.M, precision=B.MEG_FP64, eta=1.0, **common)
+        return dict(kind=B.MEG_DENSE_QUAD, data=q.M32, precision=B.MEG_FP32, eta=1.0, **common)
     return dict(kind=B.MEG_MEAS_STOCH, data=q.A_bits, y=q.y, L=q.L, precision=B.MEG_MIXED_BF16,
                 eta=1.0 / (4.0 * (1.0 + q.n / q.L)), fstar=0.0, **common)
 
@@ -231,7 +231,7 @@ def run_serving(trace, budget_bytes: int, max_active: int = 1024):
     """Replay the trace's Poisson arrivals into meg_server; returns the summary."""
     import threading
     from paper_2012_10469_gb300 import binding as B
-    srv = B.Server(budget_bytes, max_active=max_active, check_every=10, meas_check_every=50)
+    srv = B.Server(budget_bytes, max_active=max_active, check_every=10, meas_check_every=100)
     results, errors = [], []
 
     def submitter():
@@ -281,7 +281,7 @@ def torch_fp32_solve(q, device, max_iters=SERVE_MAX_ITERS, tol=SERVE_TOL):
     gen = torch.Generator(device="cpu").manual_seed(q.n)
     dense = q.kind == 0
     if dense:
-        M = torch.from_numpy(q.M.astype(np.float32)).to(device)
+        M = torch.from_numpy(q.M32).to(device)
         G0 = M
         eta, check = 1.0, 10
     else:
@@ -524,8 +524,9 @@ def run_gpu(args):
                 serving = run_serving(trace, budget_bytes=int(free * 0.6))
                 serving["arrival_rate_per_s"] = args.serve_rate
                 serving["workload"] = ("Poisson arrivals, n log-uniform [64, 1024], r uniform 1..8, 50/50 "
-                                       "dense quadratic (float64, noise 1e-4, plateau rule) / measurements "
-                                       "(bf16 A, m=50000, L=256, f*=0), tol 1e-6, max_iters 5000, p=4, q=2")
+                                       "dense quadratic (float32 data, noise 1e-4, plateau rule) / measurements "
+                                       "(bf16 A, m=50000, L=256, f*=0), tol 1e-6, max_iters 5000, p=4, q=2, objective checked every "
+                                       "10 (dense) / 100 (measurements) iterations")
                 serving["plain_fp32_form"] = torch_fp32_serve_sample(trace, device, args.serve_fp32_seconds)
             except Exception as ex:  # reported, never fatal
                 serving = {"error": repr(ex)[:300]}

@@ -144,6 +144,12 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* d);
  * meg_create.  Needs the objective.  Synchronises the stream. */
 meg_status meg_warm_start(meg_handle h, int products);
 
+/* meg_warm_start_many -- meg_warm_start for `count` solves at once (one
+ * precision and one q): the products run as grouped kernels on `stream`,
+ * with the same results as warming each alone.  f1 (host, count values,
+ * may be NULL) receives f(X_1) of each solve.  Synchronises. */
+meg_status meg_warm_start_many(const meg_handle* solves, int count, int products, void* stream, double* f1);
+
 /* meg_step -- run `nsteps` iterations of Algorithm 2 (t -> t + nsteps),
  * enqueued on the stream without a host synchronisation. */
 meg_status meg_step(meg_handle h, int nsteps);

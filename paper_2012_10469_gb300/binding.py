@@ -99,6 +99,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_objective_dense_noalloc": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_double, C.c_int, C.c_int,
                                                   C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
         "meg_group_launch": (C.c_int, [H, C.c_int]),
+        "meg_warm_start_many": (C.c_int, [_P(H), C.c_int, C.c_int, C.c_void_p, _P(C.c_double)]),
         "meg_group_objective": (C.c_int, [H, _P(C.c_double)]),
         "meg_server_create": (C.c_int, [_P(meg_server_options), _P(H)]),
         "meg_server_submit": (C.c_int, [H, _P(meg_request), _P(C.c_uint64)]),
@@ -291,6 +292,15 @@ class Group:
             self.meg_group_destroy()
         except Exception:
             pass
+
+
+def meg_warm_start_many(solves, products: int = 40, stream=None) -> np.ndarray:
+    """Warm-start several solves together; returns f(X_1) of each."""
+    arr = (C.c_void_p * len(solves))(*[s.h for s in solves])
+    f1 = np.empty(len(solves), dtype=np.float64)
+    _check(load().meg_warm_start_many(arr, len(solves), products, None if stream is None else int(stream),
+                                      _f64p(f1)), "meg_warm_start_many")
+    return f1
 
 
 class Server:

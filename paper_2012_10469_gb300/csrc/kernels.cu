@@ -1129,54 +1129,61 @@ template <> __device__ __forceinline__ float load_a<float>(const void* A, size_t
     return __uint_as_float(((unsigned)b) << 16);
 }
 
-// Minibatch pass, one warp per batch row b (MB_ROWS rows per block):
-// r_b = a^T X a - y (mode 0) or -y (mode 1, the warm start's -grad f(0)),
-// ||a||^2 and T_b = a^T W (k values).  V and W are staged MB_TILE rows at a
-// time in shared memory in the storage type (padded rows: no bank
-// conflicts) and shared by the block's rows; lanes stride the row's
-// elements, so each load of a is coalesced.  The last block of the solve
-// turns the per-block partial bounds into the shift bound.
-// one warp's batch row: products of a with the B staged columns of V (zero
-// beyond r) and of W (zero beyond k); B = k_bucket(k) >= k > r
+// Minibatch pass over MB_ROWS batch rows b per block:
+//   r_b = a_b^T X a_b - y_b (mode 0) or -y_b (mode 1, the warm start's
+//   -grad f(0)), ||a_b||^2 and T_b = a_b^T W (k values).
+// The block computes the small product [a_b rows] x [V | W] (2B columns, B =
+// k_bucket(k) >= k > r, zero columns beyond r and k) in tiles of MB_TILE
+// elements: the tile of the gathered rows of A and the tile of V (converted
+// to the storage type) and W are staged in shared memory; thread (row,
+// column group) accumulates C/8 consecutive columns of one row, so a staged
+// value of V/W serves four rows by broadcast and no cross-lane reduction is
+// needed.  The last block of the solve turns the per-block partial bounds
+// into the shift bound.
 template <typename T, int B>
-__device__ __forceinline__ void meas_batch_row(const SolveDev& s, int64_t idx, bool active, bool warm, T* sV, T* sW,
-                                               T (&av)[MEG_KMAX], T (&aw)[MEG_KMAX], T& aa) {
-    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x, lane = tid & 31;
+__device__ __forceinline__ void meas_batch_tile(const SolveDev& s, int lb, bool warm, const int64_t* sidx,
+                                                T* As, T* Xs, T (&out)[B / 4], T& aa) {
+    constexpr int C = 2 * B, CPT = C / 8;               // columns, columns per thread
+    constexpr int TL = sizeof(T) == 8 ? MB_TILE / 2 : MB_TILE, EPT = TL / 8;   // elements per tile / thread
+    constexpr int LDA = TL + 1, LDX = C + 1;
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const int row = tid >> 3, c0 = (tid & 7) * CPT;
+    const int Lb = s.nb_meas;
     const double* V = s.V;
     const T* W = (const T*)s.W;
-    for (int i0 = 0; i0 < n; i0 += MB_TILE) {
-        const int tn = min(MB_TILE, n - i0);
+    const int b0 = lb * MB_ROWS;
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) out[j] = 0;
+    for (int i0 = 0; i0 < n; i0 += TL) {
+        const int tn = min(TL, n - i0);
         __syncthreads();
-        if (!warm)
-            for (int e = tid; e < tn * B; e += NT) {
-                const int j = e / B, l = e % B;
-                sV[j * (B + 1) + l] = l < r ? (T)V[(size_t)(i0 + j) * r + l] : (T)0;
+        {   // rows of A: thread (row, EPT consecutive elements); ||a||^2 on the way
+            const int e0 = (tid & 7) * EPT;
+            const bool live = b0 + row < Lb;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                T a = 0;
+                if (live && e0 + e < tn) a = load_a<T>(s.A, (size_t)sidx[row] * n + i0 + e0 + e);
+                As[row * LDA + e0 + e] = a;
+                aa += a * a;
             }
-        for (int e = tid; e < tn * B; e += NT) {
-            const int j = e / B, c = e % B;
-            sW[j * (B + 1) + c] = c < k ? W[(size_t)(i0 + j) * k + c] : (T)0;
+        }
+        for (int e = tid; e < tn * C; e += NT) {
+            const int j = e / C, c = e % C;
+            T x = 0;
+            if (c < B) { if (!warm && c < r) x = (T)V[(size_t)(i0 + j) * r + c]; }
+            else if (c - B < k) x = W[(size_t)(i0 + j) * k + (c - B)];
+            Xs[j * LDX + c] = x;
         }
         __syncthreads();
-        if (active) {
-            for (int ii = lane; ii < tn; ii += 32) {
-                const T a = load_a<T>(s.A, (size_t)idx * n + i0 + ii);
-                aa += a * a;
-                if (!warm) {
+        for (int i = 0; i < tn; ++i) {
+            const T a = As[row * LDA + i];
 #pragma unroll
-                    for (int l = 0; l < B; ++l) av[l] += a * sV[ii * (B + 1) + l];
-                }
-#pragma unroll
-                for (int c = 0; c < B; ++c) aw[c] += a * sW[ii * (B + 1) + c];
-            }
+            for (int j = 0; j < CPT; ++j) out[j] += a * Xs[i * LDX + c0 + j];
         }
     }
-    for (int o = 16; o > 0; o >>= 1) aa += __shfl_xor_sync(0xffffffffu, aa, o);
-#pragma unroll
-    for (int c = 0; c < B; ++c)
-        for (int o = 16; o > 0; o >>= 1) {
-            aw[c] += __shfl_xor_sync(0xffffffffu, aw[c], o);
-            if (!warm) av[c] += __shfl_xor_sync(0xffffffffu, av[c], o);
-        }
+    // the eight threads of a row hold pieces of ||a||^2 (consecutive lanes)
+    for (int o = 4; o > 0; o >>= 1) aa += __shfl_xor_sync(0xffffffffu, aa, o);
 }
 
 template <typename T>
@@ -1186,51 +1193,79 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
     const int lb = blockIdx.x - s.off[PK_MEAS];
     const int Lb = s.nb_meas, nblk = (Lb + MB_ROWS - 1) / MB_ROWS;
     if (lb < 0 || lb >= nblk) return;
-    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
     const bool warm = (s.mode == 1);
-    const int b = lb * MB_ROWS + warp;
-    const bool active = b < Lb;
-    int64_t idx = 0;
-    if (active)
-        idx = warm ? (int64_t)b
-                   : (int64_t)(splitmix64(s.seed + ((uint64_t)s.sm[SM_T] * (uint64_t)s.L + (uint64_t)b + 1ull) *
-                                                       0x9E3779B97F4A7C15ull) %
-                               (uint64_t)s.m);
-    __shared__ T sV[MB_TILE * (MEG_KMAX + 1)];
-    __shared__ T sW[MB_TILE * (MEG_KMAX + 1)];
-    T av[MEG_KMAX], aw[MEG_KMAX], aa = 0;
-#pragma unroll
-    for (int c = 0; c < MEG_KMAX; ++c) { av[c] = 0; aw[c] = 0; }
-    switch (k_bucket(k)) {
-        case 8: meas_batch_row<T, 8>(s, idx, active, warm, sV, sW, av, aw, aa); break;
-        case 16: meas_batch_row<T, 16>(s, idx, active, warm, sV, sW, av, aw, aa); break;
-        default: meas_batch_row<T, 32>(s, idx, active, warm, sV, sW, av, aw, aa); break;
+    __shared__ int64_t sidx[MB_ROWS];
+    if (tid < MB_ROWS) {
+        const int b = lb * MB_ROWS + tid;
+        int64_t idx = 0;
+        if (b < Lb)
+            idx = warm ? (int64_t)b
+                       : (int64_t)(splitmix64(s.seed + ((uint64_t)s.sm[SM_T] * (uint64_t)s.L + (uint64_t)b + 1ull) *
+                                                           0x9E3779B97F4A7C15ull) %
+                                   (uint64_t)s.m);
+        sidx[tid] = idx;
     }
+    // shared tiles: rows of A (MB_ROWS x (MB_TILE+1)), V|W (MB_TILE x (2*32+1)), products
+    constexpr int TL = sizeof(T) == 8 ? MB_TILE / 2 : MB_TILE;
+    __shared__ T As[MB_ROWS * (TL + 1)];
+    __shared__ T Xs[TL * (2 * MEG_KMAX + 1)];
+    __shared__ double Ps[MB_ROWS][2 * MEG_KMAX + 1];
+    __syncthreads();
+    const int row = tid >> 3;
+    T aa = 0;
+    switch (k_bucket(k)) {
+        case 8: {
+            T out[2];
+            meas_batch_tile<T, 8>(s, lb, warm, sidx, As, Xs, out, aa);
+            for (int j = 0; j < 2; ++j) Ps[row][(tid & 7) * 2 + j] = (double)out[j];
+            if ((tid & 7) == 0) Ps[row][2 * MEG_KMAX] = (double)aa;
+            break;
+        }
+        case 16: {
+            T out[4];
+            meas_batch_tile<T, 16>(s, lb, warm, sidx, As, Xs, out, aa);
+            for (int j = 0; j < 4; ++j) Ps[row][(tid & 7) * 4 + j] = (double)out[j];
+            if ((tid & 7) == 0) Ps[row][2 * MEG_KMAX] = (double)aa;
+            break;
+        }
+        default: {
+            T out[8];
+            meas_batch_tile<T, 32>(s, lb, warm, sidx, As, Xs, out, aa);
+            for (int j = 0; j < 8; ++j) Ps[row][(tid & 7) * 8 + j] = (double)out[j];
+            if ((tid & 7) == 0) Ps[row][2 * MEG_KMAX] = (double)aa;
+            break;
+        }
+    }
+    __syncthreads();
+    const int B = k_bucket(k);
     double* sc = s.meas;              // [Lb] residual, [Lb] ||a||^2, [Lb x 32] T_b, [nblk] bounds
+    // T_b: one thread per (row, column)
+    for (int e = tid; e < MB_ROWS * k; e += NT) {
+        const int rr = e / k, c = e % k, b = lb * MB_ROWS + rr;
+        if (b < Lb) sc[2 * (size_t)Lb + (size_t)b * MEG_KMAX + c] = Ps[rr][B + c];
+    }
     __shared__ double bpart[MB_ROWS];
-    if (lane == 0) {
+    if (tid < MB_ROWS) {
+        const int b = lb * MB_ROWS + tid;
         double contrib = 0.0;
-        if (active) {
+        if (b < Lb) {
+            const double aav = Ps[tid][2 * MEG_KMAX];
             const double sv = warm ? 0.0 : s.sm[SM_S];
-            double q = sv * (double)aa;
+            double q = sv * aav;
             if (!warm)
-#pragma unroll
-                for (int l = 0; l < MEG_RMAX; ++l)
-                    if (l < r) q += (s.sm[SM_MU + l] - sv) * (double)av[l] * (double)av[l];
-            const double res = q - s.y[idx];
+                for (int l = 0; l < r; ++l) q += (s.sm[SM_MU + l] - sv) * Ps[tid][l] * Ps[tid][l];
+            const double res = q - s.y[sidx[tid]];
             sc[b] = res;
-            sc[Lb + b] = (double)aa;
-#pragma unroll
-            for (int c = 0; c < MEG_KMAX; ++c)
-                if (c < k) sc[2 * (size_t)Lb + (size_t)b * MEG_KMAX + c] = (double)aw[c];
-            if (!warm) s.bidx[b] = (int)idx;
+            sc[Lb + b] = aav;
+            if (!warm) s.bidx[b] = (int)sidx[tid];
             // Minibatch (mode 0): the L vectors a_b are nearly orthogonal, so the
             // eigenvalues of (2/L) sum r_b a_b a_b^T are close to (2/L) r_b ||a_b||^2;
             // ||grad||_2 is estimated by (2/L) max_b |r_b| ||a_b||^2 (1 + sqrt(L/n))^2.
             // Warm start (mode 1, r_b = -y_b): lambda_min(-grad f(0)) >= -(2/m) sum_{y<0} |y| ||a||^2.
-            contrib = warm ? (res > 0.0 ? res * (double)aa : 0.0) : fabs(res) * (double)aa;
+            contrib = warm ? (res > 0.0 ? res * aav : 0.0) : fabs(res) * aav;
         }
-        bpart[warp] = contrib;
+        bpart[tid] = contrib;
     }
     __syncthreads();
     __shared__ int am_last;

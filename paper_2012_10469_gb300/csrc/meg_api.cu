@@ -764,13 +764,25 @@ meg_status meg_destroy(meg_handle h) {
 }
 
 // ---------------------------------------------------------------------------- groups
+namespace {
+// warm: the descriptors get the warm-start mode (operator -grad f(0), the
+// measurement pass over all m measurements) and X_1 need not be set yet
+meg_status group_create_impl(const meg_handle* solves, int count, void* stream, bool warm, meg_group* out);
+}  // namespace
+
 meg_status meg_group_create(const meg_handle* solves, int count, void* stream, meg_group* out) {
+    return group_create_impl(solves, count, stream, false, out);
+}
+
+namespace {
+meg_status group_create_impl(const meg_handle* solves, int count, void* stream, bool warm, meg_group* out) {
     if (!solves || count < 1 || !out) return fail(MEG_ERR_INVALID_ARG, "meg_group_create: arguments");
     *out = nullptr;
+    if (!solves[0]) return fail(MEG_ERR_INVALID_ARG, "meg_group_create: null handle");
     const int prec = solves[0]->prec, q = solves[0]->q;
     for (int i = 0; i < count; ++i) {
         meg_solve_s* h = solves[i];
-        if (!h || !h->has_obj || !h->has_x) return fail(MEG_ERR_STATE, "meg_group_create: solve not ready");
+        if (!h || !h->has_obj || (!warm && !h->has_x)) return fail(MEG_ERR_STATE, "meg_group_create: solve not ready");
         if (h->in_group) return fail(MEG_ERR_STATE, "meg_group_create: solve already in a group");
         if (h->prec != prec || h->q != q)
             return fail(MEG_ERR_INVALID_ARG, "meg_group_create: solves must share precision and q");
@@ -791,9 +803,13 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
         meg_solve_s* h = solves[i];
         g->solves.push_back(h);
         descs[i] = h->desc;
+        if (warm) {
+            descs[i].mode = 1;
+            if (descs[i].kind == MEG_MEAS_STOCH) descs[i].nb_meas = (int)descs[i].m;
+        }
         for (int p = 0; p < PK_COUNT; ++p) {
             descs[i].off[p] = tot[p];
-            tot[p] += blocks_of(h->desc, p);
+            tot[p] += blocks_of(descs[i], p);
         }
         const int kind = h->desc.kind;
         g->has_dense |= (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR);
@@ -888,6 +904,51 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
     }
     for (auto* h : g->solves) { h->in_group = true; h->group_stream = g->stream; }
     *out = g;
+    return MEG_OK;
+}
+}  // namespace
+
+meg_status meg_warm_start_many(const meg_handle* solves, int count, int products, void* stream, double* f1) {
+    if (!solves || count < 1 || products < 1) return fail(MEG_ERR_INVALID_ARG, "meg_warm_start_many: arguments");
+    for (int i = 0; i < count; ++i) {
+        meg_solve_s* h = solves[i];
+        if (!h) return fail(MEG_ERR_INVALID_ARG, "meg_warm_start_many: null handle");
+        if (!h->has_obj) return fail(MEG_ERR_STATE, "meg_warm_start_many: objective not set");
+        if (h->in_group) return fail(MEG_ERR_STATE, "meg_warm_start_many: solve belongs to a group");
+    }
+    // random start block, as meg_warm_start draws it
+    for (int i = 0; i < count; ++i) {
+        meg_solve_s* h = solves[i];
+        const int n = h->n, r = h->r, k = h->k;
+        std::vector<double> vh((size_t)n * r), wh((size_t)n * k);
+        std::mt19937_64 gen(h->opt.seed ^ 0xA11CE5ull);
+        std::normal_distribution<double> nd(0.0, 1.0);
+        for (int a = 0; a < n; ++a)
+            for (int j = 0; j < k; ++j) {
+                const double v = nd(gen);
+                wh[(size_t)a * k + j] = v;
+                if (j < r) vh[(size_t)a * r + j] = v;
+            }
+        meg_status st;
+        if ((st = upload_f64(h, h->V, vh)) != MEG_OK || (st = upload_T(h, h->W, wh)) != MEG_OK) return st;
+    }
+    meg_group g = nullptr;
+    meg_status st = group_create_impl(solves, count, stream, true, &g);
+    if (st != MEG_OK) return st;
+    st = enqueue_init_orth(g->gl);
+    if (st == MEG_OK && g->has_csr) st = launch_csr(g->gl) == cudaSuccess ? MEG_OK : MEG_ERR_CUDA;
+    if (st == MEG_OK) st = enqueue_iteration(g->gl, g->has_dense, g->has_csr, g->has_meas, products);
+    if (st == MEG_OK && f1) st = meg_internal::group_objective_enqueue(g, f1);
+    if (st == MEG_OK && cudaStreamSynchronize(g->stream) != cudaSuccess) st = fail(MEG_ERR_CUDA, "meg_warm_start_many");
+    meg_group_destroy(g);
+    if (st != MEG_OK) return st;
+    for (int i = 0; i < count; ++i) {
+        meg_solve_s* h = solves[i];
+        cudaStreamSynchronize(h->stream);
+        h->has_x = true;
+        if ((st = check_device_status(h)) != MEG_OK) return st;
+        if ((st = refresh_bounds(h)) != MEG_OK) return st;
+    }
     return MEG_OK;
 }
 

@@ -58,13 +58,14 @@ enum SmallSlot : int {
 // Work-partition kinds (one offset table per kind in a group).
 enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_DTC = 4, PK_MAP = 5, PK_COUNT = 6 };
 
-// Minibatch kernels (MEAS_STOCH).  k_meas_batch: one warp per batch row,
-// MB_ROWS rows per block, V and W staged MB_TILE rows at a time.
+// Minibatch kernels (MEAS_STOCH).  k_meas_batch: MB_ROWS batch rows per
+// block as a small tiled product [rows of A] x [V | W], MB_TILE elements of
+// the rows staged at a time.
 // k_meas_apply: MA_ROWS rows of Y per block times one chunk of the batch;
 // a batch of more than MA_CHUNK rows (the warm start's full set of m
 // measurements) is split into up to MEAS_CHUNKS chunks whose partial
 // products k_combine sums in chunk order.
-#define MB_ROWS 8
+#define MB_ROWS 32
 #define MB_TILE 64
 #define MA_ROWS 64
 #define MA_CHUNK 256

@@ -37,6 +37,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "../../include/meg.h"
@@ -110,8 +111,10 @@ struct meg_server_s {
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
+    cudaStream_t admit_stream = nullptr;
     void run();
     bool admit(Req* q);
+    void admit_batch(std::vector<Req*>& ready);
     int class_of(const meg_request& rq);
     void launch_tick(Class& c);
     void finish_tick(Class& c);
@@ -134,6 +137,7 @@ int meg_server_s::class_of(const meg_request& rq) {
     return (int)classes.size() - 1;
 }
 
+// First half of admission: stream, device copy of the data, solve, objective.
 bool meg_server_s::admit(Req* q) {
     const meg_request& rq = q->rq;
     const int n = rq.opt.n;
@@ -165,18 +169,47 @@ bool meg_server_s::admit(Req* q) {
     const bool warm = rq.warm_start_products > 0;
     if (st == MEG_OK) st = meg_create(&o, warm ? nullptr : rq.V0, warm ? nullptr : rq.lam0, &q->h);
     if (st == MEG_OK) st = meg_set_objective(q->h, &d);
-    if (st == MEG_OK && warm) st = meg_warm_start(q->h, rq.warm_start_products);
     if (st == MEG_OK && std::isfinite(rq.fstar)) st = meg_set_fstar(q->h, rq.fstar);
-    if (st == MEG_OK) st = meg_objective(q->h, &q->f1);
+    if (st == MEG_OK && !warm) st = meg_objective(q->h, &q->f1);
     if (st != MEG_OK) {
         q->status = st;
         retire(q);
         return false;
     }
-    q->f = q->f1;
-    q->cls = class_of(rq);
-    classes[q->cls].joining.push_back(q);     // enters the group at the next tick boundary
     return true;
+}
+
+// Second half for a batch of prepared requests: warm starts run together
+// (grouped kernels, one pass for every solve of the same precision, q and
+// product count), f(X_1) from the same grouped pass; then each request joins
+// its class at the next tick boundary.
+void meg_server_s::admit_batch(std::vector<Req*>& ready) {
+    std::map<std::tuple<int, int, int>, std::vector<Req*>> warm;
+    for (Req* q : ready)
+        if (q->rq.warm_start_products > 0)
+            warm[std::make_tuple(q->rq.opt.precision, q->rq.opt.q, q->rq.warm_start_products)].push_back(q);
+    for (auto& kv : warm) {
+        std::vector<Req*>& v = kv.second;
+        std::vector<meg_handle> hs;
+        for (Req* q : v) hs.push_back(q->h);
+        std::vector<double> f1(v.size(), NAN);
+        const meg_status st =
+            meg_warm_start_many(hs.data(), (int)hs.size(), std::get<2>(kv.first), admit_stream, f1.data());
+        for (size_t i = 0; i < v.size(); ++i) {
+            v[i]->f1 = f1[i];
+            if (st != MEG_OK) v[i]->status = st;
+        }
+    }
+    for (Req* q : ready) {
+        if (q->status != MEG_OK || !std::isfinite(q->f1)) {
+            if (q->status == MEG_OK) q->status = MEG_ERR_NUMERIC;
+            retire(q);
+            continue;
+        }
+        q->f = q->f1;
+        q->cls = class_of(q->rq);
+        classes[q->cls].joining.push_back(q);     // enters the group at the next tick boundary
+    }
 }
 
 void meg_server_s::launch_tick(Class& c) {
@@ -290,6 +323,7 @@ void meg_server_s::retire(Req* q) {
 
 void meg_server_s::run() {
     cudaSetDevice(device);
+    cudaStreamCreateWithFlags(&admit_stream, cudaStreamNonBlocking);
     while (!stop.load()) {
         // admission, FIFO
         std::vector<Req*> take;
@@ -304,11 +338,13 @@ void meg_server_s::run() {
                 take.push_back(q);
             }
         }
+        std::vector<Req*> ready;
         for (Req* q : take) {
             used += q->footprint;
             active += 1;
-            admit(q);
+            if (admit(q)) ready.push_back(q);
         }
+        if (!ready.empty()) admit_batch(ready);
         bool busy = false;
         for (Class& c : classes) {
             if (c.inflight) {
@@ -356,6 +392,7 @@ void meg_server_s::run() {
         if (c.stream) cudaStreamDestroy(c.stream);
     }
     classes.clear();
+    if (admit_stream) cudaStreamDestroy(admit_stream);
 }
 
 extern "C" {

@@ -239,6 +239,7 @@ class ServingRequest:
     r: int
     kind: int                # 0: dense quadratic (float64), 1: measurements (bf16)
     M: Optional[np.ndarray] = None       # dense: n x n float64
+    M32: Optional[np.ndarray] = None     # dense: the same matrix rounded to float32
     A_bits: Optional[np.ndarray] = None  # measurements: m x n bf16 bits (a view of the pool)
     A: Optional[np.ndarray] = None       # the same values as float64 (a view of the pool)
     y: Optional[np.ndarray] = None       # m float64
@@ -274,7 +275,8 @@ def serving_trace(count: int, rate: float, seed: int, m: int = 50000, L: int = 2
         w = rj.dirichlet(np.ones(r))
         if kind == 0:
             M = (U * w) @ U.T + E[:n, :n]
-            out.append(ServingRequest(t=t, n=n, r=r, kind=0, M=0.5 * (M + M.T)))
+            M = 0.5 * (M + M.T)
+            out.append(ServingRequest(t=t, n=n, r=r, kind=0, M=M, M32=M.astype(np.float32)))
         else:
             off = int(rj.integers(0, (pool_len - m * n) // 8 + 1)) * 8
             A = pool[off:off + m * n].reshape(m, n)

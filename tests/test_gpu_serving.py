@@ -122,3 +122,29 @@ def test_admission_by_memory_budget():
         assert ei.value.status == B.MEG_ERR_OOM
     finally:
         srv.meg_server_destroy()
+
+
+def test_warm_start_many_equals_alone():
+    """meg_warm_start_many warms several solves with grouped kernels exactly as
+    meg_warm_start warms each alone, and reports f(X_1)."""
+    import torch
+    from meg_cases import make_gpu_solve, gpu_factored
+    B = _B()
+    cases = [("dense_quadratic", synth.dense_quadratic(n, r, 3300 + n, sigma=1e-4), r, B.MEG_FP64, 1.0)
+             for n, r in ((96, 2), (200, 4), (64, 3))]
+    cases += [("measurements", synth.measurements(n, r, 20 * n, 64, 3400 + n), r, B.MEG_MIXED_BF16,
+               1.0 / (4 * (1 + n / 64))) for n, r in ((80, 2), (128, 3))]
+    for prec in (B.MEG_FP64, B.MEG_MIXED_BF16):
+        sub = [c for c in cases if c[3] == prec]
+        alone, many = [], []
+        for kind, prob, r, _, eta in sub:
+            a = make_gpu_solve(kind, prob, r, 4, 2, prec, eta, 11)
+            a.meg_warm_start(30)
+            alone.append((gpu_factored(a), a.meg_objective()))
+            a.meg_destroy()
+            many.append(make_gpu_solve(kind, prob, r, 4, 2, prec, eta, 11))
+        f1 = B.meg_warm_start_many(many, 30, stream=torch.cuda.current_stream().cuda_stream)
+        for s_, (Xa, fa), f in zip(many, alone, f1):
+            assert rel_frob(gpu_factored(s_), Xa) <= 1e-12
+            assert f == fa
+            assert s_.meg_objective() == fa
