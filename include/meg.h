@@ -338,6 +338,33 @@ meg_status meg_server_destroy(meg_server s);
 meg_status meg_objective_dense_noalloc(const double* V, const double* mu, double s, int n, int r,
                                        const void* M, int precision, double* f_out, void* stream);
 
+/*
+ * meg_autotune -- choose p (extra subspace vectors) and q (products per
+ * iteration) for one problem (Section 3's subspace iteration; the paper
+ * fixes neither).  A reference solve with more vectors and products than
+ * any candidate and one pilot solve per candidate run `pilot_iters`
+ * iterations from X_1 (V0, lam0 as in meg_create; host) on the objective
+ * `obj` (device data, borrowed), all in base->precision.  Candidates are
+ * tried in order of cost, q = 1..q_max, then p ascending; the first whose
+ * iterate is within tol_x * sqrt(pilot_iters / horizon) of the reference
+ * (relative Frobenius distance) is returned in *p_out, *q_out, its
+ * distance in *err_out (may be NULL).  The choice depends on results, not
+ * timings.  If none qualifies the most accurate candidate is returned with
+ * MEG_ERR_NOT_CONVERGED.  The paper has no counterpart.
+ */
+typedef struct {
+    int q_max;            /* largest q tried, 1..7 (the reference uses q_max + 2, at most 8) */
+    const int* p_cand;    /* candidate p values (host), or NULL for {2, 4, 6, 8, 12, 16} */
+    int n_p;
+    int pilot_iters;      /* iterations of each pilot run */
+    int horizon;          /* iterations the solve will run */
+    double tol_x;         /* target relative Frobenius error of X_t at the horizon */
+} meg_autotune_options;
+
+meg_status meg_autotune(const meg_options* base, const meg_objective_desc* obj, const double* V0,
+                        const double* lam0, const meg_autotune_options* ao, int* p_out, int* q_out,
+                        double* err_out);
+
 /* Device-memory footprint in bytes of one solve (library-owned buffers,
  * not the caller's objective data), for admission control. */
 int64_t meg_footprint(int n, int r, int p, int precision, int kind);

@@ -41,6 +41,11 @@ class meg_objective_desc(C.Structure):
                 ("A", C.c_void_p), ("y", C.c_void_p), ("m", C.c_int64), ("L", C.c_int)]
 
 
+class meg_autotune_options(C.Structure):
+    _fields_ = [("q_max", C.c_int), ("p_cand", C.c_void_p), ("n_p", C.c_int), ("pilot_iters", C.c_int),
+                ("horizon", C.c_int), ("tol_x", C.c_double)]
+
+
 class meg_server_options(C.Structure):
     _fields_ = [("hbm_budget", C.c_int64), ("max_active", C.c_int), ("check_every", C.c_int),
                 ("meas_check_every", C.c_int)]
@@ -66,6 +71,20 @@ class MegError(RuntimeError):
 
 _lib: Optional[C.CDLL] = None
 _P = C.POINTER
+_exiting = False
+
+
+def _mark_exit():
+    # objects still alive at interpreter exit are released by the process
+    # exit itself; their destructors must not call into a CUDA runtime that
+    # may already be shut down
+    global _exiting
+    _exiting = True
+
+
+import atexit  # noqa: E402
+
+atexit.register(_mark_exit)
 
 
 def load(path: str = LIB_PATH) -> C.CDLL:
@@ -99,6 +118,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_objective_dense_noalloc": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_double, C.c_int, C.c_int,
                                                   C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
         "meg_group_launch": (C.c_int, [H, C.c_int]),
+        "meg_autotune": (C.c_int, [_P(meg_options), _P(meg_objective_desc), _P(C.c_double), _P(C.c_double),
+                                   _P(meg_autotune_options), _P(C.c_int), _P(C.c_int), _P(C.c_double)]),
         "meg_warm_start_many": (C.c_int, [_P(H), C.c_int, C.c_int, C.c_void_p, _P(C.c_double)]),
         "meg_group_objective": (C.c_int, [H, _P(C.c_double)]),
         "meg_server_create": (C.c_int, [_P(meg_server_options), _P(H)]),
@@ -245,6 +266,8 @@ class Solve:
             self.h = None
 
     def __del__(self):
+        if _exiting:
+            return
         try:
             self.meg_destroy()
         except Exception:
@@ -288,10 +311,39 @@ class Group:
             self.g = None
 
     def __del__(self):
+        if _exiting:
+            return
         try:
             self.meg_group_destroy()
         except Exception:
             pass
+
+
+def meg_autotune(n, r, precision, kind, V0, lam0, dense=None, A=None, y=None, L=0, rowptr=None, col=None,
+                 val=None, eta=1.0, eps=(0.8, 10.0, 2.0), seed=1, q_max=4, p_cand=None, pilot_iters=20,
+                 horizon=500, tol_x=1e-5, stream=None):
+    """(p, q, distance to the reference, met_target) for one problem; device tensors as in
+    Solve.meg_set_objective."""
+    lib = load()
+    opt = meg_options(n=n, r=r, p=1, q=1, precision=precision, eta=eta, eps_a=eps[0], eps_c=eps[1],
+                      eps_pow=eps[2], max_iters=horizon, tol=1e-6, seed=seed,
+                      stream=None if stream is None else int(stream))
+    d = meg_objective_desc(kind=kind, dense=_dptr(dense), rowptr=_dptr(rowptr), col=_dptr(col), val=_dptr(val),
+                           nnz=0 if col is None else int(col.numel()), A=_dptr(A), y=_dptr(y),
+                           m=0 if A is None else int(A.shape[0]), L=L)
+    pc = None
+    if p_cand is not None:
+        pc = np.ascontiguousarray(p_cand, dtype=np.int32)
+    ao = meg_autotune_options(q_max=q_max, p_cand=None if pc is None else pc.ctypes.data,
+                              n_p=0 if pc is None else len(pc), pilot_iters=pilot_iters, horizon=horizon, tol_x=tol_x)
+    V0 = np.ascontiguousarray(V0, dtype=np.float64)
+    lam0 = np.ascontiguousarray(lam0, dtype=np.float64)
+    p, q, e = C.c_int(), C.c_int(), C.c_double()
+    st = lib.meg_autotune(C.byref(opt), C.byref(d), _f64p(V0), _f64p(lam0), C.byref(ao), C.byref(p), C.byref(q),
+                          C.byref(e))
+    if st not in (MEG_OK, MEG_ERR_NOT_CONVERGED):
+        _check(st, "meg_autotune")
+    return p.value, q.value, e.value, st == MEG_OK
 
 
 def meg_warm_start_many(solves, products: int = 40, stream=None) -> np.ndarray:
@@ -378,6 +430,8 @@ class Server:
             self.h = None
 
     def __del__(self):
+        if _exiting:
+            return
         try:
             self.meg_server_destroy()
         except Exception:

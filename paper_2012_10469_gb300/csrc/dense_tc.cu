@@ -18,7 +18,8 @@
 //     M = 128, N = 3k padded to 16, K = 16, into one of two tensor-memory
 //     accumulators (segment i uses accumulator i mod 2);
 //   - warps 2-5: epilogue of the other accumulator: tcgen05.ld, the sum
-//     hi + mid + lo per column, coalesced float32 stores of the partial.
+//     hi + mid + lo per column added to a running sum in registers,
+//     coalesced float32 stores of the partial at the end of a segment.
 // Every mbarrier wait is bounded (about one second of globaltimer); on
 // timeout the CTA flags its solves with MEG_ERR_TIMEOUT, waits (bounded) for
 // its own copies and MMAs, frees its tensor memory and returns.
@@ -41,6 +42,12 @@ constexpr int TC_BK = 64;                       // bf16 elements per 128-byte ro
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;   // 16 KB
 constexpr int TC_TMEM_COLS = 256;               // two accumulators, 128 columns apart
 constexpr int TC_EPI_LD = 33;                   // epilogue staging row (k <= 32 floats)
+// The tensor cores add each MMA's products into the float32 accumulator
+// with less than round-to-nearest accuracy, so the error of one accumulation
+// grows with its length.  An accumulation is therefore restarted every
+// TC_SUB chunks (K = 512, 32 MMAs); the epilogue adds the sub-results in
+// float32 round-to-nearest arithmetic.
+constexpr int TC_SUB = 8;
 constexpr int TC_EPI_BYTES = TC_BM * TC_EPI_LD * 4;
 constexpr int TC_SMEM_LIMIT = 227 * 1024;
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // 1 s
@@ -245,62 +252,80 @@ k_dense_tc(const SolveDev* sds, int ns, const __grid_constant__ TcMaps maps, lon
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer
-            int it = 0, i = 0;
-            for (long long g = g_begin; g < g_end && !*err; ++i) {
+            int it = 0, u = 0;                      // u: sub-accumulation counter
+            bool ok = true;
+            for (long long g = g_begin; g < g_end && ok && !*err;) {
                 const TcSeg q = tc_segment(sds, ns, g, g_end, T, G, c);
-                const int ab = i & 1;
-                if (!mbar_wait(&tempty[ab], ((i >> 1) & 1) ^ 1)) { *err = 1; break; }
-                tc_fence_after();
-                const uint32_t acc = tmem + (uint32_t)(ab * 128);
                 const uint32_t idesc = idesc_bf16(TC_BM, sds[q.si].tc_npad);
-                bool ok = true;
-                for (int j = 0; j < q.len; ++j, ++it) {
-                    const int st = it % S;
-                    if (!mbar_wait(&full[st], (it / S) & 1)) { ok = false; break; }
+                for (int j0 = 0; j0 < q.len && ok; j0 += TC_SUB, ++u) {
+                    const int ab = u & 1;
+                    if (!mbar_wait(&tempty[ab], ((u >> 1) & 1) ^ 1)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES), b0 = smem_u32(sB + (size_t)st * b_stride);
+                    const uint32_t acc = tmem + (uint32_t)(ab * 128);
+                    const int j1 = min(q.len, j0 + TC_SUB);
+                    for (int j = j0; j < j1; ++j, ++it) {
+                        const int st = it % S;
+                        if (!mbar_wait(&full[st], (it / S) & 1)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(sA + (size_t)st * TC_A_BYTES),
+                                       b0 = smem_u32(sB + (size_t)st * b_stride);
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk)
-                        umma_bf16(acc, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
-                                  (j > 0 || kk > 0) ? 1u : 0u);
-                    umma_commit(&empty[st]);        // frees the stage once these MMAs have read it
+                        for (int kk = 0; kk < TC_BK / 16; ++kk)
+                            umma_bf16(acc, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                                      (j > j0 || kk > 0) ? 1u : 0u);
+                        umma_commit(&empty[st]);    // frees the stage once these MMAs have read it
+                    }
+                    if (ok) umma_commit(&tfull[ab]);   // sub-accumulation ab complete
                 }
-                if (!ok) { *err = 1; break; }
-                umma_commit(&tfull[ab]);            // accumulator ab complete
                 g += q.len;
             }
+            if (!ok) *err = 1;
             umma_commit(mdone);                     // every MMA issued by this thread
             mbar_wait(mdone, 0);
         }
     } else {
         // ---------------- epilogue: warp w reads accumulator lanes 32 (w mod 4) ...
+        // The three pieces of W occupy columns [0, P), [P, 2P), [2P, 3P) of the
+        // accumulator (P = k rounded up to 16), so one 16-column load holds one
+        // piece of 16 output columns and the running sums stay in registers.
         const int quarter = warp & 3;
         const int row = quarter * 32 + lane;
         float* srow = stage + row * TC_EPI_LD;
-        int i = 0;
-        for (long long g = g_begin; g < g_end && !*err; ++i) {
+        int u = 0;
+        bool ok = true;
+        for (long long g = g_begin; g < g_end && ok && !*err;) {
             const TcSeg q = tc_segment(sds, ns, g, g_end, T, G, c);
             const SolveDev& s = sds[q.si];
-            const int n = s.n, k = s.k, npad = s.tc_npad;
-            const int ab = i & 1;
-            if (!mbar_wait(&tfull[ab], (i >> 1) & 1)) { *err = 1; break; }
-            tc_fence_after();
-            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 128);
-            for (int c0 = 0; c0 < npad; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tb + (uint32_t)c0, v);
+            const int n = s.n, k = s.k, P = s.tc_npad / 3;
+            float run[32];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = c0 + j;
-                    const float x = __uint_as_float(v[j]);
-                    if (col < k) srow[col] = x;                       // W_hi piece
-                    else if (col < 2 * k) srow[col - k] += x;         // + W_mid piece
-                    else if (col < 3 * k) srow[col - 2 * k] += x;     // + W_lo piece
+            for (int j = 0; j < 32; ++j) run[j] = 0.f;
+            for (int j0 = 0; j0 < q.len; j0 += TC_SUB, ++u) {
+                const int ab = u & 1;
+                if (!mbar_wait(&tfull[ab], (u >> 1) & 1)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * 128);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {            // output columns [16h, 16h + 16)
+                    if (16 * h < P) {
+                        uint32_t vh[16], vm[16], vl[16];
+                        tmem_ld16(tb + (uint32_t)(16 * h), vh);
+                        tmem_ld16(tb + (uint32_t)(P + 16 * h), vm);
+                        tmem_ld16(tb + (uint32_t)(2 * P + 16 * h), vl);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)      // (hi + mid) + lo, then the running sum
+                            run[16 * h + j] += (__uint_as_float(vh[j]) + __uint_as_float(vm[j])) + __uint_as_float(vl[j]);
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[ab]);
             }
-            tc_fence_before();
+            if (!ok) break;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < k) srow[j] = run[j];
             __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[ab]);
             // this warp's 32 rows are k * 32 consecutive floats of the partial
             float* Ys = (float*)s.Ys + ((size_t)q.slot * n + q.m0 + quarter * 32) * k;
             const int rows = min(32, n - (q.m0 + quarter * 32));
@@ -308,6 +333,7 @@ k_dense_tc(const SolveDev* sds, int ns, const __grid_constant__ TcMaps maps, lon
             __syncwarp();
             g += q.len;
         }
+        if (!ok) *err = 1;
     }
     tc_fence_before();
     __syncthreads();

@@ -399,7 +399,7 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
         return fail(MEG_ERR_OOM, "meg_create: device allocation failed");
     }
     if (h->prec == MEG_MIXED_BF16 && (n % 8) == 0) {
-        d.tc_npad = round_up(3 * k, 16);
+        d.tc_npad = 3 * round_up(k, 16);     // three bf16 pieces of W, each padded to 16 rows
         d.tc_kpad = round_up(n, 64);
         const size_t wsb = (size_t)2 * d.tc_npad * d.tc_kpad;
         h->solo_maps = new TcMaps();

@@ -22,7 +22,7 @@ TOL_X, TOL_F, TOL_SIG = 1e-5, 1e-6, 1e-6
 
 
 def _check(rows, r, tol_x=TOL_X, tol_f=TOL_F, tol_sig=TOL_SIG, tol_r1=None, tol_eval=None,
-           r1_from=10):
+           r1_from=10, r1_slack=1e-9):
     """Objective: the kernel's f(X_t) must equal the oracle's f on the same
     (GPU) iterate to tol_eval (relative), and the GPU iterate's f must match
     the oracle iterate's f to tol_f relative to the run's objective scale
@@ -32,7 +32,8 @@ def _check(rows, r, tol_x=TOL_X, tol_f=TOL_F, tol_sig=TOL_SIG, tol_r1=None, tol_
     iteration r1_from on (cases whose (r+1)-th eigenvalue is separated from
     the rest; the extra subspace vectors start random).  Always: the GPU's
     sigma_{r+1} is a Ritz value of a k-dimensional subspace, so it never
-    exceeds the exact eigenvalue."""
+    exceeds the exact eigenvalue (up to r1_slack relative: the rounding of the
+    storage precision)."""
     for row in rows:
         ex = rel_frob(row["Xg"], row["Xo"])
         es = np.max(np.abs(row["sig_g"][:r] - row["sig_o"][:r]) / np.abs(row["sig_o"][:r]))
@@ -44,7 +45,8 @@ def _check(rows, r, tol_x=TOL_X, tol_f=TOL_F, tol_sig=TOL_SIG, tol_r1=None, tol_
         assert ef <= tol_f, f"t={row['t']}: f rel err {ef:.3e} ({row['fo_at_g']!r} vs {row['fo']!r})"
         assert ee <= (tol_eval or 1e-7), f"t={row['t']}: f evaluation rel err {ee:.3e}"
         dr1 = row["sig_g"][r] - row["sig_o"][r]
-        assert dr1 <= 1e-9 * abs(row["sig_o"][r]), f"t={row['t']}: Ritz sigma_r+1 above the eigenvalue"
+        if r1_slack is not None:     # None: the oracle's sigma_r+1 is itself a Ritz value
+            assert dr1 <= r1_slack * abs(row["sig_o"][r]), f"t={row['t']}: Ritz sigma_r+1 above the eigenvalue"
         if tol_r1 is not None and row["t"] >= r1_from:
             assert abs(dr1) <= tol_r1 * abs(row["sig_o"][r]), f"t={row['t']}: sigma_r+1 err {dr1:.3e}"
         # the certificate the GPU reports is the paper's formula on its own Ritz values
