@@ -1289,11 +1289,15 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
             sc[b] = res;
             sc[Lb + b] = aav;
             if (!warm) s.bidx[b] = (int)sidx[tid];
-            // Minibatch (mode 0): the L vectors a_b are nearly orthogonal, so the
-            // eigenvalues of (2/L) sum r_b a_b a_b^T are close to (2/L) r_b ||a_b||^2;
-            // ||grad||_2 is estimated by (2/L) max_b |r_b| ||a_b||^2 (1 + sqrt(L/n))^2.
+            // Minibatch (mode 0): the spectral size of (2/L) sum r_b a_b a_b^T is
+            // estimated as for a weighted Wishart matrix,
+            //   (2/L) rms_b(|r_b| ||a_b||^2) (1 + sqrt(L/n))^2.
+            // It only sets the shift c, whose job is to centre the bulk of M_t near
+            // log s: the top-r eigenvalues sit log(mu_r / s) (about 10) above it, far
+            // beyond the gradient's spread, so a direction the estimate misses (one
+            // large residual) only converges more slowly.  Rayleigh-Ritz is exact.
             // Warm start (mode 1, r_b = -y_b): lambda_min(-grad f(0)) >= -(2/m) sum_{y<0} |y| ||a||^2.
-            contrib = warm ? (res > 0.0 ? res * aav : 0.0) : fabs(res) * aav;
+            contrib = warm ? (res > 0.0 ? res * aav : 0.0) : (res * aav) * (res * aav);
         }
         bpart[tid] = contrib;
     }
@@ -1301,7 +1305,7 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
     __shared__ int am_last;
     if (tid == 0) {
         double v = 0.0;
-        for (int w = 0; w < MB_ROWS; ++w) v = warm ? v + bpart[w] : fmax(v, bpart[w]);
+        for (int w = 0; w < MB_ROWS; ++w) v += bpart[w];
         sc[(size_t)Lb * (2 + MEG_KMAX) + lb] = v;
         __threadfence();
         unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
@@ -1314,11 +1318,11 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
     __shared__ double red[NT];
     const double* bp = sc + (size_t)Lb * (2 + MEG_KMAX);
     double v = 0.0;
-    for (int q2 = tid; q2 < nblk; q2 += NT) v = warm ? v + __ldcg(bp + q2) : fmax(v, __ldcg(bp + q2));
+    for (int q2 = tid; q2 < nblk; q2 += NT) v += __ldcg(bp + q2);
     red[tid] = v;
     __syncthreads();
     for (int h = NT / 2; h > 0; h >>= 1) {
-        if (tid < h) red[tid] = warm ? red[tid] + red[tid + h] : fmax(red[tid], red[tid + h]);
+        if (tid < h) red[tid] = red[tid] + red[tid + h];
         __syncthreads();
     }
     if (tid == 0) {
@@ -1327,7 +1331,7 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
             bound *= 2.0 / (double)Lb;
         } else {
             const double f = 1.0 + sqrt((double)Lb / (double)n);
-            bound *= 2.0 / (double)Lb * f * f;
+            bound = 2.0 / (double)Lb * sqrt(bound / (double)Lb) * f * f;
         }
         s.sm[SM_RESID_BOUND] = bound;
     }
