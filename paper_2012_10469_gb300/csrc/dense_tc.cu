@@ -185,6 +185,8 @@ __device__ __forceinline__ TcSeg tc_segment(const SolveDev* sds, int ns, long lo
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_dense_tc(const SolveDev* sds, int ns, const __grid_constant__ TcMaps maps, long long T, int S, int b_stride) {
+    pdl_wait();
+    pdl_trigger();
     const int G = gridDim.x, c = blockIdx.x;
     const long long g_begin = tc_chunk_start(c, G, T), g_end = tc_chunk_start(c + 1, G, T);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -399,6 +401,6 @@ cudaError_t launch_dense_tc(const SolveDev* d_solves, int ns, long long T, int G
     if (T <= 0 || G <= 0) return cudaSuccess;
     const int b_stride = npad_max * TC_BK * 2;      // a multiple of 2048: keeps 1024-byte tile alignment
     const int S = tc_stages(b_stride);
-    k_dense_tc<<<G, TC_THREADS, tc_smem_bytes(S, b_stride), st>>>(d_solves, ns, maps, T, S, b_stride);
-    return cudaGetLastError();
+    return launch_k(k_dense_tc, dim3(G), dim3(TC_THREADS), tc_smem_bytes(S, b_stride), st, 1, d_solves, ns, maps, T,
+                    S, b_stride);
 }

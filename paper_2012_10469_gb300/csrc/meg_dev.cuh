@@ -129,6 +129,49 @@ struct SolveDev {
 };
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Every kernel of the library begins with
+// pdl_wait() -- it returns once the preceding kernel on the stream has
+// completed and its memory is visible, before any global data is touched --
+// and then pdl_trigger(), which lets the next kernel's blocks be launched and
+// placed while this one runs.  The attribute is set only with MEG_PDL=1 in
+// the environment; without it both instructions are no-ops and the launches
+// are plain stream-ordered launches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+bool meg_pdl_enabled();
+
+// Launch with the programmatic-serialization attribute and, for cluster > 1,
+// thread-block clusters of that size.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, int cluster,
+                     Args... args) {
+    if (grid.x == 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    unsigned na = 0;
+    if (cluster > 1) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = cluster;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (meg_pdl_enabled()) {
+        attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// ---------------------------------------------------------------------------
 // Block -> solve lookup for grouped launches.
 __device__ __forceinline__ int find_solve(const SolveDev* sd, int ns, int kind, int b) {
     int lo = 0, hi = ns - 1;
