@@ -786,11 +786,15 @@ __global__ void __launch_bounds__(NT) k_orth1(const SolveDev* sds, int ns, int p
     const T* W = (const T*)s.W;
     T* Wp = (T*)s.Wp;
     double* Vn = s.Vn;
+    // the block's rows of Z are one contiguous span: stage it (coalesced), then W' = Z M1
+    T* sZ = (T*)(ent + 528);
+    for (int idx = tid; idx < nr * k; idx += NT) sZ[idx] = Z[(size_t)row0 * k + idx];
+    __syncthreads();
     for (int idx = tid; idx < nr * k; idx += NT) {
-        const int q = idx / k, j = idx % k, i = row0 + q;
+        const int q = idx / k, j = idx % k;
         T acc = 0;
-        for (int l = 0; l < k; ++l) acc += Z[(size_t)i * k + l] * M1[l * k + j];
-        Wp[(size_t)i * k + j] = acc;
+        for (int l = 0; l < k; ++l) acc += sZ[q * k + l] * M1[l * k + j];
+        Wp[(size_t)row0 * k + idx] = acc;
         sW[idx] = acc;
     }
     if (fin) {
@@ -896,26 +900,17 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
     T* W = (T*)s.W;
     double* V = s.V;
     const double* Vn = s.Vn;
+    // the block's rows of W' are one contiguous span: stage it (coalesced), then W = W' M2;
+    // in float storage the staging area is the entries' buffer (unused until the Gram)
+    T* sIn = sizeof(T) == 4 ? (T*)ent : (T*)(ent + RED_MAX_ENTRIES);
+    for (int idx = tid; idx < nr * k; idx += NT) sIn[idx] = Wp[(size_t)row0 * k + idx];
+    __syncthreads();
     for (int idx = tid; idx < nr * k; idx += NT) {
-        const int i = row0 + idx / k, j = idx % k;
+        const int q = idx / k, j = idx % k;
         T acc = 0;
-        for (int l = 0; l < k; ++l) acc += Wp[(size_t)i * k + l] * M2[l * k + j];
-        W[(size_t)i * k + j] = acc;
+        for (int l = 0; l < k; ++l) acc += sIn[q * k + l] * M2[l * k + j];
+        W[(size_t)row0 * k + idx] = acc;
         sW[idx] = acc;
-        if (s.Wsp) {
-            // exact split for the tensor-core product: W = hi + mid + lo in bf16
-            const float w = (float)acc;
-            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
-            const float r1 = w - __bfloat162float(hi);
-            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-            const float r2 = r1 - __bfloat162float(mid);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
-            const size_t kp = (size_t)s.tc_kpad;
-            const size_t P = (size_t)(s.tc_npad / 3);    // rows per piece (k rounded up to 16)
-            s.Wsp[(size_t)j * kp + i] = __bfloat16_as_ushort(hi);
-            s.Wsp[(P + j) * kp + i] = __bfloat16_as_ushort(mid);
-            s.Wsp[(2 * P + j) * kp + i] = __bfloat16_as_ushort(lo);
-        }
     }
     for (int idx = tid; idx < nr * r; idx += NT) {
         const int i = row0 + idx / r, j = idx % r;
@@ -932,6 +927,25 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
         sVl[idx] = (float)(v - (double)vh);
     }
     __syncthreads();
+    if (s.Wsp) {
+        // exact split for the tensor-core product, W = hi + mid + lo in bf16; Wsp is
+        // K-major (row j of a piece holds column j of W), so consecutive threads
+        // take consecutive rows i of W for coalesced stores
+        const size_t kp = (size_t)s.tc_kpad;
+        const size_t P = (size_t)(s.tc_npad / 3);        // rows per piece (k rounded up to 16)
+        for (int idx = tid; idx < nr * k; idx += NT) {
+            const int j = idx / nr, q = idx % nr, i = row0 + q;
+            const float w = (float)sW[q * k + j];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const float r1 = w - __bfloat162float(hi);
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(mid);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
+            s.Wsp[(size_t)j * kp + i] = __bfloat16_as_ushort(hi);
+            s.Wsp[(P + j) * kp + i] = __bfloat16_as_ushort(mid);
+            s.Wsp[(2 * P + j) * kp + i] = __bfloat16_as_ushort(lo);
+        }
+    }
     const int nsym = k * (k + 1) / 2;
     const int E = nsym + r * k;
     for (int e = tid; e < E; e += NT) {
@@ -1608,13 +1622,15 @@ size_t combine_smem(int prec) {
     size_t tsz = prec == MEG_FP64 ? 8 : 4;
     return 8 * MEG_RMAX * MEG_KMAX + 3 * ROWS_MAX * MEG_KMAX * tsz + 2 * 528 * sizeof(dw) + 16;
 }
-size_t orth1_smem(int prec) {
+size_t orth1_smem(int prec) {      // M1, Qv, rows of W', entries, rows of Z
     size_t tsz = prec == MEG_FP64 ? 8 : 4;
-    return MEG_KMAX * MEG_KMAX * tsz + 8 * MEG_KMAX * MEG_RMAX + ROWS_MAX * MEG_KMAX * tsz + 528 * sizeof(dw) + 16;
+    return MEG_KMAX * MEG_KMAX * tsz + 8 * MEG_KMAX * MEG_RMAX + ROWS_MAX * MEG_KMAX * tsz + 528 * sizeof(dw) + 16 +
+           ROWS_MAX * MEG_KMAX * tsz;
 }
-size_t orth2_smem(int prec) {
+size_t orth2_smem(int prec) {      // M2, rows of W, V, entries (float: also the rows of W'), rows of W' (double)
     size_t tsz = prec == MEG_FP64 ? 8 : 4;
-    return MEG_KMAX * MEG_KMAX * tsz + ROWS_MAX * MEG_KMAX * tsz + 8 + ROWS_MAX * MEG_RMAX * 8 + RED_MAX_ENTRIES * sizeof(dw) + 16;
+    return MEG_KMAX * MEG_KMAX * tsz + ROWS_MAX * MEG_KMAX * tsz + 8 + ROWS_MAX * MEG_RMAX * 8 + RED_MAX_ENTRIES * sizeof(dw) + 16 +
+           (prec == MEG_FP64 ? ROWS_MAX * MEG_KMAX * tsz : 0);
 }
 size_t island_smem() {
     return 4 * 32 * MEG_LDK * sizeof(float) + RED_MAX_ENTRIES * sizeof(dw) + (6 * 32 * MEG_LDK + 32 + 96 + 32) * sizeof(double);
