@@ -258,7 +258,7 @@ def run_serving(trace, budget_bytes: int, max_active: int = 1024):
     """Replay the trace's Poisson arrivals into meg_server; returns the summary."""
     import threading
     from paper_2012_10469_gb300 import binding as B
-    srv = B.Server(budget_bytes, max_active=max_active, check_every=10, meas_check_every=100)
+    srv = B.Server(budget_bytes, max_active=max_active, check_every=10, meas_check_every=250)
     results, errors = [], []
 
     def submitter():
@@ -551,7 +551,7 @@ def run_gpu(args):
                 serving["workload"] = ("Poisson arrivals, n log-uniform [64, 1024], r uniform 1..8, 50/50 "
                                        "dense quadratic (float32 data, noise 1e-4, plateau rule) / measurements "
                                        "(bf16 A, m=50000, L=256, f*=0), tol 1e-6, max_iters 5000, p=4, q=2, objective checked every "
-                                       "10 (dense) / 100 (measurements) iterations")
+                                       "10 (dense) / 250 (measurements) iterations")
                 serving["plain_fp32_form"] = torch_fp32_serve_sample(trace, device, args.serve_fp32_seconds)
             except Exception as ex:  # reported, never fatal
                 serving = {"error": repr(ex)[:300]}

@@ -1177,23 +1177,19 @@ template <> __device__ __forceinline__ float load_a<float>(const void* A, size_t
 // into the shift bound.
 template <typename T, int B>
 __device__ __forceinline__ void meas_batch_tile(const SolveDev& s, int lb, bool warm, const int64_t* sidx,
-                                                T* As, T* Xs, T* Xlo, double (&out)[B / 4], T& aa) {
+                                                T* As, T* Xs, double (&out)[B / 4], T& aa) {
     constexpr int C = 2 * B, CPT = C / 8;               // columns, columns per thread
     constexpr int TL = sizeof(T) == 8 ? MB_TILE / 2 : MB_TILE, EPT = TL / 8;   // elements per tile / thread
-    constexpr int LDA = TL + 1, LDX = C + 1, LDL = B + 1;
-    constexpr bool SPLIT = sizeof(T) == 4;              // float storage: a^T v in double-word arithmetic
+    constexpr int LDA = TL + 1, LDX = C + 1;
     const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
     const int row = tid >> 3, c0 = (tid & 7) * CPT;
-    const bool vpart = c0 < B;                          // this thread's columns are of V (else of W)
     const int Lb = s.nb_meas;
     const double* V = s.V;
     const T* W = (const T*)s.W;
     const int b0 = lb * MB_ROWS;
     T acc[CPT];
-    dw accv[CPT];
-    float acclo[CPT];
 #pragma unroll
-    for (int j = 0; j < CPT; ++j) { acc[j] = 0; accv[j] = {0.f, 0.f}; acclo[j] = 0.f; }
+    for (int j = 0; j < CPT; ++j) acc[j] = 0;
     for (int i0 = 0; i0 < n; i0 += TL) {
         const int tn = min(TL, n - i0);
         __syncthreads();
@@ -1211,40 +1207,19 @@ __device__ __forceinline__ void meas_batch_tile(const SolveDev& s, int lb, bool 
         for (int e = tid; e < tn * C; e += NT) {
             const int j = e / C, c = e % C;
             T x = 0;
-            if (c < B) {
-                if (!warm && c < r) {
-                    const double v = V[(size_t)(i0 + j) * r + c];
-                    x = (T)v;
-                    if (SPLIT) Xlo[j * LDL + c] = (T)(v - (double)x);
-                } else if (SPLIT) {
-                    Xlo[j * LDL + c] = 0;
-                }
-            } else if (c - B < k) {
-                x = W[(size_t)(i0 + j) * k + (c - B)];
-            }
+            if (c < B) { if (!warm && c < r) x = (T)V[(size_t)(i0 + j) * r + c]; }
+            else if (c - B < k) x = W[(size_t)(i0 + j) * k + (c - B)];
             Xs[j * LDX + c] = x;
         }
         __syncthreads();
-        if (SPLIT && vpart && !warm) {
-            for (int i = 0; i < tn; ++i) {
-                const float a = (float)As[row * LDA + i];
+        for (int i = 0; i < tn; ++i) {
+            const T a = As[row * LDA + i];
 #pragma unroll
-                for (int j = 0; j < CPT; ++j) {
-                    dot2_acc(accv[j], a, (float)Xs[i * LDX + c0 + j]);
-                    acclo[j] = fmaf(a, (float)Xlo[i * LDL + c0 + j], acclo[j]);
-                }
-            }
-        } else {
-            for (int i = 0; i < tn; ++i) {
-                const T a = As[row * LDA + i];
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) acc[j] += a * Xs[i * LDX + c0 + j];
-            }
+            for (int j = 0; j < CPT; ++j) acc[j] += a * Xs[i * LDX + c0 + j];
         }
     }
 #pragma unroll
-    for (int j = 0; j < CPT; ++j)
-        out[j] = (SPLIT && vpart && !warm) ? dw_value(accv[j]) + (double)acclo[j] : (double)acc[j];
+    for (int j = 0; j < CPT; ++j) out[j] = (double)acc[j];
     // the eight threads of a row hold pieces of ||a||^2 (consecutive lanes)
     for (int o = 4; o > 0; o >>= 1) aa += __shfl_xor_sync(0xffffffffu, aa, o);
 }
@@ -1275,7 +1250,6 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
     constexpr int TL = sizeof(T) == 8 ? MB_TILE / 2 : MB_TILE;
     __shared__ T As[MB_ROWS * (TL + 1)];
     __shared__ T Xs[TL * (2 * MEG_KMAX + 1)];
-    __shared__ T Xlo[sizeof(T) == 4 ? TL * (MEG_KMAX + 1) : 1];     // low parts of V (float storage)
     __shared__ double Ps[MB_ROWS][2 * MEG_KMAX + 1];
     __syncthreads();
     const int row = tid >> 3;
@@ -1283,21 +1257,21 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
     switch (k_bucket(k)) {
         case 8: {
             double out[2];
-            meas_batch_tile<T, 8>(s, lb, warm, sidx, As, Xs, Xlo, out, aa);
+            meas_batch_tile<T, 8>(s, lb, warm, sidx, As, Xs, out, aa);
             for (int j = 0; j < 2; ++j) Ps[row][(tid & 7) * 2 + j] = out[j];
             if ((tid & 7) == 0) Ps[row][2 * MEG_KMAX] = (double)aa;
             break;
         }
         case 16: {
             double out[4];
-            meas_batch_tile<T, 16>(s, lb, warm, sidx, As, Xs, Xlo, out, aa);
+            meas_batch_tile<T, 16>(s, lb, warm, sidx, As, Xs, out, aa);
             for (int j = 0; j < 4; ++j) Ps[row][(tid & 7) * 4 + j] = out[j];
             if ((tid & 7) == 0) Ps[row][2 * MEG_KMAX] = (double)aa;
             break;
         }
         default: {
             double out[8];
-            meas_batch_tile<T, 32>(s, lb, warm, sidx, As, Xs, Xlo, out, aa);
+            meas_batch_tile<T, 32>(s, lb, warm, sidx, As, Xs, out, aa);
             for (int j = 0; j < 8; ++j) Ps[row][(tid & 7) * 8 + j] = out[j];
             if ((tid & 7) == 0) Ps[row][2 * MEG_KMAX] = (double)aa;
             break;

@@ -66,7 +66,7 @@ enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_DTC 
 // measurements) is split into up to MEAS_CHUNKS chunks whose partial
 // products k_combine sums in chunk order.
 #define MB_ROWS 32
-#define MB_TILE 32
+#define MB_TILE 64
 #define MA_ROWS 64
 #define MA_CHUNK 256
 #define MEAS_CHUNKS 16
