@@ -539,6 +539,10 @@ def run_gpu(args):
             single = single_solve_rate(probs[0], device)
         except Exception as ex:  # reported, never fatal
             single = {"error": repr(ex)}
+        try:
+            others = other_kernel_rooflines(device, stream.cuda_stream, hbm_peak)
+        except Exception as ex:  # reported, never fatal
+            others = {"error": repr(ex)[:300]}
         cpu_rate, cores, it, el = oracle_sample(args.cpu_seconds)
         serving = None
         if args.serve_requests > 0:
@@ -579,6 +583,7 @@ def run_gpu(args):
                                        f"n={N} instance in {el:.1f} s"},
             "fp32_torch_form": fp32_form,
             "single_solve": single,
+            "other_kernels": others,
             "serving": serving,
         }
     group.meg_group_destroy()
@@ -588,6 +593,53 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def other_kernel_rooflines(device, stream, hbm_peak):
+    """Gradient-product kernels of the other workloads at their full sizes, each
+    timed alone (CUDA events around back-to-back launches, warm):
+      * n = 20000 matrix completion (1% of the upper triangle, mirrored): the
+        fused SDDMM + SpMM pass reads each stored entry's column index and
+        value once (8 bytes); the rows of V and W it gathers (n (r + k) words)
+        stay in L2;
+      * n = 2048 stochastic measurements (m = 50000, L = 256): the implicit
+        minibatch product A_B^T (r o (A_B W)) reads the L gathered rows of A
+        (bf16) twice, 4 L n k flops; the explicit SYRK form would be n(n+1)L."""
+    import torch
+    import synth
+    from paper_2012_10469_gb300 import binding as B
+    out = {}
+    prob = synth.config(2)
+    nnz = int(len(prob.col))
+    s = B.Solve(prob.n, 8, p=8, q=6, precision=B.MEG_FP32, seed=1002, stream=stream, V0=prob.U, lam0=prob.w)
+    rp = torch.from_numpy(prob.rowptr.astype(np.int32)).to(device)
+    cl = torch.from_numpy(prob.col.astype(np.int32)).to(device)
+    vl = torch.from_numpy(prob.val.astype(np.float32)).to(device)
+    s.meg_set_objective(B.MEG_CSR_QUAD, rowptr=rp, col=cl, val=vl)
+    g = B.Group([s], stream=stream)
+    ms = g.meg_group_time_product(50)
+    alg = nnz * 8 + (prob.n + 1) * 4
+    out["csr_product_n20000"] = {"bound": "hbm", "ms_per_launch": ms, "bytes_per_launch": alg,
+                                 "achieved_GBs": alg / (ms / 1e3) / 1e9,
+                                 "frac": alg / (ms / 1e3) / 1e9 / hbm_peak, "nnz": nnz}
+    g.meg_group_destroy()
+    s.meg_destroy()
+    prob = synth.config(3)
+    n, L, k = prob.n, prob.L, 4 + 8
+    s = B.Solve(n, 4, p=8, q=6, precision=B.MEG_MIXED_BF16, eta=1.0 / (4 * (1 + n / L)), seed=1003, stream=stream,
+                V0=prob.U, lam0=np.full(4, 0.25))
+    A = torch.from_numpy(np.ascontiguousarray(prob.bits().view(np.int16))).to(device)
+    y = torch.from_numpy(prob.y).to(device)
+    s.meg_set_objective(B.MEG_MEAS_STOCH, A=A, y=y, L=L)
+    g = B.Group([s], stream=stream)
+    ms = g.meg_group_time_product(50)
+    alg = 2 * L * n * 2
+    out["minibatch_product_n2048"] = {"bound": "latency (L2-resident batch)", "ms_per_launch": ms,
+                                      "bytes_per_launch": alg, "achieved_GBs": alg / (ms / 1e3) / 1e9,
+                                      "flops_implicit": 4 * L * n * k, "flops_explicit_syrk": n * (n + 1) * L}
+    g.meg_group_destroy()
+    s.meg_destroy()
+    return out
 
 
 def single_solve_rate(prob, device, iters: int = 200):

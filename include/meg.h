@@ -217,8 +217,8 @@ meg_status meg_group_create(const meg_handle* solves, int count, void* stream, m
 meg_status meg_group_step(meg_group g, int nsteps);
 meg_status meg_group_destroy(meg_group g);
 
-/* Profiling: average device time of the group's gradient-product kernel
- * (the dense or CSR product that dominates an iteration), from `reps`
+/* Profiling: average device time of the group's gradient-product kernels
+ * (the dense or CSR product, or the two minibatch passes), from `reps`
  * back-to-back launches between two CUDA events on the group's stream.
  * The launches compute the product for the current W and leave the
  * solves' iterates unchanged.  Synchronises the stream. */

@@ -1081,15 +1081,119 @@ __global__ void __launch_bounds__(NT) k_dense(const SolveDev* sds, int ns) {
 // R_ij = X_ij - M_ij formed on the fly from the factors (never stored).
 // One warp per row.  Also sum of R_ij^2 (for the shift bound of the next
 // iteration), reduced deterministically through per-block partials.
-template <typename T>
-__global__ void __launch_bounds__(NT) k_csr(const SolveDev* sds, int ns) {
+// Float rows of V and W for the sparse product of the float-storage modes,
+// padded to a multiple of 4 floats (16-byte aligned: one row is a few
+// vector loads), in the solve's scratch after the row-block maxima.
+__host__ __device__ __forceinline__ int csr_pad4(int x) { return (x + 3) & ~3; }
+__device__ __forceinline__ float* csr_vf(const SolveDev& s) { return (float*)(s.meas + ((s.nb_csr + 1) & ~1)); }
+__device__ __forceinline__ float* csr_wf(const SolveDev& s) { return csr_vf(s) + (size_t)s.n * csr_pad4(s.r); }
+
+// One row i of the sparse product, KB = k_bucket(k) >= k > r: each lane takes
+// every 32nd stored entry (i, j) of the row, forms R = X_ij - M_ij from the
+// gathered row j of V and adds R W[j][:] into its own k running sums; the
+// warp then sums the lanes' vectors.  Float storage gathers the padded float
+// rows (vector loads); float64 storage the rows of V and W themselves.
+// Returns sum_j |R_ij| (on every lane).
+template <typename T, int KB>
+__device__ __forceinline__ double csr_row(const SolveDev& s, int i, const double* coef, int lane) {
+    const int r = s.r, k = s.k;
+    const T* val = (const T*)s.val;
+    T vi[KB], z[KB];
+#pragma unroll
+    for (int l = 0; l < KB; ++l) {
+        // V_il (mu_l - s) formed in float64 and rounded once: the rounding errors are
+        // independent across (i, l) instead of a shared error in (mu_l - s)
+        vi[l] = l < r ? (T)(s.V[(size_t)i * r + l] * coef[l]) : (T)0;
+        z[l] = 0;
+    }
+    const T sd = (T)coef[MEG_RMAX];
+    double rabs = 0.0;
+    const int b = s.rowptr[i], e = s.rowptr[i + 1];
+#pragma unroll 2
+    for (int p = b + lane; p < e; p += 32) {
+        const int j = s.col[p];
+        T x = (j == i) ? sd : (T)0;
+        T R;
+        if constexpr (sizeof(T) == 4) {
+            const float4* vj = (const float4*)(csr_vf(s) + (size_t)j * csr_pad4(r));
+#pragma unroll
+            for (int l4 = 0; l4 < KB / 4; ++l4)
+                if (4 * l4 < r) {
+                    const float4 v = vj[l4];
+                    x += vi[4 * l4] * v.x + vi[4 * l4 + 1] * v.y + vi[4 * l4 + 2] * v.z + vi[4 * l4 + 3] * v.w;
+                }
+            R = x - val[p];
+            const float4* wj = (const float4*)(csr_wf(s) + (size_t)j * csr_pad4(k));
+#pragma unroll
+            for (int c4 = 0; c4 < KB / 4; ++c4)
+                if (4 * c4 < k) {
+                    const float4 w = wj[c4];
+                    z[4 * c4] += R * w.x;
+                    z[4 * c4 + 1] += R * w.y;
+                    z[4 * c4 + 2] += R * w.z;
+                    z[4 * c4 + 3] += R * w.w;
+                }
+        } else {
+            const T* vj = (const T*)s.V + (size_t)j * r;
+#pragma unroll
+            for (int l = 0; l < KB; ++l)
+                if (l < r) x += vi[l] * vj[l];
+            R = x - val[p];
+            const T* wj = (const T*)s.W + (size_t)j * k;
+#pragma unroll
+            for (int c = 0; c < KB; ++c)
+                if (c < k) z[c] += R * wj[c];
+        }
+        rabs += fabs((double)R);
+    }
+    T mine = 0;
+#pragma unroll
+    for (int c = 0; c < KB; ++c)
+        if (c < k) {
+            T v = z[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == c) mine = v;
+        }
+    if (lane < k) ((T*)s.Y)[(size_t)i * k + lane] = mine;
+    for (int o = 16; o > 0; o >>= 1) rabs += __shfl_xor_sync(0xffffffffu, rabs, o);
+    return rabs;
+}
+
+// The padded float rows of V and W for the block's rows (one pass per product).
+__global__ void __launch_bounds__(NT) k_csr_prep(const SolveDev* sds, int ns) {
     pdl_wait();
     pdl_trigger();
     const int si = find_solve(sds, ns, PK_CSR, blockIdx.x);
     const SolveDev& s = sds[si];
     const int lb = blockIdx.x - s.off[PK_CSR];
     if (lb < 0 || lb >= s.nb_csr) return;
-    const int n = s.n, k = s.k, r = s.r;
+    const int r = s.r, k = s.k, rs = csr_pad4(r), ks = csr_pad4(k);
+    const int row0 = lb * (NT / 32), nr = min(NT / 32, s.n - row0);
+    float* Vf = csr_vf(s);
+    float* Wf = csr_wf(s);
+    const float* W = (const float*)s.W;
+    for (int e = threadIdx.x; e < nr * rs; e += NT) {
+        const int q = e / rs, l = e % rs;
+        Vf[(size_t)(row0 + q) * rs + l] = l < r ? (float)s.V[(size_t)(row0 + q) * r + l] : 0.f;
+    }
+    for (int e = threadIdx.x; e < nr * ks; e += NT) {
+        const int q = e / ks, c = e % ks;
+        Wf[(size_t)(row0 + q) * ks + c] = c < k ? W[(size_t)(row0 + q) * k + c] : 0.f;
+    }
+}
+
+// Matrix completion: Y = P_Omega(X - M) W, fused (the residual of each stored
+// entry is formed on the fly and never stored), one warp per row; also the
+// row abs-sums of the residual, whose maximum bounds ||P_Omega(X - M)||_2.
+template <typename T>
+__global__ void __launch_bounds__(NT, 3) k_csr(const SolveDev* sds, int ns) {
+    pdl_wait();
+    pdl_trigger();
+    const int si = find_solve(sds, ns, PK_CSR, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_CSR];
+    if (lb < 0 || lb >= s.nb_csr) return;
+    const int n = s.n, r = s.r;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = lb * (NT / 32) + warp;
     __shared__ double coef[MEG_RMAX + 1];
@@ -1098,50 +1202,40 @@ __global__ void __launch_bounds__(NT) k_csr(const SolveDev* sds, int ns) {
     if (threadIdx.x < r) coef[threadIdx.x] = warm ? 0.0 : s.sm[SM_MU + threadIdx.x] - s.sm[SM_S];
     if (threadIdx.x == 0) coef[MEG_RMAX] = warm ? 0.0 : s.sm[SM_S];
     __syncthreads();
-    const double* V = s.V;
-    const T* W = (const T*)s.W;
-    const T* val = (const T*)s.val;
     double rabs = 0.0;        // sum_j |R_ij| of this row: ||P_Omega(X - M)||_2 <= max_i of it
     if (i < n) {
-        T vi[MEG_RMAX];
-        // V_il (mu_l - s) formed in float64 and rounded once: the rounding errors are
-        // independent across (i, l) instead of a shared error in (mu_l - s)
-        for (int l = 0; l < r; ++l) vi[l] = (T)(V[(size_t)i * r + l] * coef[l]);
-        T z[MEG_KMAX];
-        for (int c = 0; c < k; ++c) z[c] = 0;
-        const int b = s.rowptr[i], e = s.rowptr[i + 1];
-        for (int p = b + lane; p < e; p += 32) {
-            const int j = s.col[p];
-            T x = (j == i) ? (T)coef[MEG_RMAX] : (T)0;
-            for (int l = 0; l < r; ++l) x += vi[l] * (T)V[(size_t)j * r + l];
-            const T R = x - val[p];
-            rabs += fabs((double)R);
-            for (int c = 0; c < k; ++c) z[c] += R * W[(size_t)j * k + c];
-        }
-        for (int c = 0; c < k; ++c) {
-            T v = z[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) ((T*)s.Y)[(size_t)i * k + c] = v;
+        switch (k_bucket(s.k)) {
+            case 8: rabs = csr_row<T, 8>(s, i, coef, lane); break;
+            case 16: rabs = csr_row<T, 16>(s, i, coef, lane); break;
+            default: rabs = csr_row<T, 32>(s, i, coef, lane); break;
         }
     }
-    for (int o = 16; o > 0; o >>= 1) rabs += __shfl_xor_sync(0xffffffffu, rabs, o);
     if (lane == 0) wsum[warp] = rabs;
     __syncthreads();
+    __shared__ int am_last;
+    double* pr = s.meas;                      // CSR kinds use the scratch for row-block maxima
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < NT / 32; ++w) t = fmax(t, wsum[w]);
-        double* pr = s.meas;                  // CSR kinds use the scratch for row-block sums
         pr[lb] = t;
         __threadfence();
         unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 1;
-        unsigned prev = atomicAdd(c, 1u);
-        if (prev == (unsigned)(s.nb_csr - 1)) {
-            *c = 0u;
-            double tot = 0.0;
-            for (int q = 0; q < s.nb_csr; ++q) tot = fmax(tot, __ldcg(pr + q));
-            s.sm[SM_RSS] = tot;
-        }
+        am_last = (atomicAdd(c, 1u) == (unsigned)(s.nb_csr - 1));
+        if (am_last) *c = 0u;
     }
+    __syncthreads();
+    if (!am_last) return;
+    // last block: the maximum over every block, all threads (a max is order-free)
+    __shared__ double red[NT];
+    double t = 0.0;
+    for (int q = threadIdx.x; q < s.nb_csr; q += NT) t = fmax(t, __ldcg(pr + q));
+    red[threadIdx.x] = t;
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + h]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) s.sm[SM_RSS] = red[0];
 }
 
 // ==========================================================================
@@ -1658,6 +1752,8 @@ cudaError_t launch_dense(const GroupLaunch& g) {
 cudaError_t launch_csr(const GroupLaunch& g) {
     const dim3 grid(g.blocks[PK_CSR]), blk(NT);
     if (g.prec == MEG_FP64) return launch_k(k_csr<double>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
+    cudaError_t e = launch_k(k_csr_prep, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
+    if (e != cudaSuccess) return e;
     return launch_k(k_csr<float>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
 }
 

@@ -499,7 +499,11 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     if (o->kind == MEG_MEAS_STOCH || o->kind == MEG_CSR_QUAD) {
         // minibatch scratch: [Lb] residuals, [Lb] ||a||^2, [Lb x 32] a^T W, one partial bound per block
         const size_t lbm = (size_t)std::max<int64_t>(o->m, o->L);
-        size_t cnt = o->kind == MEG_MEAS_STOCH ? lbm * (2 + MEG_KMAX) + lbm / MB_ROWS + 1 : (size_t)d.nb_csr;
+        // CSR: one maximum per row block (rounded up to 16 bytes), then V and W as
+        // float rows padded to a multiple of 4 for the sparse product
+        const size_t pad4r = (size_t)((h->r + 3) & ~3), pad4k = (size_t)((k + 3) & ~3);
+        size_t cnt = o->kind == MEG_MEAS_STOCH ? lbm * (2 + MEG_KMAX) + lbm / MB_ROWS + 1
+                                               : (size_t)((d.nb_csr + 1) & ~1) + ((size_t)n * (pad4r + pad4k) + 1) / 2;
         if (h->meas) cudaFreeAsync(h->meas, h->stream);
         if (h->bidx) cudaFreeAsync(h->bidx, h->stream);
         h->meas = nullptr; h->bidx = nullptr;
@@ -992,13 +996,17 @@ meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch) {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     // one untimed launch, then `reps` back-to-back launches between two events
-    if (g->has_dense) CU(launch_dense(g->gl));
-    if (g->has_csr) CU(launch_csr(g->gl));
+    auto product = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (g->has_dense && (e = launch_dense(g->gl)) != cudaSuccess) return e;
+        if (g->has_csr && (e = launch_csr(g->gl)) != cudaSuccess) return e;
+        if (g->has_meas && (e = launch_meas_batch(g->gl)) != cudaSuccess) return e;
+        if (g->has_meas && (e = launch_meas_apply(g->gl)) != cudaSuccess) return e;
+        return e;
+    };
+    CU(product());
     CU(cudaEventRecord(e0, g->stream));
-    for (int i = 0; i < reps; ++i) {
-        if (g->has_dense) CU(launch_dense(g->gl));
-        if (g->has_csr) CU(launch_csr(g->gl));
-    }
+    for (int i = 0; i < reps; ++i) CU(product());
     CU(cudaEventRecord(e1, g->stream));
     CU(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -1016,7 +1024,8 @@ int meg_group_kernels_per_step(meg_group g) {
     // the two minibatch passes, and combine / orth1 / orth2, each a row kernel
     // followed by an island kernel; plus the begin kernel once per iteration
     const int dense = g->gl.tc_chunks + (g->gl.blocks[PK_DENSE] > 0 ? 1 : 0);
-    const int per = dense + (g->has_csr ? 1 : 0) + (g->has_meas ? 2 : 0) + 6;
+    const int csr = g->has_csr ? (g->gl.prec == MEG_FP64 ? 1 : 2) : 0;   // float modes: V cast + product
+    const int per = dense + csr + (g->has_meas ? 2 : 0) + 6;
     return g->q * per + 1;
 }
 
