@@ -499,6 +499,8 @@ def run_gpu(args):
 
     # ---- dominant kernel: grouped dense product, timed alone with CUDA events
     prod_ms = group.meg_group_time_product(20)
+    # ---- the kernels after an intermediate product, each timed alone (warm)
+    chain_us = group.meg_group_time_chain(20)
     hbm_peak, peak_kind = peaks()
     alg = algorithmic_bytes_dense_product()
     achieved = alg / (prod_ms / 1e3) / 1e9
@@ -581,6 +583,10 @@ def run_gpu(args):
             "cpu_baseline": {"value": cpu_rate, "unit": "iters/s", "cores": cores, "kind": "oracle",
                              "sample": f"{it} oracle iterations (float64, subspace eigensolver) of one "
                                        f"n={N} instance in {el:.1f} s"},
+            "chain_us": {"what": "warm microseconds per launch of the kernels after an intermediate product, "
+                                 "each timed alone (back-to-back launches), all 8 solves",
+                         **dict(zip(("combine", "factor_1", "orth1", "factor_2", "orth2", "reduce_U_G"),
+                                    [round(v, 2) for v in chain_us]))},
             "fp32_torch_form": fp32_form,
             "single_solve": single,
             "other_kernels": others,

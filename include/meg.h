@@ -224,6 +224,20 @@ meg_status meg_group_destroy(meg_group g);
  * solves' iterates unchanged.  Synchronises the stream. */
 meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch);
 
+/* meg_group_time_chain -- profiling aid: the warm duration, in microseconds,
+ * of each kernel of the chain that follows an intermediate product of the
+ * subspace iteration (Section 3: the mirror operator, then CholeskyQR2):
+ * us[0] the row kernel forming Z = (M_t - c I) W and the partials of Z^T Z,
+ * us[1] its per-solve kernel (first factor), us[2] W' = Z M1 with the
+ * partials of W'^T W', us[3] the second factor, us[4] W = W' M2 with the
+ * partials of V^T W and W^T W, us[5] their reduction.  Each kernel is
+ * launched `reps` times back-to-back between two CUDA events on the group's
+ * stream after one untimed launch.  W, its split and the solves' small
+ * state are copied aside first and restored afterwards, so the iterates and
+ * the next step are unchanged.  us must hold 6 floats.  Synchronises the
+ * group's stream.  MEG_ERR_OOM if the copies cannot be allocated. */
+meg_status meg_group_time_chain(meg_group g, int reps, float* us);
+
 /* Number of kernels one meg_group_step iteration launches. */
 int meg_group_kernels_per_step(meg_group g);
 

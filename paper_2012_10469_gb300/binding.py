@@ -115,6 +115,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_footprint": (C.c_int64, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
         "meg_group_time_product": (C.c_int, [H, C.c_int, _P(C.c_float)]),
         "meg_group_kernels_per_step": (C.c_int, [H]),
+        "meg_group_time_chain": (C.c_int, [H, C.c_int, _P(C.c_float)]),
         "meg_objective_dense_noalloc": (C.c_int, [C.c_void_p, _P(C.c_double), C.c_double, C.c_int, C.c_int,
                                                   C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
         "meg_group_launch": (C.c_int, [H, C.c_int]),
@@ -293,6 +294,13 @@ class Group:
         ms = C.c_float()
         _check(load().meg_group_time_product(self.g, reps, C.byref(ms)), "meg_group_time_product")
         return ms.value
+
+    def meg_group_time_chain(self, reps: int = 20) -> list:
+        """Warm microseconds of each kernel after an intermediate product:
+        [combine, its island, orth1, its island, orth2, its island]."""
+        us = (C.c_float * 6)()
+        _check(load().meg_group_time_chain(self.g, reps, us), "meg_group_time_chain")
+        return [float(v) for v in us]
 
     def meg_group_kernels_per_step(self) -> int:
         return int(load().meg_group_kernels_per_step(self.g))

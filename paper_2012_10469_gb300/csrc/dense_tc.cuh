@@ -17,6 +17,8 @@ struct TcMaps {
 #define TC_YS_SLOTS 8       // partial slots per solve: a tile is cut into at most this many segments
 
 cudaError_t tc_init();
+// resident CTAs of a launch over T chunks per SM (1 or 2); the ring shrinks to fit
+int tc_ctas_per_sm(long long T, int sms);
 bool tc_make_maps(const void* D, int n, const void* Wsp, int kpad, int npad, CUtensorMap* a, CUtensorMap* b);
 // T = chunks of the launch (sum over its solves of row tiles x K chunks), G = CTAs
 cudaError_t launch_dense_tc(const SolveDev* d_solves, int ns, long long T, int G, int npad_max, const TcMaps& maps,

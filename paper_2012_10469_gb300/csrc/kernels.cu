@@ -1797,6 +1797,29 @@ cudaError_t launch_orth2(const GroupLaunch& g, int phase) {
     return launch_row_island<float>(k_orth2<float>, k_island_o2<float>, g, orth2_smem(g.prec), phase);
 }
 
+// one kernel of the chain after a product, for timing: 0 combine, 1 its island,
+// 2 orth1, 3 its island, 4 orth2, 5 its island
+cudaError_t launch_chain_kernel(const GroupLaunch& g, int which, int phase) {
+    const bool f64 = g.prec == MEG_FP64;
+    switch (which) {
+    case 0:
+        return f64 ? launch_clustered<double>(k_combine<double>, g, combine_smem(g.prec), phase)
+                   : launch_clustered<float>(k_combine<float>, g, combine_smem(g.prec), phase);
+    case 2:
+        return f64 ? launch_clustered<double>(k_orth1<double>, g, orth1_smem(g.prec), phase)
+                   : launch_clustered<float>(k_orth1<float>, g, orth1_smem(g.prec), phase);
+    case 4:
+        return f64 ? launch_clustered<double>(k_orth2<double>, g, orth2_smem(g.prec), phase)
+                   : launch_clustered<float>(k_orth2<float>, g, orth2_smem(g.prec), phase);
+    default: break;
+    }
+    void (*isl)(const SolveDev*, int, int) =
+        which == 1 ? (f64 ? k_island_c<double> : k_island_c<float>)
+                   : which == 3 ? (f64 ? k_island_o1<double> : k_island_o1<float>)
+                                : (f64 ? k_island_o2<double> : k_island_o2<float>);
+    return launch_k(isl, dim3(g.ns), dim3(NT), island_smem(), g.stream, 1, g.d_solves, g.ns, phase);
+}
+
 cudaError_t launch_objective(const GroupLaunch& g, double* out_f) {
     const dim3 grid(g.blocks[PK_RED]), blk(NT);
     if (g.prec == MEG_FP64) return launch_k(k_objective<double>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns, out_f, 0);

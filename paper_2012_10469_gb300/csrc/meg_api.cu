@@ -65,12 +65,13 @@ int num_sms() {
 long long tc_chunks_of(const SolveDev& d) { return (long long)d.nb_tm * (d.tc_kpad / 64); }
 
 // CTAs of a stream-K launch over T chunks whose tiles have at most nkb_max
-// chunks: one per SM, fewer when a CTA's share would be so short that a tile
+// chunks: one or two per SM, fewer when a CTA's share would be so short that a tile
 // could be cut into more than TC_YS_SLOTS segments (a share of at least
 // ceil(nkb_max / (slots - 1)) chunks meets at most `slots` CTAs per tile).
 int tc_grid(long long T, int nkb_max) {
     const long long need = (nkb_max + TC_YS_SLOTS - 2) / (TC_YS_SLOTS - 1);
-    const long long G = std::min<long long>(num_sms(), T / std::max<long long>(1, need));
+    const long long G = std::min<long long>((long long)num_sms() * tc_ctas_per_sm(T, num_sms()),
+                                            T / std::max<long long>(1, need));
     return (int)std::max<long long>(1, G);
 }
 
@@ -1014,6 +1015,58 @@ meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *ms_per_launch = ms / reps;
+    return MEG_OK;
+}
+
+meg_status meg_group_time_chain(meg_group g, int reps, float* us) {
+    if (!g || reps < 1 || !us) return fail(MEG_ERR_INVALID_ARG, "meg_group_time_chain: arguments");
+    // the kernels rewrite W, its bf16 split and the small-slot state: copy them
+    // aside and put them back afterwards (the other buffers they write are scratch)
+    std::vector<std::pair<void*, size_t>> regions;
+    for (auto* h : g->solves) {
+        regions.push_back({h->W, tsize(h->prec) * h->n * h->k});
+        regions.push_back({h->sm, sizeof(double) * SM_TOTAL});
+        if (h->Wsp) regions.push_back({h->Wsp, (size_t)2 * h->desc.tc_npad * h->desc.tc_kpad});
+    }
+    size_t total = 0;
+    for (auto& r : regions) total += (r.second + 255) / 256 * 256;
+    char* keep = nullptr;
+    if (cudaMallocAsync((void**)&keep, total, g->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MEG_ERR_OOM, "meg_group_time_chain: scratch");
+    }
+    auto copy = [&](bool back) -> cudaError_t {
+        size_t o = 0;
+        for (auto& r : regions) {
+            cudaError_t e = back ? cudaMemcpyAsync(r.first, keep + o, r.second, cudaMemcpyDeviceToDevice, g->stream)
+                                 : cudaMemcpyAsync(keep + o, r.first, r.second, cudaMemcpyDeviceToDevice, g->stream);
+            if (e != cudaSuccess) return e;
+            o += (r.second + 255) / 256 * 256;
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = copy(false);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int w = 0; w < 6 && e == cudaSuccess; ++w) {
+        for (int i = 0; i <= reps && e == cudaSuccess; ++i) {      // one untimed launch first
+            if (i == 1) e = cudaEventRecord(e0, g->stream);
+            if (e == cudaSuccess) e = launch_chain_kernel(g->gl, w, PH_ADVANCE);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        us[w] = 1000.f * ms / reps;
+    }
+    const cudaError_t e2 = copy(true);
+    if (e == cudaSuccess) e = e2;
+    cudaFreeAsync(keep, g->stream);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("meg_group_time_chain: ") + cudaGetErrorString(e));
     return MEG_OK;
 }
 
