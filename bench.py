@@ -584,9 +584,11 @@ def run_gpu(args):
                              "sample": f"{it} oracle iterations (float64, subspace eigensolver) of one "
                                        f"n={N} instance in {el:.1f} s"},
             "chain_us": {"what": "warm microseconds per launch of the kernels after an intermediate product, "
-                                 "each timed alone (back-to-back launches), all 8 solves",
-                         **dict(zip(("combine", "factor_1", "orth1", "factor_2", "orth2", "reduce_U_G"),
-                                    [round(v, 2) for v in chain_us]))},
+                                 "each timed alone (back-to-back launches), all 8 solves; one CholeskyQR pass "
+                                 "(float storage)",
+                         **{name: round(v, 2) for name, v in
+                            zip(("combine", "factor", "orth", "factor_2", "orth_2", "reduce_U_G"), chain_us)
+                            if v > 0}},
             "fp32_torch_form": fp32_form,
             "single_solve": single,
             "other_kernels": others,

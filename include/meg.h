@@ -228,9 +228,12 @@ meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch);
  * of each kernel of the chain that follows an intermediate product of the
  * subspace iteration (Section 3: the mirror operator, then CholeskyQR2):
  * us[0] the row kernel forming Z = (M_t - c I) W and the partials of Z^T Z,
- * us[1] its per-solve kernel (first factor), us[2] W' = Z M1 with the
- * partials of W'^T W', us[3] the second factor, us[4] W = W' M2 with the
- * partials of V^T W and W^T W, us[5] their reduction.  Each kernel is
+ * us[1] its per-solve kernel (the CholeskyQR factor).  Float64 storage
+ * (two CholeskyQR passes): us[2] W' = Z M1 with the partials of W'^T W',
+ * us[3] the second factor, us[4] W = W' M2 with the partials of V^T W and
+ * W^T W.  Float storage (one pass): us[2] W = Z M1 with those partials,
+ * us[3] = us[4] = 0 (not launched).  us[5] the reduction of V^T W and
+ * W^T W.  Each kernel is
  * launched `reps` times back-to-back between two CUDA events on the group's
  * stream after one untimed launch.  W, its split and the solves' small
  * state are copied aside first and restored afterwards, so the iterates and

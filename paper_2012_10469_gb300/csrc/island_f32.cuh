@@ -1,7 +1,9 @@
 // k x k island in float32 with double-word refinement, for the float-storage
 // precision modes.  GB300 runs float64 at about 1/58 of the float32 rate, so
-// the Cholesky factors of CholeskyQR2 are computed in float32 (equilibrated,
-// one warp) and the Rayleigh-Ritz eigenproblem is solved by float32 Jacobi
+// the k x k work stays in one warp's registers: the CholeskyQR factor
+// (equilibrated; float64 for the single pass of the float-storage modes,
+// float32 where a second pass follows) and the Rayleigh-Ritz eigenproblem,
+// solved by float32 Jacobi
 // rotations followed by a refinement whose products are exact (Dot2):
 // Rayleigh quotients for the Ritz values and a first-order correction of
 // the top-r Ritz vectors.  All routines are called by every thread of the
@@ -11,72 +13,87 @@
 #include "meg_dev.cuh"
 
 // ---------------------------------------------------------------------------
-// A (k x k SPD, float) -> M = L^{-T} with A = L L^T, computed on the
-// equilibrated matrix B = D A D (D = diag(A)^{-1/2}): B = Lb Lb^T,
-// L = D^{-1} Lb, L^{-T} = D Lb^{-T}.  Warp 0 only, in registers: lane i
-// holds row i of B (then of Lb) and column i of X = Lb^{-1}; the entries
-// other lanes need travel by warp shuffles.  The order KP is k rounded up to
-// a multiple of 8 and fixed at compile time, B padded with the identity, so
-// every loop is straight-line code; pivots use the hardware reciprocal
-// square root (one or two units in the last place, removed by the second
-// CholeskyQR pass).  Returns false on a non-positive pivot (M then holds the
-// identity).  A is not modified.
-template <int KP>
-__device__ __forceinline__ void chol_inv_f32_k(const float* A, float* M, float* dsc, int k, int* flag) {
+// A (k x k SPD) -> M = L^{-T} with A = L L^T, computed on the equilibrated
+// matrix B = D A D (D = diag(A)^{-1/2}): B = Lb Lb^T, L = D^{-1} Lb,
+// L^{-T} = D Lb^{-T}.  Warp 0 only, in registers: lane i holds row i of B
+// (then of Lb) and column i of X = Lb^{-1}; the entries other lanes need
+// travel by warp shuffles.  The order KP is k rounded up to a multiple of 8
+// and fixed at compile time, B padded with the identity, so every loop is
+// straight-line code.  F = float: pivots from the hardware reciprocal square
+// root (one or two units in the last place; used where a second CholeskyQR
+// pass follows); F = double: correctly rounded square roots and divisions,
+// for the single CholeskyQR pass of the float-storage modes, whose factor
+// must hold the accuracy of a double-word Gram.  Returns false on a
+// non-positive pivot (M then holds the identity).  A is not modified.
+template <typename F> __device__ __forceinline__ F chol_rsqrt(F d);
+template <> __device__ __forceinline__ float chol_rsqrt<float>(float d) { return rsqrtf(d); }
+template <> __device__ __forceinline__ double chol_rsqrt<double>(double d) { return 1.0 / sqrt(d); }
+template <typename F> __device__ __forceinline__ F chol_rcp(F d);
+template <> __device__ __forceinline__ float chol_rcp<float>(float d) { return __frcp_rn(d); }
+template <> __device__ __forceinline__ double chol_rcp<double>(double d) { return 1.0 / d; }
+
+template <typename F, int KP>
+__device__ __forceinline__ void chol_inv_k(const F* A, F* M, F* dsc, int k, int* flag) {
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    const float dl = (lane < k) ? A[lane * MEG_LDK + lane] : 1.f;
-    const float sl = (lane < k && dl > 0.f) ? rsqrtf(dl) : 0.f;
+    const F one = (F)1, zero = (F)0;
+    const F dl = (lane < k) ? A[lane * MEG_LDK + lane] : one;
+    const F sl = (lane < k && dl > zero) ? chol_rsqrt<F>(dl) : zero;
     if (lane < k) dsc[lane] = sl;
-    float a[KP];
+    F a[KP];
 #pragma unroll
     for (int c = 0; c < KP; ++c) {
-        const float sc = __shfl_sync(full, sl, c);
-        a[c] = (lane < k && c < k) ? A[lane * MEG_LDK + c] * sl * sc : (c == lane ? 1.f : 0.f);
+        const F sc = __shfl_sync(full, sl, c);
+        a[c] = (lane < k && c < k) ? A[lane * MEG_LDK + c] * sl * sc : (c == lane ? one : zero);
     }
     int bad = 0;
     // right-looking Cholesky: column j of Lb, then the trailing update
 #pragma unroll
     for (int j = 0; j < KP; ++j) {
-        float d = __shfl_sync(full, a[j], j);
-        if (!(d > 0.f)) { bad = 1; d = 1.f; }
-        const float inv = rsqrtf(d), pj = d * inv;
+        F d = __shfl_sync(full, a[j], j);
+        if (!(d > zero)) { bad = 1; d = one; }
+        const F inv = chol_rsqrt<F>(d), pj = d * inv;
         a[j] = (lane == j) ? pj : (lane > j ? a[j] * inv : a[j]);
 #pragma unroll
         for (int c = j + 1; c < KP; ++c) {
-            const float lcj = __shfl_sync(full, a[j], c);
-            a[c] = (lane > j) ? fmaf(-a[j], lcj, a[c]) : a[c];
+            const F lcj = __shfl_sync(full, a[j], c);
+            a[c] = (lane > j) ? fma(-a[j], lcj, a[c]) : a[c];
         }
     }
     // X = Lb^{-1}, lane = column: X_ic = (delta_ic - sum_{m<i} L_im X_mc) / L_ii
-    float x[KP];
+    F x[KP];
 #pragma unroll
     for (int i = 0; i < KP; ++i) {
-        float acc = (lane == i) ? 1.f : 0.f;
+        F acc = (lane == i) ? one : zero;
 #pragma unroll
-        for (int m = 0; m < i; ++m) acc = fmaf(-__shfl_sync(full, a[m], i), x[m], acc);
-        x[i] = acc * __frcp_rn(__shfl_sync(full, a[i], i));
+        for (int m = 0; m < i; ++m) acc = fma(-__shfl_sync(full, a[m], i), x[m], acc);
+        x[i] = acc * chol_rcp<F>(__shfl_sync(full, a[i], i));
     }
     // M = D X^T: lane c writes row c (zero left of the diagonal since X is lower)
     if (lane < k) {
 #pragma unroll
         for (int i = 0; i < KP; ++i)
-            if (i < k) M[lane * MEG_LDK + i] = bad ? (i == lane ? 1.f : 0.f) : sl * x[i];
+            if (i < k) M[lane * MEG_LDK + i] = bad ? (i == lane ? one : zero) : sl * x[i];
     }
     if (lane == 0) *flag = bad;
 }
 
-__device__ inline bool chol_inv_f32(const float* A, float* M, float* dsc, int k, int* flag) {
+template <typename F>
+__device__ inline bool chol_inv(const F* A, F* M, F* dsc, int k, int* flag) {
     if (threadIdx.x < 32) {
         switch ((k + 7) >> 3) {
-            case 1: chol_inv_f32_k<8>(A, M, dsc, k, flag); break;
-            case 2: chol_inv_f32_k<16>(A, M, dsc, k, flag); break;
-            case 3: chol_inv_f32_k<24>(A, M, dsc, k, flag); break;
-            default: chol_inv_f32_k<32>(A, M, dsc, k, flag); break;
+            case 1: chol_inv_k<F, 8>(A, M, dsc, k, flag); break;
+            case 2: chol_inv_k<F, 16>(A, M, dsc, k, flag); break;
+            case 3: chol_inv_k<F, 24>(A, M, dsc, k, flag); break;
+            default: chol_inv_k<F, 32>(A, M, dsc, k, flag); break;
         }
     }
     __syncthreads();
     return *flag == 0;
+}
+
+__device__ inline bool chol_inv_f32(const float* A, float* M, float* dsc, int k, int* flag) {
+    return chol_inv<float>(A, M, dsc, k, flag);
 }
 
 // C = op(A) B in float32 (k x k or given shapes)
@@ -179,4 +196,63 @@ __device__ inline int jacobi_warp_f32(float** pA, float* B, float* Q, float* pr,
 __device__ __forceinline__ void dw_split(double v, float& hi, float& lo) {
     hi = (float)v;
     lo = (float)(v - (double)hi);
+}
+
+// ---------------------------------------------------------------------------
+// M (k x k, float) with M^T S M = I to float32 accuracy for a Gram matrix S
+// known to double-word accuracy (given in float64, leading dimension
+// MEG_LDK): the second CholeskyQR pass carried out in Gram space instead of
+// on the n rows.  M1 = L1^{-T} from the float32 Cholesky of S leaves
+// M1^T S M1 = I + E with ||E|| about kappa(S) float rounding units;
+// B = M1^T S M1 is formed with exact products (Dot2 over the (hi, lo) float
+// split of S, then of T = S M1), M2 = L_B^{-T} from the float32 Cholesky of
+// the well-conditioned B, and M = M1 M2 (exact products, returned in
+// float64 to be applied as a (hi, lo) pair) gives M^T S M = M2^T B M2 = I to
+// float accuracy.  F0..F3: four float k x k work matrices; T: a float64 one;
+// M may alias none of them.  Returns false on a non-positive pivot.
+__device__ inline bool gram_factor_f32(const double* S, float* F0, float* F1, float* F2, float* F3, double* T,
+                                       double* M, float* dsc, int k, int* flag) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < k * k; e += nt) {
+        const int i = e / k, j = e - i * k;
+        float hi, lo;
+        dw_split(S[i * MEG_LDK + j], hi, lo);
+        F0[i * MEG_LDK + j] = hi;
+        F1[i * MEG_LDK + j] = lo;
+    }
+    __syncthreads();
+    bool ok = chol_inv<float>(F0, F2, dsc, k, flag);             // M1 in F2
+    for (int e = tid; e < k * k; e += nt) {                     // T = S M1 (exact products)
+        const int i = e / k, j = e - i * k;
+        dw acc = {0.f, 0.f};
+        for (int a = 0; a < k; ++a) {
+            const float m = F2[a * MEG_LDK + j];
+            dot2_acc(acc, F0[i * MEG_LDK + a], m);
+            dot2_acc(acc, F1[i * MEG_LDK + a], m);
+        }
+        T[i * MEG_LDK + j] = dw_value(acc);
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {                     // B = M1^T T (exact products)
+        const int i = e / k, j = e - i * k;
+        dw acc = {0.f, 0.f};
+        for (int a = 0; a < k; ++a) {
+            float hi, lo;
+            dw_split(T[a * MEG_LDK + j], hi, lo);
+            const float m = F2[a * MEG_LDK + i];
+            dot2_acc(acc, m, hi);
+            dot2_acc(acc, m, lo);
+        }
+        F3[i * MEG_LDK + j] = (float)dw_value(acc);
+    }
+    __syncthreads();
+    ok = chol_inv<float>(F3, F1, dsc, k, flag) && ok;            // M2 in F1
+    for (int e = tid; e < k * k; e += nt) {                     // M = M1 M2 (exact products)
+        const int i = e / k, j = e - i * k;
+        dw acc = {0.f, 0.f};
+        for (int a = 0; a < k; ++a) dot2_acc(acc, F2[i * MEG_LDK + a], F1[a * MEG_LDK + j]);
+        M[i * MEG_LDK + j] = dw_value(acc);
+    }
+    __syncthreads();
+    return ok;
 }

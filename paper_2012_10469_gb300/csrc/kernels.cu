@@ -10,7 +10,12 @@
 //   combine  : Z = alpha Y + V (d o U) + (c0 - c) W,  U = V^T W;  Z^T Z, W^T Y
 //              last block: Rayleigh-Ritz on span W (final product), exp-map
 //              (Definition 2), certificate (Lemma 2), CholeskyQR factor
-//   orth1/2  : W <- CholeskyQR2(Z) (two passes), V_{t+1} = W Q_r; V^T W, W^T W
+//   orth1/2  : float64 storage: W <- CholeskyQR2(Z) (two passes), V_{t+1} = W Q_r;
+//              V^T W, W^T W
+//   orth     : float storage: W <- Z L^{-T}, one CholeskyQR pass whose factor is
+//              computed in float64 from the double-word Gram, V_{t+1} = W Q_r;
+//              V^T W, W^T W (the Rayleigh-Ritz step uses the exact Gram of W)
+#include <algorithm>
 #include <cooperative_groups.h>
 #include <cuda_bf16.h>
 #include <math.h>
@@ -256,13 +261,16 @@ __global__ void k_begin(const SolveDev* sds, int ns) {
 
 // ---------------------------------------------------------------------------
 // Rayleigh-Ritz for float storage (float64 results from float32 work).
-//   Ht = G^{-1/2} H G^{-1/2} = H - (E H + H E)/2 + O(E^2),  E = G - I (|E| < 1e-3,
-//        so the neglected terms are below 1e-6 |E| |H|; W is float32-orthonormal)
+//   Ht = G^{-1/2} H G^{-1/2},  E = G - I (|E| < 1e-3: W is orthonormal to about
+//        kappa(Z) float32 units after its CholeskyQR pass), to second order:
+//        G^{-1/2} = I - E/2 + 3 E^2/8 + O(E^3), so
+//        Ht = H - (E H + H E)/2 + 3 (E^2 H + H E^2)/8 + E H E/4 + O(E^3 |H|)
+//        (the second-order terms in float32: they are below 1e-6 |H|)
 //   float32 Jacobi on Ht -> Q
 //   theta_i = q_i^T Ht q_i / q_i^T q_i  with exact (Dot2) products
 //   top r vectors: q_i + sum_j q_j (q_j^T Ht q_i)/(theta_i - theta_j)  (first order;
 //        pairs closer than 100 |q_j^T Ht q_i| are left as they are),
-//        Lowdin re-orthonormalisation, map back x = (I - E/2) q
+//        Lowdin re-orthonormalisation, map back x = (I - E/2 + 3 E^2/8) q
 // Scratch: F (4 float matrices), the double regions C, JB, Bm (G), H.
 // Writes sigma, mu, s, t, certificate, objective estimate, QV, M1 like the
 // float64 island.
@@ -279,7 +287,8 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
     float* Bl = Bh + FM;
     __shared__ int perm[MEG_KMAX];
     __shared__ int flag2;
-    // 1. E, H in float; Ht = H - (E H + (E H)^T)/2 in float64
+    // 1. E, H in float; Ht = H - (T + T^T)/2 + 3 (E T + (E T)^T)/8 + T E/4 in
+    //    float64, T = E H (T E = E H E is symmetric)
     for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e % k;
         F0[i * MEG_LDK + j] = (float)(G[i * MEG_LDK + j] - (i == j ? 1.0 : 0.0));
@@ -287,9 +296,14 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
     }
     __syncthreads();
     mm_f32(F0, false, F1, F2, k, k, k);                       // T = E H
+    mm_f32(F0, false, F2, F1, k, k, k);                       // E T = E^2 H
+    mm_f32(F2, false, F0, F3, k, k, k);                       // T E = E H E
     for (int e = tid; e < k * k; e += nt) {
         const int i = e / k, j = e % k;
-        H[i * MEG_LDK + j] -= 0.5 * ((double)F2[i * MEG_LDK + j] + (double)F2[j * MEG_LDK + i]);
+        const double t1 = (double)F2[i * MEG_LDK + j] + (double)F2[j * MEG_LDK + i];
+        const double t2 = (double)F1[i * MEG_LDK + j] + (double)F1[j * MEG_LDK + i];
+        const double t3 = (double)F3[i * MEG_LDK + j] + (double)F3[j * MEG_LDK + i];
+        H[i * MEG_LDK + j] += -0.5 * t1 + 0.375 * t2 + 0.125 * t3;
     }
     __syncthreads();
     // 2. float32 Jacobi on Ht
@@ -382,11 +396,12 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
         Bh[a * MEG_LDK + i] = (float)v;
     }
     __syncthreads();
-    // 7. back to the W basis: x = (I - E/2) q
+    // 7. back to the W basis: x = (I - E/2 + 3 E^2/8) q
     mm_f32(F0, false, Bh, Bl, k, k, r);                        // E QV (k x r)
+    mm_f32(F0, false, Bl, F1, k, k, r);                        // E^2 QV
     for (int e = tid; e < k * r; e += nt) {
         const int a = e / r, i = e % r;
-        const double v = JB[a * MEG_LDK + i] - 0.5 * (double)Bl[a * MEG_LDK + i];
+        const double v = JB[a * MEG_LDK + i] - 0.5 * (double)Bl[a * MEG_LDK + i] + 0.375 * (double)F1[a * MEG_LDK + i];
         smw[SM_QV + a * 32 + i] = v;
         Bh[a * MEG_LDK + i] = (float)v;
     }
@@ -470,18 +485,65 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
         }
     }
     __syncthreads();
-    // 10. next block: W' = Z Q L^{-T}, L = chol(Q^T S1 Q) (Ritz-ordered, float32)
+    // 10. next block W = Z Q M (Ritz-ordered), M^T (Q^T S1 Q) M = I.  With q > 1
+    //     the next product's CholeskyQR pass restores orthonormality before any
+    //     Rayleigh-Ritz step, so a float32 factor suffices (it changes how
+    //     orthonormal W is, not its span); with q = 1 the Gram Q^T S1 Q is formed
+    //     with exact products and factored by gram_factor_f32, Q M in float64.
     for (int e = tid; e < k * k; e += nt) {
         const int a = e / k, i = e % k;
         F1[a * MEG_LDK + i] = F2[a * MEG_LDK + perm[i]];       // Q, sorted columns
-        F3[a * MEG_LDK + i] = (float)S1[a * MEG_LDK + i];
+        if (s.q > 1) F3[a * MEG_LDK + i] = (float)S1[a * MEG_LDK + i];
     }
     __syncthreads();
-    mm_f32(F3, false, F1, Bh, k, k, k);                        // S1 Q
-    mm_f32(F1, true, Bh, Bl, k, k, k);                         // Q^T S1 Q
-    if (!chol_inv_f32(Bl, F3, (float*)pr, k, &flag2) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
-    mm_f32(F1, false, F3, Bh, k, k, k);                        // M1 = Q L^{-T}
-    for (int e = tid; e < k * k; e += nt) smw[SM_M1 + (e / k) * 32 + e % k] = (double)Bh[(e / k) * MEG_LDK + e % k];
+    if (s.q > 1) {
+        mm_f32(F3, false, F1, Bh, k, k, k);                    // S1 Q
+        mm_f32(F1, true, Bh, Bl, k, k, k);                     // Q^T S1 Q
+        if (!chol_inv_f32(Bl, F3, (float*)pr, k, &flag2) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+        mm_f32(F1, false, F3, Bh, k, k, k);                    // M1 = Q L^{-T}
+        for (int e = tid; e < k * k; e += nt) smw[SM_M1 + (e / k) * 32 + e % k] = (double)Bh[(e / k) * MEG_LDK + e % k];
+        return;
+    }
+    for (int e = tid; e < k * k; e += nt) {                     // C = S1 Q (exact products)
+        const int i = e / k, j = e % k;
+        dw acc = {0.f, 0.f};
+        for (int a = 0; a < k; ++a) {
+            float hi, lo;
+            dw_split(S1[i * MEG_LDK + a], hi, lo);
+            const float q = F1[a * MEG_LDK + j];
+            dot2_acc(acc, hi, q);
+            dot2_acc(acc, lo, q);
+        }
+        C[i * MEG_LDK + j] = dw_value(acc);
+    }
+    __syncthreads();
+    for (int e = tid; e < k * k; e += nt) {                     // H = Q^T C
+        const int i = e / k, j = e % k;
+        dw acc = {0.f, 0.f};
+        for (int a = 0; a < k; ++a) {
+            float hi, lo;
+            dw_split(C[a * MEG_LDK + j], hi, lo);
+            const float q = F1[a * MEG_LDK + i];
+            dot2_acc(acc, q, hi);
+            dot2_acc(acc, q, lo);
+        }
+        H[i * MEG_LDK + j] = dw_value(acc);
+    }
+    __syncthreads();
+    if (!gram_factor_f32(H, F0, F2, F3, Bh, C, JB, (float*)pr, k, &flag2) && tid == 0)
+        smw[SM_STATUS] = MEG_ERR_NUMERIC;
+    for (int e = tid; e < k * k; e += nt) {                     // M1 = Q M (exact products)
+        const int i = e / k, j = e % k;
+        dw acc = {0.f, 0.f};
+        for (int a = 0; a < k; ++a) {
+            float hi, lo;
+            dw_split(JB[a * MEG_LDK + j], hi, lo);
+            const float q = F1[i * MEG_LDK + a];
+            dot2_acc(acc, q, hi);
+            dot2_acc(acc, q, lo);
+        }
+        smw[SM_M1 + i * 32 + j] = dw_value(acc);
+    }
 }
 
 // ==========================================================================
@@ -618,12 +680,15 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
     if (!fin) {
         // W' = Z L^{-T}, L = chol(Z^T Z)
         if constexpr (sizeof(T) == 4) {
-            float* Af = (float*)A;
-            float* Mf = (float*)C;
-            for (int e = tid; e < k * k; e += NT) Af[(e / k) * MEG_LDK + e % k] = (float)S1[(e / k) * MEG_LDK + e % k];
-            __syncthreads();
-            if (!chol_inv_f32(Af, Mf, (float*)pr, k, &flag) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
-            for (int e = tid; e < k * k; e += NT) smw[SM_M1 + (e / k) * 32 + e % k] = (double)Mf[(e / k) * MEG_LDK + e % k];
+            // the only CholeskyQR pass of the float-storage modes: a factor of the
+            // double-word Gram refined in Gram space, so that W = Z M1 is
+            // orthonormal to about kappa(Z) float rounding units (a plain float
+            // factor would leave kappa(Z)^2 of them and need a second pass)
+            float* F = (float*)smraw;                  // the reduction's scratch, free again
+            constexpr int FM = 32 * MEG_LDK;
+            if (!gram_factor_f32(S1, F, F + FM, F + 2 * FM, F + 3 * FM, A, C, (float*)pr, k, &flag) && tid == 0)
+                smw[SM_STATUS] = MEG_ERR_NUMERIC;
+            store_kxk(smw + SM_M1, C, k, k);
         } else {
             for (int e = tid; e < k * k; e += NT) A[(e / k) * MEG_LDK + e % k] = S1[(e / k) * MEG_LDK + e % k];
             __syncthreads();
@@ -658,7 +723,8 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
     __shared__ double mun[MEG_KMAX];
     __shared__ int use_fast;
     if constexpr (sizeof(T) == 4) {
-        // E = G - I; W is orthonormal to float32 accuracy after CholeskyQR2
+        // E = G - I; after the CholeskyQR pass ||E|| is about kappa(Z) float32
+        // rounding units, so second-order terms in E are negligible here
         if (tid < 32) {
             float em = 0.f;
             for (int e = tid; e < k * k; e += 32)
@@ -925,6 +991,150 @@ __global__ void __launch_bounds__(NT) k_orth2(const SolveDev* sds, int ns, int p
         const float vh = (float)v;
         sVh[idx] = vh;
         sVl[idx] = (float)(v - (double)vh);
+    }
+    __syncthreads();
+    if (s.Wsp) {
+        // exact split for the tensor-core product, W = hi + mid + lo in bf16; Wsp is
+        // K-major (row j of a piece holds column j of W), so consecutive threads
+        // take consecutive rows i of W for coalesced stores
+        const size_t kp = (size_t)s.tc_kpad;
+        const size_t P = (size_t)(s.tc_npad / 3);        // rows per piece (k rounded up to 16)
+        for (int idx = tid; idx < nr * k; idx += NT) {
+            const int j = idx / nr, q = idx % nr, i = row0 + q;
+            const float w = (float)sW[q * k + j];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const float r1 = w - __bfloat162float(hi);
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(mid);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
+            s.Wsp[(size_t)j * kp + i] = __bfloat16_as_ushort(hi);
+            s.Wsp[(P + j) * kp + i] = __bfloat16_as_ushort(mid);
+            s.Wsp[(2 * P + j) * kp + i] = __bfloat16_as_ushort(lo);
+        }
+    }
+    const int nsym = k * (k + 1) / 2;
+    const int E = nsym + r * k;
+    for (int e = tid; e < E; e += NT) {
+        Acc<T> a, b;
+        a.zero();
+        b.zero();
+        if (e < nsym) {
+            int i, j;
+            tri_decode(e, i, j);
+            int q = 0;
+            for (; q + 1 < nr; q += 2) {
+                a.add_prod(sW[q * k + i], sW[q * k + j]);
+                b.add_prod(sW[(q + 1) * k + i], sW[(q + 1) * k + j]);
+            }
+            if (q < nr) a.add_prod(sW[q * k + i], sW[q * k + j]);
+        } else {
+            int l = (e - nsym) / k, j = (e - nsym) % k;
+            for (int q = 0; q < nr; ++q) {
+                if constexpr (sizeof(T) == 8) {
+                    a.add_prod(sV[q * r + l], sW[q * k + j]);
+                } else {      // V is float64: two floats per entry, both products exact in Dot2
+                    a.add_prod(sVh[q * r + l], sW[q * k + j]);
+                    b.add_prod(sVl[q * r + l], sW[q * k + j]);
+                }
+            }
+        }
+        dw r0 = a.as_dw();
+        dw_add(r0, b.as_dw());
+        ent[e] = r0;
+    }
+    __syncthreads();
+    write_partial(s, lb, ent, E);
+}
+
+// ==========================================================================
+// orth (float storage): W = Z M1, the single CholeskyQR pass (M1 = L^{-T} of
+// the double-word Gram of Z, factored in float64); on the final product
+// M1 = Qg L^{-T} and V_{t+1} = W Qv is formed from the block's rows of the
+// previous W and committed.  Reductions U = V^T W and G = W^T W for the next
+// product's operator and Rayleigh-Ritz step, and the bf16 split of W for the
+// tensor-core product.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_orth(const SolveDev* sds, int ns, int phase) {
+    pdl_wait();
+    pdl_trigger();
+    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_RED];     // blocks past nb_red pad the last cluster
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const int row0 = min(n, lb * s.rows_red), row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Coef<T>* M1 = (Coef<T>*)smraw;                      // k x k, float64 values as (hi, lo)
+    Coef<T>* Qv = M1 + MEG_KMAX * MEG_KMAX;             // k x r
+    T* sW = (T*)(Qv + MEG_KMAX * MEG_RMAX);             // rows of W (first the previous W)
+    double* sV = (double*)(((uintptr_t)(sW + s.rows_red * k) + 7) & ~(uintptr_t)7);
+    dw* ent = (dw*)(((uintptr_t)(sV + s.rows_red * r) + 15) & ~(uintptr_t)15);
+    // float storage: V as (hi, lo) floats in the area of sV
+    float* sVh = (float*)sV;
+    float* sVl = sVh + s.rows_red * r;
+    const double* sm = s.sm;
+    const bool fin = (phase == PH_FINAL);
+    for (int e = tid; e < k * k; e += NT) M1[e].set(sm[SM_M1 + (e / k) * 32 + e % k]);
+    if (fin)
+        for (int e = tid; e < k * r; e += NT) Qv[e].set(sm[SM_QV + (e / r) * 32 + e % r]);
+    const T* Z = (const T*)s.Z;
+    T* W = (T*)s.W;
+    double* V = s.V;
+    // the block's rows of Z (and of the previous W) are contiguous spans: stage
+    // them (coalesced); Z goes to the entries' buffer, unused until the Gram
+    T* sZ = (T*)ent;
+    for (int idx = tid; idx < nr * k; idx += NT) sZ[idx] = Z[(size_t)row0 * k + idx];
+    if (fin)
+        for (int idx = tid; idx < nr * k; idx += NT) sW[idx] = W[(size_t)row0 * k + idx];
+    __syncthreads();
+    for (int idx = tid; idx < nr * r; idx += NT) {
+        const int q = idx / r, j = idx % r;
+        double v;
+        if (fin) {
+            // V_{t+1} = W Qv evaluated exactly enough to keep X_{t+1} at float64 accuracy
+            if constexpr (sizeof(T) == 8) {
+                v = 0.0;
+                for (int l = 0; l < k; ++l) v = Qv[l * r + j].fma_(sW[q * k + l], v);
+            } else {
+                dw acc = {0.f, 0.f};
+                for (int l = 0; l < k; ++l) {
+                    const float w = sW[q * k + l];
+                    dot2_acc(acc, w, Qv[l * r + j].hi);
+                    dot2_acc(acc, w, Qv[l * r + j].lo);
+                }
+                v = dw_value(acc);
+            }
+            V[(size_t)row0 * r + idx] = v;
+        } else {
+            v = V[(size_t)row0 * r + idx];
+        }
+        if constexpr (sizeof(T) == 8) {
+            sV[idx] = v;
+        } else {
+            const float vh = (float)v;
+            sVh[idx] = vh;
+            sVl[idx] = (float)(v - (double)vh);
+        }
+    }
+    __syncthreads();      // the previous W rows are read
+    for (int idx = tid; idx < nr * k; idx += NT) {
+        const int q = idx / k, j = idx % k;
+        // W = Z M1 with exact products (Dot2 over the (hi, lo) pair of M1): the
+        // entries of Z and M1 reach kappa(Z) times those of W, and a float sum
+        // would leave k kappa(Z) rounding units in W instead of one
+        T acc;
+        if constexpr (sizeof(T) == 4) {
+            dw a2 = {0.f, 0.f};
+            for (int l = 0; l < k; ++l) {
+                dot2_acc(a2, sZ[q * k + l], M1[l * k + j].hi);
+                dot2_acc(a2, sZ[q * k + l], M1[l * k + j].lo);
+            }
+            acc = a2.hi + a2.lo;
+        } else {
+            acc = 0;
+            for (int l = 0; l < k; ++l) acc = M1[l * k + j].fma_(sZ[q * k + l], acc);
+        }
+        W[(size_t)row0 * k + idx] = acc;
+        sW[idx] = acc;
     }
     __syncthreads();
     if (s.Wsp) {
@@ -1700,6 +1910,11 @@ size_t orth2_smem(int prec) {      // M2, rows of W, V, entries (float: also the
     return MEG_KMAX * MEG_KMAX * tsz + ROWS_MAX * MEG_KMAX * tsz + 8 + ROWS_MAX * MEG_RMAX * 8 + RED_MAX_ENTRIES * sizeof(dw) + 16 +
            (prec == MEG_FP64 ? ROWS_MAX * MEG_KMAX * tsz : 0);
 }
+size_t orth_smem(int prec) {       // M1, Qv, rows of W, rows of V, entries (first the rows of Z)
+    size_t tsz = prec == MEG_FP64 ? 8 : 4;
+    return 8 * MEG_KMAX * MEG_KMAX + 8 * MEG_KMAX * MEG_RMAX + ROWS_MAX * MEG_KMAX * tsz + 8 +
+           ROWS_MAX * MEG_RMAX * 8 + 16 + std::max<size_t>(RED_MAX_ENTRIES * sizeof(dw), ROWS_MAX * MEG_KMAX * tsz);
+}
 size_t island_smem() {
     return 4 * 32 * MEG_LDK * sizeof(float) + RED_MAX_ENTRIES * sizeof(dw) + (6 * 32 * MEG_LDK + 32 + 96 + 32) * sizeof(double);
 }
@@ -1723,6 +1938,7 @@ cudaError_t init_kernel_attributes() {
     if ((e = set_smem(k_orth1<float>, orth1_smem(MEG_FP32))) != cudaSuccess) return e;
     if ((e = set_smem(k_orth2<double>, orth2_smem(MEG_FP64))) != cudaSuccess) return e;
     if ((e = set_smem(k_orth2<float>, orth2_smem(MEG_FP32))) != cudaSuccess) return e;
+    if ((e = set_smem(k_orth<float>, orth_smem(MEG_FP32))) != cudaSuccess) return e;
     if ((e = set_smem(k_island_c<double>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_c<float>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_o1<double>, island_smem())) != cudaSuccess) return e;
@@ -1797,10 +2013,25 @@ cudaError_t launch_orth2(const GroupLaunch& g, int phase) {
     return launch_row_island<float>(k_orth2<float>, k_island_o2<float>, g, orth2_smem(g.prec), phase);
 }
 
+// the subspace block after combine's factor: float64 storage runs both
+// CholeskyQR passes (orth1, its factor, orth2); the float-storage modes run
+// the single pass k_orth (their factor is computed in float64 from a
+// double-word Gram); both end with the reduction of U and G
+cudaError_t launch_orthonormalise(const GroupLaunch& g, int phase) {
+    cudaError_t e;
+    if (g.prec == MEG_FP64) {
+        if ((e = launch_orth1(g, phase)) != cudaSuccess) return e;
+        return launch_orth2(g, phase);
+    }
+    return launch_row_island<float>(k_orth<float>, k_island_o2<float>, g, orth_smem(g.prec), phase);
+}
+
 // one kernel of the chain after a product, for timing: 0 combine, 1 its island,
 // 2 orth1, 3 its island, 4 orth2, 5 its island
 cudaError_t launch_chain_kernel(const GroupLaunch& g, int which, int phase) {
     const bool f64 = g.prec == MEG_FP64;
+    if (!f64 && (which == 3 || which == 4)) return cudaErrorNotSupported;   // single pass
+    if (!f64 && which == 2) return launch_clustered<float>(k_orth<float>, g, orth_smem(g.prec), phase);
     switch (which) {
     case 0:
         return f64 ? launch_clustered<double>(k_combine<double>, g, combine_smem(g.prec), phase)

@@ -204,16 +204,14 @@ meg_status enqueue_iteration(const GroupLaunch& g, bool has_dense, bool has_csr,
         if (has_csr) CU(launch_csr(g));
         if (has_meas) CU(launch_meas_apply(g));
         CU(launch_combine(g, phase));
-        CU(launch_orth1(g, phase));
-        CU(launch_orth2(g, phase));
+        CU(launch_orthonormalise(g, phase));
     }
     return MEG_OK;
 }
 
 meg_status enqueue_init_orth(const GroupLaunch& g) {
     CU(launch_combine(g, PH_INIT));
-    CU(launch_orth1(g, PH_INIT));
-    CU(launch_orth2(g, PH_INIT));
+    CU(launch_orthonormalise(g, PH_INIT));
     return MEG_OK;
 }
 
@@ -596,8 +594,7 @@ meg_status meg_warm_start(meg_handle h, int products) {
         if (dw.kind == MEG_CSR_QUAD) CU(launch_csr(g));
         if (dw.kind == MEG_MEAS_STOCH) CU(launch_meas_apply(g));
         CU(launch_combine(g, phase));
-        CU(launch_orth1(g, phase));
-        CU(launch_orth2(g, phase));
+        CU(launch_orthonormalise(g, phase));
     }
     if ((st = upload_desc(h, h->desc)) != MEG_OK) return st;
     CU(cudaStreamSynchronize(h->stream));
@@ -1050,6 +1047,8 @@ meg_status meg_group_time_chain(meg_group g, int reps, float* us) {
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     for (int w = 0; w < 6 && e == cudaSuccess; ++w) {
+        us[w] = 0.f;
+        if (g->gl.prec != MEG_FP64 && (w == 3 || w == 4)) continue;   // single CholeskyQR pass
         for (int i = 0; i <= reps && e == cudaSuccess; ++i) {      // one untimed launch first
             if (i == 1) e = cudaEventRecord(e0, g->stream);
             if (e == cudaSuccess) e = launch_chain_kernel(g->gl, w, PH_ADVANCE);
@@ -1074,11 +1073,12 @@ int meg_group_kernels_per_step(meg_group g) {
     if (!g) return -1;
     // per product: the gradient-part kernels (one tensor-core launch per chunk of
     // tensor-core solves, one FFMA launch for the other dense solves), CSR,
-    // the two minibatch passes, and combine / orth1 / orth2, each a row kernel
-    // followed by an island kernel; plus the begin kernel once per iteration
+    // the two minibatch passes, and combine plus the orthonormalisation, each a
+    // row kernel followed by an island kernel (float64 storage: combine, orth1,
+    // orth2; float storage: combine, orth); plus the begin kernel once per iteration
     const int dense = g->gl.tc_chunks + (g->gl.blocks[PK_DENSE] > 0 ? 1 : 0);
     const int csr = g->has_csr ? (g->gl.prec == MEG_FP64 ? 1 : 2) : 0;   // float modes: V cast + product
-    const int per = dense + csr + (g->has_meas ? 2 : 0) + 6;
+    const int per = dense + csr + (g->has_meas ? 2 : 0) + (g->gl.prec == MEG_FP64 ? 6 : 4);
     return g->q * per + 1;
 }
 
