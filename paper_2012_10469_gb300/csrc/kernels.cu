@@ -1118,17 +1118,20 @@ __global__ void __launch_bounds__(NT) k_orth(const SolveDev* sds, int ns, int ph
     __syncthreads();      // the previous W rows are read
     for (int idx = tid; idx < nr * k; idx += NT) {
         const int q = idx / k, j = idx % k;
-        // W = Z M1 with exact products (Dot2 over the (hi, lo) pair of M1): the
+        // W = Z M1 with exact products (Dot2) over the high part of M1: the
         // entries of Z and M1 reach kappa(Z) times those of W, and a float sum
-        // would leave k kappa(Z) rounding units in W instead of one
+        // would leave k kappa(Z) rounding units in W instead of one; the low
+        // part (a float rounding unit of M1) adds in plain float arithmetic
         T acc;
         if constexpr (sizeof(T) == 4) {
             dw a2 = {0.f, 0.f};
+            float lo = 0.f;
             for (int l = 0; l < k; ++l) {
-                dot2_acc(a2, sZ[q * k + l], M1[l * k + j].hi);
-                dot2_acc(a2, sZ[q * k + l], M1[l * k + j].lo);
+                const float z = sZ[q * k + l];
+                dot2_acc(a2, z, M1[l * k + j].hi);
+                lo = fmaf(z, M1[l * k + j].lo, lo);
             }
-            acc = a2.hi + a2.lo;
+            acc = a2.hi + (a2.lo + lo);
         } else {
             acc = 0;
             for (int l = 0; l < k; ++l) acc = M1[l * k + j].fma_(sZ[q * k + l], acc);
@@ -1173,13 +1176,21 @@ __global__ void __launch_bounds__(NT) k_orth(const SolveDev* sds, int ns, int ph
             if (q < nr) a.add_prod(sW[q * k + i], sW[q * k + j]);
         } else {
             int l = (e - nsym) / k, j = (e - nsym) % k;
-            for (int q = 0; q < nr; ++q) {
-                if constexpr (sizeof(T) == 8) {
-                    a.add_prod(sV[q * r + l], sW[q * k + j]);
-                } else {      // V is float64: two floats per entry, both products exact in Dot2
-                    a.add_prod(sVh[q * r + l], sW[q * k + j]);
-                    b.add_prod(sVl[q * r + l], sW[q * k + j]);
+            if constexpr (sizeof(T) == 8) {
+                for (int q = 0; q < nr; ++q) a.add_prod(sV[q * r + l], sW[q * k + j]);
+            } else {
+                // V is float64, held as (hi, lo) floats: the high part in Dot2, the
+                // low part (a float rounding unit of V) in plain float arithmetic
+                float lo = 0.f;
+                for (int q = 0; q < nr; ++q) {
+                    const float w = sW[q * k + j];
+                    a.add_prod(sVh[q * r + l], w);
+                    lo = fmaf(sVl[q * r + l], w, lo);
                 }
+                dw r0 = a.as_dw();
+                dw_add(r0, dw{lo, 0.f});
+                ent[e] = r0;
+                continue;
             }
         }
         dw r0 = a.as_dw();
