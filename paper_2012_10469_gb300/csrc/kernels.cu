@@ -1946,14 +1946,11 @@ cudaError_t init_kernel_attributes() {
     if ((e = set_smem(k_combine<double>, combine_smem(MEG_FP64))) != cudaSuccess) return e;
     if ((e = set_smem(k_combine<float>, combine_smem(MEG_FP32))) != cudaSuccess) return e;
     if ((e = set_smem(k_orth1<double>, orth1_smem(MEG_FP64))) != cudaSuccess) return e;
-    if ((e = set_smem(k_orth1<float>, orth1_smem(MEG_FP32))) != cudaSuccess) return e;
     if ((e = set_smem(k_orth2<double>, orth2_smem(MEG_FP64))) != cudaSuccess) return e;
-    if ((e = set_smem(k_orth2<float>, orth2_smem(MEG_FP32))) != cudaSuccess) return e;
     if ((e = set_smem(k_orth<float>, orth_smem(MEG_FP32))) != cudaSuccess) return e;
     if ((e = set_smem(k_island_c<double>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_c<float>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_o1<double>, island_smem())) != cudaSuccess) return e;
-    if ((e = set_smem(k_island_o1<float>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_o2<double>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_o2<float>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_objective<float>, OBJ_SMEM_MAX)) != cudaSuccess) return e;
@@ -2012,53 +2009,45 @@ cudaError_t launch_combine(const GroupLaunch& g, int phase) {
     return launch_row_island<float>(k_combine<float>, k_island_c<float>, g, combine_smem(g.prec), phase);
 }
 
-cudaError_t launch_orth1(const GroupLaunch& g, int phase) {
-    if (g.prec == MEG_FP64)
-        return launch_row_island<double>(k_orth1<double>, k_island_o1<double>, g, orth1_smem(g.prec), phase);
-    return launch_row_island<float>(k_orth1<float>, k_island_o1<float>, g, orth1_smem(g.prec), phase);
-}
-
-cudaError_t launch_orth2(const GroupLaunch& g, int phase) {
-    if (g.prec == MEG_FP64)
-        return launch_row_island<double>(k_orth2<double>, k_island_o2<double>, g, orth2_smem(g.prec), phase);
-    return launch_row_island<float>(k_orth2<float>, k_island_o2<float>, g, orth2_smem(g.prec), phase);
-}
-
 // the subspace block after combine's factor: float64 storage runs both
-// CholeskyQR passes (orth1, its factor, orth2); the float-storage modes run
-// the single pass k_orth (their factor is computed in float64 from a
-// double-word Gram); both end with the reduction of U and G
+// CholeskyQR passes (orth1, its factor, orth2: the two-pass kernels exist
+// for float64 only); the float-storage modes run the single pass k_orth
+// (their factor refined in Gram space by combine's factor kernel); both end
+// with the reduction of U and G
 cudaError_t launch_orthonormalise(const GroupLaunch& g, int phase) {
-    cudaError_t e;
     if (g.prec == MEG_FP64) {
-        if ((e = launch_orth1(g, phase)) != cudaSuccess) return e;
-        return launch_orth2(g, phase);
+        cudaError_t e =
+            launch_row_island<double>(k_orth1<double>, k_island_o1<double>, g, orth1_smem(MEG_FP64), phase);
+        if (e != cudaSuccess) return e;
+        return launch_row_island<double>(k_orth2<double>, k_island_o2<double>, g, orth2_smem(MEG_FP64), phase);
     }
     return launch_row_island<float>(k_orth<float>, k_island_o2<float>, g, orth_smem(g.prec), phase);
 }
 
 // one kernel of the chain after a product, for timing: 0 combine, 1 its island,
-// 2 orth1, 3 its island, 4 orth2, 5 its island
+// 2 orth1 (float storage: k_orth), 3 its island, 4 orth2 (float64 storage
+// only), 5 the reduction of U and G
 cudaError_t launch_chain_kernel(const GroupLaunch& g, int which, int phase) {
-    const bool f64 = g.prec == MEG_FP64;
-    if (!f64 && (which == 3 || which == 4)) return cudaErrorNotSupported;   // single pass
-    if (!f64 && which == 2) return launch_clustered<float>(k_orth<float>, g, orth_smem(g.prec), phase);
-    switch (which) {
-    case 0:
-        return f64 ? launch_clustered<double>(k_combine<double>, g, combine_smem(g.prec), phase)
-                   : launch_clustered<float>(k_combine<float>, g, combine_smem(g.prec), phase);
-    case 2:
-        return f64 ? launch_clustered<double>(k_orth1<double>, g, orth1_smem(g.prec), phase)
-                   : launch_clustered<float>(k_orth1<float>, g, orth1_smem(g.prec), phase);
-    case 4:
-        return f64 ? launch_clustered<double>(k_orth2<double>, g, orth2_smem(g.prec), phase)
-                   : launch_clustered<float>(k_orth2<float>, g, orth2_smem(g.prec), phase);
-    default: break;
+    void (*isl)(const SolveDev*, int, int) = nullptr;
+    if (g.prec == MEG_FP64) {
+        switch (which) {
+        case 0: return launch_clustered<double>(k_combine<double>, g, combine_smem(MEG_FP64), phase);
+        case 2: return launch_clustered<double>(k_orth1<double>, g, orth1_smem(MEG_FP64), phase);
+        case 4: return launch_clustered<double>(k_orth2<double>, g, orth2_smem(MEG_FP64), phase);
+        case 1: isl = k_island_c<double>; break;
+        case 3: isl = k_island_o1<double>; break;
+        default: isl = k_island_o2<double>; break;
+        }
+    } else {
+        switch (which) {
+        case 0: return launch_clustered<float>(k_combine<float>, g, combine_smem(g.prec), phase);
+        case 2: return launch_clustered<float>(k_orth<float>, g, orth_smem(g.prec), phase);
+        case 3:
+        case 4: return cudaErrorNotSupported;                  // single pass
+        case 1: isl = k_island_c<float>; break;
+        default: isl = k_island_o2<float>; break;
+        }
     }
-    void (*isl)(const SolveDev*, int, int) =
-        which == 1 ? (f64 ? k_island_c<double> : k_island_c<float>)
-                   : which == 3 ? (f64 ? k_island_o1<double> : k_island_o1<float>)
-                                : (f64 ? k_island_o2<double> : k_island_o2<float>);
     return launch_k(isl, dim3(g.ns), dim3(NT), island_smem(), g.stream, 1, g.d_solves, g.ns, phase);
 }
 

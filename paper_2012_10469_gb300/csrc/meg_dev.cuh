@@ -311,8 +311,6 @@ cudaError_t launch_csr(const GroupLaunch& g);
 cudaError_t launch_meas_batch(const GroupLaunch& g);
 cudaError_t launch_meas_apply(const GroupLaunch& g);
 cudaError_t launch_combine(const GroupLaunch& g, int phase);
-cudaError_t launch_orth1(const GroupLaunch& g, int phase);
-cudaError_t launch_orth2(const GroupLaunch& g, int phase);
 cudaError_t launch_orthonormalise(const GroupLaunch& g, int phase);
 cudaError_t launch_chain_kernel(const GroupLaunch& g, int which, int phase);
 cudaError_t launch_objective(const GroupLaunch& g, double* out_f);

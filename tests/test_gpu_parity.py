@@ -210,6 +210,43 @@ def test_group_equals_alone():
     g.meg_group_destroy()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16"])
+def test_group_time_chain_leaves_iterates(prec):
+    """meg_group_time_chain runs the chain kernels many times on the group's
+    current block; W, its split and the small state are restored, so a group
+    timed mid-run reaches bitwise the iterate of an untimed twin."""
+    import torch
+    from paper_2012_10469_gb300 import binding as B
+    precision = B.PRECISION[prec]
+    storage = {"fp64": "f64", "bf16": "bf16"}[prec]
+    probs = [synth.dense_quadratic(n, r, seed=70 + n, sigma=1e-4, storage=storage) for n, r in ((256, 3), (384, 5))]
+    rs = (3, 5)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def group():
+        ss = [make_gpu_solve("dense_quadratic", p, r, 4, 3, precision, 1.0, 13, V0=p.U, lam0=p.w)
+              for p, r in zip(probs, rs)]
+        return ss, B.Group(ss, stream=stream)
+
+    timed, gt = group()
+    plain, gp = group()
+    try:
+        gt.meg_group_step(3)
+        us = gt.meg_group_time_chain(5)
+        assert len(us) == 6 and all(v > 0 for v in (us[0], us[1], us[2], us[5]))
+        assert (us[3] > 0 and us[4] > 0) if prec == "fp64" else (us[3] == 0 and us[4] == 0)
+        gt.meg_group_step(3)
+        gp.meg_group_step(6)
+        for a, b in zip(timed, plain):
+            Xa, Xb = gpu_factored(a), gpu_factored(b)
+            assert np.array_equal(Xa.V, Xb.V) and np.array_equal(Xa.mu, Xb.mu) and Xa.s == Xb.s
+    finally:
+        gt.meg_group_destroy()
+        gp.meg_group_destroy()
+        for x in timed + plain:
+            x.meg_destroy()
+
+
 def test_invalid_arguments_rejected():
     from paper_2012_10469_gb300 import binding as B
     with pytest.raises(B.MegError) as e:
