@@ -27,8 +27,10 @@ Optimization"):
 * ``warm_start`` -- eq. (exp:init) with U = 0: the top-r eigenpairs of
   -grad f(0), eigenvalues projected onto the unit simplex.
 * objectives: dense quadratic 1/2||X - M||_F^2, linear <C, X>, matrix
-  completion on a mirrored sample Omega, and stochastic quadratic
-  measurements with minibatches drawn by SplitMix64.
+  completion on a mirrored sample Omega, stochastic quadratic
+  measurements with minibatches drawn by SplitMix64, and the experiments'
+  bilinear measurements 1/2 sum (a^T X b - y)^2 on the tau-spectrahedron
+  (Section 7), with ``warm_start_at`` for their initialization.
 
 Readings of points the paper leaves open are listed with the code that
 takes them (eps schedule, shift of the subspace iteration, minibatch
@@ -338,6 +340,84 @@ class Measurements:
     def neg_grad0_apply(self, W):
         # -grad f(0) = (2/m) sum_i y_i a_i a_i^T  (full data)
         return (2.0 / self.m) * (self.A.T @ (self.y[:, None] * (self.A @ W)))
+
+
+class BilinearMeasurements:
+    """The paper's experiment objective (Section 7, eq. recoveryProb) in
+    trace-1 variables: f(X) = 1/2 sum_i (a_i^T X b_i - y_i)^2 over the
+    tau-spectrahedron, written for X' = X / tau on the unit spectrahedron,
+    f'(X') = f(tau X') = 1/2 sum_i (tau a_i^T X' b_i - y_i)^2 (the library is
+    trace-1 only).  For symmetric X, a^T X b = <X, (a b^T + b a^T)/2>, so
+    grad f'(X') = tau sum_i r_i (a_i b_i^T + b_i a_i^T)/2 with
+    r_i = tau a_i^T X' b_i - y_i (full gradients: the experiments' setting).
+    """
+    kind = "bilinear"
+
+    def __init__(self, A: np.ndarray, B: np.ndarray, y: np.ndarray, tau: float = 1.0):
+        self.A = np.asarray(A, dtype=np.float64)
+        self.B = np.asarray(B, dtype=np.float64)
+        self.y = np.asarray(y, dtype=np.float64)
+        self.m, self.n = self.A.shape
+        self.tau = float(tau)
+
+    def bil(self, X) -> np.ndarray:
+        """tau a_i^T X b_i for every i; Factored X: sum_l (mu_l - s)(a_i.v_l)(b_i.v_l) + s a_i.b_i."""
+        if isinstance(X, Factored):
+            pa, pb = self.A @ X.V, self.B @ X.V
+            q = (pa * pb) @ (X.mu - X.s) + X.s * np.einsum("ij,ij->i", self.A, self.B)
+        else:
+            q = np.einsum("ij,jk,ik->i", self.A, np.asarray(X), self.B)
+        return self.tau * q
+
+    def residual(self, X) -> np.ndarray:
+        return self.bil(X) - self.y
+
+    def value(self, X: Factored) -> float:
+        r = self.residual(X)
+        return 0.5 * float(r @ r)
+
+    def value_dense(self, X: np.ndarray) -> float:
+        r = self.residual(X)
+        return 0.5 * float(r @ r)
+
+    def grad_dense(self, X, t: int = 0) -> np.ndarray:
+        r = self.residual(X)
+        G = (self.A.T * r) @ self.B
+        return 0.5 * self.tau * (G + G.T)
+
+    def grad_apply(self, X: Factored, W: np.ndarray, t: int = 0) -> np.ndarray:
+        r = self.residual(X)[:, None]
+        return 0.5 * self.tau * (self.A.T @ (r * (self.B @ W)) + self.B.T @ (r * (self.A @ W)))
+
+    def grad_norm_bound(self, X: Factored, t: int = 0) -> float:
+        # ||(a b^T + b a^T)/2||_2 <= ||a|| ||b||
+        r = self.residual(X)
+        na, nb = np.linalg.norm(self.A, axis=1), np.linalg.norm(self.B, axis=1)
+        return self.tau * float(np.sum(np.abs(r) * na * nb))
+
+    def neg_grad0_apply(self, W):
+        # -grad f'(0) = tau sum_i y_i (a_i b_i^T + b_i a_i^T)/2
+        y = self.y[:, None]
+        return 0.5 * self.tau * (self.A.T @ (y * (self.B @ W)) + self.B.T @ (y * (self.A @ W)))
+
+
+def warm_start_at(obj, r: int, U: np.ndarray, printed_sign: bool = False):
+    """eq. (exp:init) at a given U (||U||_F = 1), in trace-1 variables:
+    X_0 = V_r diag(Pi_{Delta_tau}(w)) V_r^T with (V_r, Lambda_r) the top-r
+    eigenpairs of -grad f(tau U U^T), and X'_0 = X_0 / tau =
+    V_r diag(Pi_Delta(w / tau)) V_r^T.  With grad f(tau U U^T) =
+    grad f'(U U^T) / tau, Lambda_r / tau are the top eigenvalues of
+    -grad f'(U U^T) / tau^2.  w = Lambda_r is the reading of ``warm_start``;
+    printed_sign=True takes the equation as printed, w = -Lambda_r, which is
+    what reproduces the initialization errors of the paper's Table 1 (rank 5
+    and 20, where the projection of -Lambda_r weights the r-th eigenvector
+    most).  Returns (V0 n x r, lam0 on the unit simplex).
+    """
+    tau = getattr(obj, "tau", 1.0)
+    G = obj.grad_dense(U @ U.T)
+    lam, V = eigh_desc(-0.5 * (G + G.T) / (tau * tau))
+    w = -lam[:r] if printed_sign else lam[:r]
+    return V[:, :r], project_simplex(w)
 
 
 # ---------------------------------------------------------------- certificate

@@ -219,6 +219,54 @@ def measurements(n: int, r: int, m: int, L: int, seed: int,
     return Measurements(n=n, A=A, y=y, L=L, U=U, w=w)
 
 
+@dataclasses.dataclass
+class BilinearRecovery:
+    """Recovery from bilinear measurements (the paper's experiment, Section 7):
+    ground truth M = (sqrt(n) G)(sqrt(n) G)^T with G Gaussian, ||G||_F = 1;
+    m pairs of uniform unit vectors (a_i, b_i); y = y0 + kappa ||y0|| v with
+    y0_i = a_i^T M b_i and v a uniform unit vector; trace bound tau; U the
+    Gaussian, ||U||_F = 1, matrix of the initialization."""
+    n: int
+    r: int
+    A: np.ndarray        # m x n
+    B: np.ndarray        # m x n
+    y: np.ndarray        # m
+    G: np.ndarray        # n x r, M = n G G^T
+    tau: float
+    U: np.ndarray        # n x r
+
+    @property
+    def M(self) -> np.ndarray:
+        return self.n * (self.G @ self.G.T)
+
+
+def _unit_rows(rng: np.random.Generator, m: int, n: int) -> np.ndarray:
+    x = rng.standard_normal((m, n))
+    return x / np.linalg.norm(x, axis=1, keepdims=True)
+
+
+def bilinear_recovery(n: int, r: int, seed: int, kappa: float = 0.5, m: Optional[int] = None,
+                      tau_frac: Optional[float] = None) -> BilinearRecovery:
+    """The instance of Section 7: m = 20 n r measurements, noise level kappa,
+    tau = 0.5 tr(M) for rank 1 and 5 and 0.65 tr(M) for rank 20 (unless given)."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, r))
+    G /= np.linalg.norm(G)
+    m = 20 * n * r if m is None else int(m)
+    A = _unit_rows(rng, m, n)
+    B = _unit_rows(rng, m, n)
+    y0 = n * np.einsum("ij,ij->i", A @ G, B @ G)
+    v = rng.standard_normal(m)
+    v /= np.linalg.norm(v)
+    y = y0 + kappa * np.linalg.norm(y0) * v
+    if tau_frac is None:
+        tau_frac = 0.65 if r >= 20 else 0.5
+    tau = tau_frac * float(n)          # tr(M) = n ||G||_F^2 = n
+    U = rng.standard_normal((n, r))
+    U /= np.linalg.norm(U)
+    return BilinearRecovery(n=n, r=r, A=A, B=B, y=y, G=G, tau=tau, U=U)
+
+
 def arrival_trace(count: int, rate: float, seed: int, n_lo: int = 64, n_hi: int = 1024,
                   r_max: int = 8):
     """Poisson arrivals: (time_s, n, r, kind) with n log-uniform, r uniform."""
