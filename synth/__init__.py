@@ -246,13 +246,16 @@ def _unit_rows(rng: np.random.Generator, m: int, n: int) -> np.ndarray:
 
 
 def bilinear_recovery(n: int, r: int, seed: int, kappa: float = 0.5, m: Optional[int] = None,
-                      tau_frac: Optional[float] = None) -> BilinearRecovery:
-    """The instance of Section 7: m = 20 n r measurements, noise level kappa,
-    tau = 0.5 tr(M) for rank 1 and 5 and 0.65 tr(M) for rank 20 (unless given)."""
+                      tau_frac: Optional[float] = None, r_svd: Optional[int] = None) -> BilinearRecovery:
+    """The instance of Section 7: ground truth of rank r, noise level kappa,
+    tau = 0.5 tr(M) for rank 1 and 5 and 0.65 tr(M) for rank 20 (unless
+    given), m = 20 n r_svd measurements and U with r_svd columns, r_svd the
+    algorithm's rank parameter (r unless the rank is overestimated)."""
     rng = np.random.default_rng(seed)
     G = rng.standard_normal((n, r))
     G /= np.linalg.norm(G)
-    m = 20 * n * r if m is None else int(m)
+    r_svd = r if r_svd is None else int(r_svd)
+    m = 20 * n * r_svd if m is None else int(m)
     A = _unit_rows(rng, m, n)
     B = _unit_rows(rng, m, n)
     y0 = n * np.einsum("ij,ij->i", A @ G, B @ G)
@@ -262,7 +265,7 @@ def bilinear_recovery(n: int, r: int, seed: int, kappa: float = 0.5, m: Optional
     if tau_frac is None:
         tau_frac = 0.65 if r >= 20 else 0.5
     tau = tau_frac * float(n)          # tr(M) = n ||G||_F^2 = n
-    U = rng.standard_normal((n, r))
+    U = rng.standard_normal((n, r_svd))
     U /= np.linalg.norm(U)
     return BilinearRecovery(n=n, r=r, A=A, B=B, y=y, G=G, tau=tau, U=U)
 
