@@ -567,7 +567,8 @@ def run_gpu(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"dense quadratic n={N} r={R} k={R + P} q={Q}, {BATCH} independent "
                                    f"instances per step (grouped kernels, CUDA graph), bf16 data, "
-                                   f"float32 subspace, float32 k x k island with double-word refinement, "
+                                   f"float32 subspace (one CholeskyQR pass per product, factor refined in Gram space), "
+                                   f"float32 k x k island with double-word refinement, "
                                    f"X_0 = planted point",
                        "autotune": tuned,
                        "global_batch": ws * BATCH, "l2": "inputs larger than L2 (268 MB bf16 per rank)",
