@@ -12,8 +12,9 @@
  * (Definition 2, eq. LowRankMDvonNeumannUpdate).  X_t is held in the
  * factored form of eq. (eigenFastUpdate): V (n x r, orthonormal), mu (r)
  * and s, X = V diag(mu) V^T + s (I - V V^T).  The eigenpairs come from a
- * warm-started block subspace iteration with CholeskyQR2 and a
- * Rayleigh-Ritz step (Section 3).
+ * warm-started block subspace iteration (CholeskyQR: two passes in float64
+ * storage, one pass with a factor refined in Gram space in the float
+ * storage modes) and a Rayleigh-Ritz step (Section 3).
  *
  * Conventions for every call:
  *   - Matrices are row-major.  "host" pointers are ordinary CPU memory,
@@ -226,7 +227,7 @@ meg_status meg_group_time_product(meg_group g, int reps, float* ms_per_launch);
 
 /* meg_group_time_chain -- profiling aid: the warm duration, in microseconds,
  * of each kernel of the chain that follows an intermediate product of the
- * subspace iteration (Section 3: the mirror operator, then CholeskyQR2):
+ * subspace iteration (Section 3: the mirror operator, then CholeskyQR):
  * us[0] the row kernel forming Z = (M_t - c I) W and the partials of Z^T Z,
  * us[1] its per-solve kernel (the CholeskyQR factor).  Float64 storage
  * (two CholeskyQR passes): us[2] W' = Z M1 with the partials of W'^T W',
