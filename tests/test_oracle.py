@@ -517,3 +517,24 @@ def test_table2_table3_certificate_onset():
     for row in gold["table3"]:
         got = np.array([_first_holds(row["n"], row["rank"], row["r_svd"], s) for s in range(4)], dtype=float)
         assert abs(got[:, 0].mean() - row["first_exact"]) <= 1.0, (row, got)
+
+
+def test_bilinear_instance_matches_section7():
+    """The generated instance has the properties Section 7 states: unit
+    measurement vectors, tr(M) = n (M = (sqrt(n) G)(sqrt(n) G)^T, ||G||_F = 1),
+    rank(M) = r, y0_i = a_i^T M b_i, and signal-to-noise ratio
+    ||y0||^2 / ||y - y0||^2 = 1 / kappa^2 (4 for kappa = 1/2); tau = 0.5 tr(M)
+    for ranks 1 and 5, 0.65 tr(M) for rank 20; m = 20 n r."""
+    for r in (1, 5, 20):
+        p = synth.bilinear_recovery(40, r, seed=11 + r)
+        assert p.A.shape == (20 * 40 * r, 40) and p.B.shape == p.A.shape
+        assert np.allclose(np.linalg.norm(p.A, axis=1), 1.0, atol=1e-14)
+        assert np.allclose(np.linalg.norm(p.B, axis=1), 1.0, atol=1e-14)
+        M = p.M
+        assert abs(np.trace(M) - 40.0) <= 1e-12 * 40
+        assert np.linalg.matrix_rank(M) == r
+        y0 = np.array([p.A[i] @ M @ p.B[i] for i in range(p.A.shape[0])])
+        noise = p.y - y0
+        assert abs(float(y0 @ y0) / float(noise @ noise) - 4.0) <= 1e-10
+        assert abs(p.tau - (0.65 if r == 20 else 0.5) * np.trace(M)) <= 1e-12
+        assert abs(np.linalg.norm(p.U) - 1.0) <= 1e-14
