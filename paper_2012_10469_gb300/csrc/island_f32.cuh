@@ -208,8 +208,10 @@ __device__ __forceinline__ void dw_split(double v, float& hi, float& lo) {
 // split of S, then of T = S M1), M2 = L_B^{-T} from the float32 Cholesky of
 // the well-conditioned B, and M = M1 M2 (exact products, returned in
 // float64 to be applied as a (hi, lo) pair) gives M^T S M = M2^T B M2 = I to
-// float accuracy.  F0..F3: four float k x k work matrices; T: a float64 one;
-// M may alias none of them.  Returns false on a non-positive pivot.
+// float accuracy.  F0..F3: four float k x k work matrices; T: a float64 one
+// (it holds T = S M1 as a normalised (hi, lo) float pair, so that no float64
+// arithmetic runs in the k^3 loops); M may alias none of them.  Returns false
+// on a non-positive pivot.
 __device__ inline bool gram_factor_f32(const double* S, float* F0, float* F1, float* F2, float* F3, double* T,
                                        double* M, float* dsc, int k, int* flag) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -222,6 +224,8 @@ __device__ inline bool gram_factor_f32(const double* S, float* F0, float* F1, fl
     }
     __syncthreads();
     bool ok = chol_inv<float>(F0, F2, dsc, k, flag);             // M1 in F2
+    float* Th = (float*)T;                                      // T = S M1 as (hi, lo) floats
+    float* Tl = Th + 32 * MEG_LDK;
     for (int e = tid; e < k * k; e += nt) {                     // T = S M1 (exact products)
         const int i = e / k, j = e - i * k;
         dw acc = {0.f, 0.f};
@@ -230,18 +234,21 @@ __device__ inline bool gram_factor_f32(const double* S, float* F0, float* F1, fl
             dot2_acc(acc, F0[i * MEG_LDK + a], m);
             dot2_acc(acc, F1[i * MEG_LDK + a], m);
         }
-        T[i * MEG_LDK + j] = dw_value(acc);
+        // normalise: hi = fl(acc.hi + acc.lo), lo its exact error -- the pair
+        // that rounding the float64 value hi + lo to float and back gives
+        float hi, lo;
+        two_sum(acc.hi, acc.lo, hi, lo);
+        Th[i * MEG_LDK + j] = hi;
+        Tl[i * MEG_LDK + j] = lo;
     }
     __syncthreads();
     for (int e = tid; e < k * k; e += nt) {                     // B = M1^T T (exact products)
         const int i = e / k, j = e - i * k;
         dw acc = {0.f, 0.f};
         for (int a = 0; a < k; ++a) {
-            float hi, lo;
-            dw_split(T[a * MEG_LDK + j], hi, lo);
             const float m = F2[a * MEG_LDK + i];
-            dot2_acc(acc, m, hi);
-            dot2_acc(acc, m, lo);
+            dot2_acc(acc, m, Th[a * MEG_LDK + j]);
+            dot2_acc(acc, m, Tl[a * MEG_LDK + j]);
         }
         F3[i * MEG_LDK + j] = (float)dw_value(acc);
     }
