@@ -261,8 +261,10 @@ __global__ void k_begin(const SolveDev* sds, int ns) {
 
 // ---------------------------------------------------------------------------
 // Rayleigh-Ritz for float storage (float64 results from float32 work).
-//   Ht = G^{-1/2} H G^{-1/2},  E = G - I (|E| < 1e-3: W is orthonormal to about
-//        kappa(Z) float32 units after its CholeskyQR pass), to second order:
+//   Ht = G^{-1/2} H G^{-1/2},  E = G - I (|E| < 1e-3: W is orthonormal to a few
+//        float32 units after its CholeskyQR pass, at most about kappa(Z) of
+//        them; with q > 1 the final product's plain float factor leaves up to
+//        kappa(Z)^2 units for the next iteration's first product), to second order:
 //        G^{-1/2} = I - E/2 + 3 E^2/8 + O(E^3), so
 //        Ht = H - (E H + H E)/2 + 3 (E^2 H + H E^2)/8 + E H E/4 + O(E^3 |H|)
 //        (the second-order terms in float32: they are below 1e-6 |H|)
@@ -681,9 +683,10 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
         // W' = Z L^{-T}, L = chol(Z^T Z)
         if constexpr (sizeof(T) == 4) {
             // the only CholeskyQR pass of the float-storage modes: a factor of the
-            // double-word Gram refined in Gram space, so that W = Z M1 is
-            // orthonormal to about kappa(Z) float rounding units (a plain float
-            // factor would leave kappa(Z)^2 of them and need a second pass)
+            // double-word Gram refined in Gram space, so that W = Z M1 (exact
+            // products, one rounding) is orthonormal to a few float rounding units
+            // (a plain float factor would leave about kappa(Z)^2 of them and need
+            // a second pass over the rows)
             float* F = (float*)smraw;                  // the reduction's scratch, free again
             constexpr int FM = 32 * MEG_LDK;
             if (!gram_factor_f32(S1, F, F + FM, F + 2 * FM, F + 3 * FM, A, C, (float*)pr, k, &flag) && tid == 0)
@@ -723,8 +726,8 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
     __shared__ double mun[MEG_KMAX];
     __shared__ int use_fast;
     if constexpr (sizeof(T) == 4) {
-        // E = G - I; after the CholeskyQR pass ||E|| is about kappa(Z) float32
-        // rounding units, so second-order terms in E are negligible here
+        // E = G - I; after the CholeskyQR pass ||E|| is a few float32 rounding
+        // units, so the second-order treatment below is exact to O(E^3)
         if (tid < 32) {
             float em = 0.f;
             for (int e = tid; e < k * k; e += 32)
