@@ -401,6 +401,70 @@ class BilinearMeasurements:
         return 0.5 * self.tau * (self.A.T @ (y * (self.B @ W)) + self.B.T @ (y * (self.A @ W)))
 
 
+class RankPMeasurements:
+    """The experiments' objective with measurement matrices of rank p > 1
+    (Section 7, higher-rank measurements): f(X) = 1/2 sum_i (Tr(A_i^T X B_i)
+    - y_i)^2 with A_i, B_i in R^{n x p}, in trace-1 variables X' = X / tau as
+    for ``BilinearMeasurements``.  For symmetric X, Tr(A^T X B) =
+    <X, (A B^T + B A^T)/2>, so grad f'(X') = tau sum_i r_i (A_i B_i^T +
+    B_i A_i^T)/2 with r_i = tau Tr(A_i^T X' B_i) - y_i.  As, Bs: m x n x p.
+    """
+    kind = "rank_p"
+
+    def __init__(self, As: np.ndarray, Bs: np.ndarray, y: np.ndarray, tau: float = 1.0):
+        self.As = np.asarray(As, dtype=np.float64)
+        self.Bs = np.asarray(Bs, dtype=np.float64)
+        self.y = np.asarray(y, dtype=np.float64)
+        self.m, self.n, self.p = self.As.shape
+        self.tau = float(tau)
+
+    def trace_form(self, X) -> np.ndarray:
+        """tau Tr(A_i^T X B_i) for every i; Factored X: sum_l (mu_l - s) <A_i^T v_l, B_i^T v_l>
+        + s <A_i, B_i>."""
+        if isinstance(X, Factored):
+            pa = np.einsum("inp,nl->ipl", self.As, X.V)
+            pb = np.einsum("inp,nl->ipl", self.Bs, X.V)
+            q = np.einsum("ipl,ipl->il", pa, pb) @ (X.mu - X.s) + X.s * np.einsum("inp,inp->i", self.As, self.Bs)
+        else:
+            q = np.einsum("inp,nk,ikp->i", self.As, np.asarray(X), self.Bs, optimize=True)
+        return self.tau * q
+
+    def residual(self, X) -> np.ndarray:
+        return self.trace_form(X) - self.y
+
+    def value(self, X: Factored) -> float:
+        r = self.residual(X)
+        return 0.5 * float(r @ r)
+
+    def value_dense(self, X: np.ndarray) -> float:
+        r = self.residual(X)
+        return 0.5 * float(r @ r)
+
+    def grad_dense(self, X, t: int = 0) -> np.ndarray:
+        r = self.residual(X)
+        G = np.einsum("i,inp,ikp->nk", r, self.As, self.Bs, optimize=True)
+        return 0.5 * self.tau * (G + G.T)
+
+    def grad_apply(self, X: Factored, W: np.ndarray, t: int = 0) -> np.ndarray:
+        r = self.residual(X)
+        bw = np.einsum("ikp,kj->ipj", self.Bs, W)
+        aw = np.einsum("ikp,kj->ipj", self.As, W)
+        return 0.5 * self.tau * (np.einsum("i,inp,ipj->nj", r, self.As, bw) + np.einsum("i,inp,ipj->nj", r, self.Bs, aw))
+
+    def grad_norm_bound(self, X: Factored, t: int = 0) -> float:
+        # ||(A B^T + B A^T)/2||_2 <= ||A||_2 ||B||_2
+        r = self.residual(X)
+        na = np.array([np.linalg.norm(a, 2) for a in self.As])
+        nb = np.array([np.linalg.norm(b, 2) for b in self.Bs])
+        return self.tau * float(np.sum(np.abs(r) * na * nb))
+
+    def neg_grad0_apply(self, W):
+        y = self.y
+        bw = np.einsum("ikp,kj->ipj", self.Bs, W)
+        aw = np.einsum("ikp,kj->ipj", self.As, W)
+        return 0.5 * self.tau * (np.einsum("i,inp,ipj->nj", y, self.As, bw) + np.einsum("i,inp,ipj->nj", y, self.Bs, aw))
+
+
 def warm_start_at(obj, r: int, U: np.ndarray, printed_sign: bool = False):
     """eq. (exp:init) at a given U (||U||_F = 1), in trace-1 variables:
     X_0 = V_r diag(Pi_{Delta_tau}(w)) V_r^T with (V_r, Lambda_r) the top-r

@@ -270,6 +270,49 @@ def bilinear_recovery(n: int, r: int, seed: int, kappa: float = 0.5, m: Optional
     return BilinearRecovery(n=n, r=r, A=A, B=B, y=y, G=G, tau=tau, U=U)
 
 
+@dataclasses.dataclass
+class RankPRecovery:
+    """The higher-rank-measurement instance of Section 7: as
+    ``BilinearRecovery`` with A_i, B_i in R^{n x p} with orthonormal columns
+    and y0_i = Tr(A_i^T M B_i)."""
+    n: int
+    r: int
+    p: int
+    As: np.ndarray       # m x n x p
+    Bs: np.ndarray       # m x n x p
+    y: np.ndarray
+    G: np.ndarray
+    tau: float
+    U: np.ndarray
+
+    @property
+    def M(self) -> np.ndarray:
+        return self.n * (self.G @ self.G.T)
+
+
+def _orthonormal_blocks(rng: np.random.Generator, m: int, n: int, p: int) -> np.ndarray:
+    return np.linalg.qr(rng.standard_normal((m, n, p)))[0]
+
+
+def rank_p_recovery(n: int, r: int, p: int, m: int, seed: int, kappa: float = 0.5,
+                    tau_frac: float = 0.5) -> RankPRecovery:
+    """Section 7 with measurement matrices of rank p (orthonormal columns);
+    ground truth and noise as in ``bilinear_recovery``; m given (the paper's
+    runs take m = 20 n r)."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, r))
+    G /= np.linalg.norm(G)
+    As = _orthonormal_blocks(rng, m, n, p)
+    Bs = _orthonormal_blocks(rng, m, n, p)
+    y0 = n * np.einsum("ipl,ipl->i", np.einsum("inp,nl->ipl", As, G), np.einsum("inp,nl->ipl", Bs, G))
+    v = rng.standard_normal(m)
+    v /= np.linalg.norm(v)
+    y = y0 + kappa * np.linalg.norm(y0) * v
+    U = rng.standard_normal((n, r))
+    U /= np.linalg.norm(U)
+    return RankPRecovery(n=n, r=r, p=p, As=As, Bs=Bs, y=y, G=G, tau=tau_frac * float(n), U=U)
+
+
 def arrival_trace(count: int, rate: float, seed: int, n_lo: int = 64, n_hi: int = 1024,
                   r_max: int = 8):
     """Poisson arrivals: (time_s, n, r, kind) with n log-uniform, r uniform."""

@@ -538,3 +538,73 @@ def test_bilinear_instance_matches_section7():
         assert abs(float(y0 @ y0) / float(noise @ noise) - 4.0) <= 1e-10
         assert abs(p.tau - (0.65 if r == 20 else 0.5) * np.trace(M)) <= 1e-12
         assert abs(np.linalg.norm(p.U) - 1.0) <= 1e-14
+
+
+# ------------------------------------------------------------------ rank-p measurements (Section 7)
+def test_rank_p_value_bruteforce_and_gradient():
+    """f'(X) = 1/2 sum_i (tau Tr(A_i^T X B_i) - y_i)^2 by plain loops; the
+    gradient against a central difference (f' is quadratic) and the
+    factored products against the dense gradient."""
+    p = synth.rank_p_recovery(6, 2, 3, 5, seed=21)
+    obj = meg.RankPMeasurements(p.As, p.Bs, p.y, 1.9)
+    rng = np.random.default_rng(4)
+    V = np.linalg.qr(rng.standard_normal((6, 2)))[0]
+    X = meg.Factored(V=V, mu=np.array([0.6, 0.3]), s=0.1 / 4)
+    Xd = X.dense()
+    total = 0.0
+    for i in range(obj.m):
+        tr = 0.0
+        for a in range(obj.p):
+            for j in range(obj.n):
+                for k in range(obj.n):
+                    tr += obj.As[i, j, a] * Xd[j, k] * obj.Bs[i, k, a]
+        total += 0.5 * (1.9 * tr - obj.y[i]) ** 2
+    assert abs(obj.value(X) - total) <= 1e-12 * total
+    D = rng.standard_normal((6, 6))
+    D = D + D.T
+    h = 1e-3
+    fd = (obj.value_dense(Xd + h * D) - obj.value_dense(Xd - h * D)) / (2 * h)
+    G = obj.grad_dense(X)
+    assert abs(fd - float(np.sum(G * D))) <= 1e-8 * max(1.0, abs(fd))
+    W = rng.standard_normal((6, 3))
+    assert np.allclose(obj.grad_apply(X, W), G @ W, rtol=1e-12, atol=1e-12)
+    assert np.allclose(obj.neg_grad0_apply(W), -obj.grad_dense(np.zeros((6, 6))) @ W, rtol=1e-12, atol=1e-12)
+    assert obj.grad_norm_bound(X) >= np.linalg.norm(G, 2) * (1 - 1e-12)
+
+
+def test_rank_p_reduces_to_bilinear_for_p1():
+    p = synth.rank_p_recovery(9, 2, 1, 7, seed=22)
+    obj = meg.RankPMeasurements(p.As, p.Bs, p.y, 2.5)
+    bil = meg.BilinearMeasurements(p.As[:, :, 0], p.Bs[:, :, 0], p.y, 2.5)
+    V = np.linalg.qr(np.random.default_rng(5).standard_normal((9, 2)))[0]
+    X = meg.Factored(V=V, mu=np.array([0.7, 0.2]), s=0.1 / 7)
+    assert abs(obj.value(X) - bil.value(X)) <= 1e-12 * bil.value(X)
+    assert np.allclose(obj.grad_dense(X), bil.grad_dense(X), rtol=1e-12, atol=1e-12)
+
+
+def test_rank_p_smoothness_footnote():
+    """Section 7, higher-rank measurements: for one measurement with
+    orthonormal-column A_1, B_1, ||grad f(X) - grad f(Y)||_F <= ||A_1 B_1^T||_F^2
+    ||X - Y||_F = p ||X - Y||_F and ||grad f(X) - grad f(Y)||_2 <=
+    ||A_1 B_1^T||_2^2 ||X - Y||_* = ||X - Y||_*."""
+    n, pp = 20, 5
+    p = synth.rank_p_recovery(n, 2, pp, 1, seed=23)
+    AB = p.As[0] @ p.Bs[0].T
+    assert abs(np.linalg.norm(AB, "fro") ** 2 - pp) <= 1e-12 * pp
+    assert abs(np.linalg.norm(AB, 2) - 1.0) <= 1e-12
+    obj = meg.RankPMeasurements(p.As, p.Bs, p.y, 1.0)
+    rng = np.random.default_rng(6)
+    for _ in range(5):
+        X, Y = rng.standard_normal((n, n)), rng.standard_normal((n, n))
+        X, Y = X + X.T, Y + Y.T
+        dG = obj.grad_dense(X) - obj.grad_dense(Y)
+        assert np.linalg.norm(dG, "fro") <= pp * np.linalg.norm(X - Y, "fro") * (1 + 1e-12)
+        assert np.linalg.norm(dG, 2) <= np.abs(np.linalg.eigvalsh(X - Y)).sum() * (1 + 1e-12)
+
+
+def test_rank_p_noiseless_truth_is_stationary():
+    p = synth.rank_p_recovery(16, 2, 4, 60, seed=24, kappa=0.0, tau_frac=1.0)
+    obj = meg.RankPMeasurements(p.As, p.Bs, p.y, p.tau)
+    Xs = p.M / p.tau
+    assert obj.value_dense(Xs) <= 1e-20 * float(p.y @ p.y)
+    assert np.linalg.norm(obj.grad_dense(Xs)) <= 1e-10 * np.linalg.norm(obj.grad_dense(np.zeros_like(Xs)))
