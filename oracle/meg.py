@@ -484,6 +484,44 @@ def warm_start_at(obj, r: int, U: np.ndarray, printed_sign: bool = False):
     return V[:, :r], project_simplex(w)
 
 
+# ---------------------------------------------------------------- trace of exp(M) by sampling
+def lanczos_quadrature(apply_M: Callable, u: np.ndarray, steps: int, fn: Callable = np.exp) -> float:
+    """u^T fn(M) u by `steps` Lanczos steps on the symmetric operator M from u
+    (Gauss quadrature): with the tridiagonal T_k of the Lanczos basis Q_k,
+    u^T fn(M) u ~ ||u||^2 e_1^T fn(T_k) e_1, exact for polynomials of degree
+    < 2k and for any fn once k reaches the dimension of the Krylov space.
+    Full re-orthogonalization keeps the basis orthonormal in floating point."""
+    nrm = float(np.linalg.norm(u))
+    Q = [u / nrm]
+    alpha, beta = [], []
+    for j in range(steps):
+        w = apply_M(Q[j])
+        a = float(Q[j] @ w)
+        alpha.append(a)
+        w = w - a * Q[j] - (beta[-1] * Q[j - 1] if j > 0 else 0.0)
+        Qm = np.array(Q)
+        w = w - Qm.T @ (Qm @ w)                         # re-orthogonalize against the basis
+        b = float(np.linalg.norm(w))
+        if j == steps - 1 or b <= 1e-14 * max(1.0, abs(a)):
+            break
+        beta.append(b)
+        Q.append(w / b)
+    T = np.diag(alpha) + np.diag(beta[: len(alpha) - 1], 1) + np.diag(beta[: len(alpha) - 1], -1)
+    th, S = np.linalg.eigh(T)
+    return nrm * nrm * float(np.sum(S[0, :] ** 2 * fn(th)))
+
+
+def hutchinson_trace_exp(apply_M: Callable, n: int, samples: int, steps: int, seed: int) -> float:
+    """Tr(exp(M)) = E_u[u^T exp(M) u], u ~ N(0, I) (the alternative for the
+    scalar b of the certificate that Section 4 notes after Lemma 2), as the
+    mean over `samples` Gaussian vectors of Lanczos quadratures."""
+    rng = np.random.default_rng(seed)
+    total = 0.0
+    for _ in range(samples):
+        total += lanczos_quadrature(apply_M, rng.standard_normal(n), steps)
+    return total / samples
+
+
 # ---------------------------------------------------------------- certificate
 def certificate(sig: np.ndarray, n: int, r: int, eps: float) -> float:
     """log((n - r) lambda_{r+1}(Y) / (eps b)) with lambda_i(Y) = exp(sigma_i).

@@ -608,3 +608,37 @@ def test_rank_p_noiseless_truth_is_stationary():
     Xs = p.M / p.tau
     assert obj.value_dense(Xs) <= 1e-20 * float(p.y @ p.y)
     assert np.linalg.norm(obj.grad_dense(Xs)) <= 1e-10 * np.linalg.norm(obj.grad_dense(np.zeros_like(Xs)))
+
+
+# ------------------------------------------------------------------ Tr exp(M) by sampling (certificate's b)
+def test_lanczos_quadrature_is_gauss_exact():
+    """k Lanczos steps integrate polynomials of degree < 2k exactly, and any
+    function once k = n."""
+    rng = np.random.default_rng(31)
+    n = 12
+    Mx = rng.standard_normal((n, n))
+    Mx = (Mx + Mx.T) / 4
+    u = rng.standard_normal(n)
+    k = 4
+    for deg in range(2 * k):
+        exact = float(u @ np.linalg.matrix_power(Mx, deg) @ u)
+        got = meg.lanczos_quadrature(lambda v: Mx @ v, u, k, fn=lambda x, d=deg: x ** d)
+        assert abs(got - exact) <= 1e-10 * max(1.0, abs(exact)), (deg, got, exact)
+    w, V = np.linalg.eigh(Mx)
+    exact = float(u @ (V * np.exp(w)) @ V.T @ u)
+    assert abs(meg.lanczos_quadrature(lambda v: Mx @ v, u, n) - exact) <= 1e-11 * exact
+
+
+def test_hutchinson_trace_within_variance_bound():
+    """E[u^T Y u] = Tr Y for u ~ N(0, I) with variance 2 ||Y||_F^2; the
+    estimate on a MEG mirror matrix M_t = log X_t - eta grad f stays within
+    four standard deviations of Tr exp(M_t)."""
+    prob = synth.dense_quadratic(60, 3, seed=32, sigma=1e-3)
+    obj = meg.DenseQuadratic(prob.M)
+    X = meg.init_X1(prob.U, prob.w, meg.eps_schedule(0))
+    Mt = meg.mirror_matrix(X, obj, 1, 1.0)
+    w = np.linalg.eigvalsh(Mt)
+    tr, fro = float(np.exp(w).sum()), float(np.sqrt((np.exp(w) ** 2).sum()))
+    N = 200
+    est = meg.hutchinson_trace_exp(lambda v: Mt @ v, 60, N, 20, seed=5)
+    assert abs(est - tr) <= 4 * math.sqrt(2.0 / N) * fro, (est, tr, fro)
