@@ -642,3 +642,18 @@ def test_hutchinson_trace_within_variance_bound():
     N = 200
     est = meg.hutchinson_trace_exp(lambda v: Mt @ v, 60, N, 20, seed=5)
     assert abs(est - tr) <= 4 * math.sqrt(2.0 / N) * fro, (est, tr, fro)
+
+
+def test_block_krylov_matches_exact_and_needs_fewer_products():
+    """The block Krylov eigensolver gives the exact-eigensolver step (Ritz
+    values of the top r + 1 to 1e-10, X to 1e-9) and reaches the residual
+    with fewer operator products than the subspace iteration."""
+    prob = synth.dense_quadratic(150, 4, seed=41, sigma=1e-3)
+    obj = meg.DenseQuadratic(prob.M)
+    X = meg.init_X1(prob.U, prob.w, meg.eps_schedule(0))
+    Xe, ie, _ = meg.lowrank_step(X, obj, 1, 1.0, meg.eps_schedule(1), method="exact")
+    Xk, ik, _ = meg.lowrank_step(X, obj, 1, 1.0, meg.eps_schedule(1), method="krylov", k=8)
+    Xs, is_, _ = meg.lowrank_step(X, obj, 1, 1.0, meg.eps_schedule(1), method="subspace", k=8, need_r1=True)
+    assert np.max(np.abs(ik.sig[:5] - ie.sig[:5]) / np.abs(ie.sig[:5])) <= 1e-10
+    assert meg.frob_dist(Xk, Xe) <= 1e-9 * math.sqrt(meg.frob_inner(Xe, Xe))
+    assert ik.products < is_.products, (ik.products, is_.products)
