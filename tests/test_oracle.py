@@ -657,3 +657,36 @@ def test_block_krylov_matches_exact_and_needs_fewer_products():
     assert np.max(np.abs(ik.sig[:5] - ie.sig[:5]) / np.abs(ie.sig[:5])) <= 1e-10
     assert meg.frob_dist(Xk, Xe) <= 1e-9 * math.sqrt(meg.frob_inner(Xe, Xe))
     assert ik.products < is_.products, (ik.products, is_.products)
+
+
+@pytest.mark.parametrize("kind", ["dense_quadratic", "linear", "completion"])
+def test_objective_gradients_central_difference(kind):
+    """Each deterministic objective is at most quadratic in X, so a central
+    difference of its value along a symmetric direction equals <grad f, D>
+    up to rounding; the factored product grad_apply matches the dense
+    gradient, and -grad f(0) applied matches the dense gradient at 0."""
+    n, r = 24, 3
+    rng = np.random.default_rng(51)
+    if kind == "dense_quadratic":
+        p = synth.dense_quadratic(n, r, seed=52, sigma=1e-2)
+        obj = meg.DenseQuadratic(p.M)
+    elif kind == "linear":
+        obj = meg.Linear(synth.linear(n, seed=53).C)
+    else:
+        p = synth.completion(n, r, 0.3, seed=54)
+        obj = meg.Completion(n, p.rowptr, p.col, p.val)
+    V = np.linalg.qr(rng.standard_normal((n, r)))[0]
+    X = meg.Factored(V=V, mu=np.array([0.5, 0.25, 0.15]), s=0.1 / (n - r))
+    Xd = X.dense()
+    D = rng.standard_normal((n, n))
+    D = D + D.T
+    h = 1e-3
+    fd = (obj.value_dense(Xd + h * D) - obj.value_dense(Xd - h * D)) / (2 * h)
+    G = obj.grad_dense(X)
+    assert abs(fd - float(np.sum(G * D))) <= 1e-8 * max(1.0, abs(fd)), (kind, fd, float(np.sum(G * D)))
+    assert abs(obj.value(X) - obj.value_dense(Xd)) <= 1e-12 * max(1.0, abs(obj.value(X)))
+    W = rng.standard_normal((n, 4))
+    assert np.allclose(obj.grad_apply(X, W), G @ W, rtol=1e-11, atol=1e-12)
+    G0 = obj.grad_dense(meg.Factored(V=np.zeros((n, 1)), mu=np.zeros(1), s=0.0))
+    assert np.allclose(obj.neg_grad0_apply(W), -G0 @ W, rtol=1e-11, atol=1e-12)
+    assert obj.grad_norm_bound(X) >= np.linalg.norm(G, 2) * (1 - 1e-12)
