@@ -354,18 +354,109 @@ def test_exact_and_subspace_variants_agree(kind):
         np.testing.assert_allclose(a.sig[:r], b.sig[:r], rtol=1e-10)
 
 
-def test_stochastic_gradient_is_unbiased():
-    n, r = 12, 2
-    p = synth.measurements(n, r, 60, 16, seed=24)
-    obj = meg.Measurements(p.A, p.y, p.L, seed=3)
-    rng = np.random.default_rng(25)
+def _meas_value_loop(A, y, X):
+    """(1/m) sum_i (a_i^T X a_i - y_i)^2 written out with plain loops over the
+    entries of X (the objective as the measurement problem states it)."""
+    m, n = A.shape
+    total = 0.0
+    for i in range(m):
+        q = 0.0
+        for a in range(n):
+            for b in range(n):
+                q += A[i, a] * X[a, b] * A[i, b]
+        total += (q - y[i]) ** 2
+    return total / m
+
+
+def _sym_dir(rng, n):
+    D = rng.standard_normal((n, n))
+    return D + D.T
+
+
+def test_measurements_value_bruteforce():
+    """Factored (chunked) value, dense value and a plain triple loop agree."""
+    n, r = 6, 2
+    p = synth.measurements(n, r, 11, 4, seed=61)
+    obj = meg.Measurements(p.A, p.y, p.L, seed=7)
+    rng = np.random.default_rng(62)
     X = _rand_factored(rng, n, r)
-    full = (2.0 / obj.m) * (p.A.T * (obj.quad(X, np.arange(obj.m)) - p.y)) @ p.A
+    ref = _meas_value_loop(p.A, p.y, X.dense())
+    assert abs(obj.value(X) - ref) <= 1e-13 * max(1.0, ref)
+    assert abs(obj.value_dense(X.dense()) - ref) <= 1e-13 * max(1.0, ref)
+    # one measurement by hand: X = I/n gives a^T X a = ||a||^2 / n
+    one = meg.Measurements(p.A[:1], p.y[:1], 1, seed=0)
+    Xi = meg.Factored(V=np.eye(n)[:, :1], mu=np.array([1.0 / n]), s=1.0 / n)
+    assert abs(one.value(Xi) - (float(p.A[0] @ p.A[0]) / n - p.y[0]) ** 2) <= 1e-14
+
+
+def test_measurements_minibatch_gradient_central_difference():
+    """The step-t gradient is the exact gradient of the minibatch objective
+    f_B(X) = (1/L) sum_{b in B_t} (a_b^T X a_b - y_b)^2 (repeats counted), i.e.
+    (2/L) sum_b r_b a_b a_b^T.  f_B is quadratic in X, so a central difference
+    of its brute-force value along a symmetric direction is exact up to
+    rounding; a wrong factor (1/L for 2/L) or a dropped y fails here."""
+    n, r = 9, 2
+    p = synth.measurements(n, r, 40, 7, seed=63)
+    obj = meg.Measurements(p.A, p.y, p.L, seed=11)
+    rng = np.random.default_rng(64)
+    X = _rand_factored(rng, n, r)
+    Xd = X.dense()
+    for t in (1, 5):
+        idx = obj.batch(t)
+        assert len(idx) == p.L
+        D = _sym_dir(rng, n)
+        h = 1e-3
+        fB = lambda Y: _meas_value_loop(p.A[idx], p.y[idx], Y)
+        fd = (fB(Xd + h * D) - fB(Xd - h * D)) / (2 * h)
+        G = obj.grad_dense(X, t)
+        assert abs(fd - float(np.sum(G * D))) <= 1e-9 * max(1.0, abs(fd)), (t, fd, float(np.sum(G * D)))
+        W = rng.standard_normal((n, 3))
+        np.testing.assert_allclose(obj.grad_apply(X, W, t), G @ W, rtol=1e-11, atol=1e-12)
+        assert obj.grad_norm_bound(X, t) >= np.linalg.norm(G, 2) * (1 - 1e-12)
+
+
+def test_measurements_full_gradient_and_warm_start_operator():
+    """The full objective f = (1/m) sum (a^T X a - y)^2: its gradient from a
+    central difference of the triple-loop value equals (i) the mean of the
+    minibatch gradients over many steps (unbiasedness, Section 6) and (ii) at
+    X = 0, minus the warm-start operator -grad f(0) = (2/m) sum y_i a_i a_i^T."""
+    n, r = 8, 2
+    p = synth.measurements(n, r, 30, 10, seed=65)
+    obj = meg.Measurements(p.A, p.y, p.L, seed=3)
+    rng = np.random.default_rng(66)
+    X = _rand_factored(rng, n, r)
+    Xd = X.dense()
+    f = lambda Y: _meas_value_loop(p.A, p.y, Y)
+    # the full gradient, entry by entry, from central differences along the
+    # symmetric unit directions E_ab + E_ba (exact for a quadratic)
+    h = 1e-3
+    G = np.zeros((n, n))
+    for a in range(n):
+        for b in range(a, n):
+            E = np.zeros((n, n))
+            E[a, b] += 1.0
+            E[b, a] += 1.0
+            g = (f(Xd + h * E) - f(Xd - h * E)) / (2 * h)     # = <grad, E>
+            if a == b:
+                G[a, a] = g / 2.0
+            else:
+                G[a, b] = G[b, a] = g / 2.0
     avg = np.mean([obj.grad_dense(X, t) for t in range(1, 3001)], axis=0)
-    assert np.linalg.norm(avg - full) < 0.08 * np.linalg.norm(full)
-    # the implicit product equals the dense stochastic gradient times W
+    assert np.linalg.norm(avg - G) < 0.08 * np.linalg.norm(G)
+    # a factor error of 2 in either the value or the gradient would be 100% off
+    assert abs(float(np.sum(avg * G)) / float(np.sum(G * G)) - 1.0) < 0.08
+    # -grad f(0) from central differences at X = 0 against the warm-start operator
+    Z = np.zeros((n, n))
     W = rng.standard_normal((n, 3))
-    np.testing.assert_allclose(obj.grad_apply(X, W, 4), obj.grad_dense(X, 4) @ W, atol=1e-10)
+    G0 = np.zeros((n, n))
+    for a in range(n):
+        for b in range(a, n):
+            E = np.zeros((n, n))
+            E[a, b] += 1.0
+            E[b, a] += 1.0
+            g = (f(Z + h * E) - f(Z - h * E)) / (2 * h)
+            G0[a, b] = G0[b, a] = g / 2.0
+    np.testing.assert_allclose(obj.neg_grad0_apply(W), -G0 @ W, rtol=1e-8, atol=1e-9)
 
 
 # ------------------------------------------------------------------ bilinear measurements (Section 7)
