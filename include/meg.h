@@ -56,7 +56,9 @@ typedef enum {
 enum {
     MEG_FP64 = 0,        /* every array and operation in float64 */
     MEG_FP32 = 1,        /* float32 arrays and products; compensated
-                            (double-word) reductions; float64 k x k island */
+                            (double-word) reductions; float32 k x k island
+                            (Cholesky, Jacobi) with double-word refinement,
+                            float64 Ritz values, exp-map and certificate */
     MEG_MIXED_BF16 = 2   /* as MEG_FP32, dense data in bfloat16 and the dense
                             product on tcgen05 tensor cores (fp32 accumulate) */
 };
@@ -73,7 +75,8 @@ enum {
 
 /*
  * Options of one solve (Algorithm 2 inputs).
- *   n, r       : dimension and SVD rank, 1 <= r <= n - 1, r <= 30.
+ *   n, r       : dimension and SVD rank, 2 <= n <= 2^28, 1 <= r <= n - 1,
+ *                r <= 30.
  *   p          : extra subspace vectors, k = r + p, 1 <= p, k <= min(n, 32).
  *                (p >= 1 because the certificate needs sigma_{r+1}.)
  *   q          : subspace-iteration products per MEG iteration, 1..8.
@@ -128,14 +131,17 @@ typedef struct {
  * V0: host, n x r row-major, orthonormal columns; lam0: host, r values on
  * the unit simplex.  V0 == NULL leaves X_1 unset until meg_warm_start.
  * The library copies V0/lam0; the caller keeps ownership.
- * Errors: MEG_ERR_INVALID_ARG (sizes, schedule), MEG_ERR_OOM, MEG_ERR_CUDA.
+ * Errors: MEG_ERR_INVALID_ARG (sizes, schedule), MEG_ERR_OOM (also when
+ * meg_footprint of the solve exceeds the device's free memory, checked
+ * before anything is allocated), MEG_ERR_CUDA.
  */
 meg_status meg_create(const meg_options* opt, const double* V0, const double* lam0,
                       meg_handle* out);
 
 /* meg_set_objective -- attach f (problem statement, eq. Model).  The
- * descriptor is copied, the arrays are borrowed.  CSR row pointers are
- * validated on the host copy the call makes (monotone, in range).
+ * descriptor is copied, the arrays are borrowed.  The CSR structure is
+ * validated on host copies the call makes: rowptr[0] = 0, rowptr[n] = nnz,
+ * rowptr monotone, every column index in [0, n).
  * Errors: MEG_ERR_INVALID_ARG, MEG_ERR_CUDA. */
 meg_status meg_set_objective(meg_handle h, const meg_objective_desc* d);
 
@@ -156,11 +162,23 @@ meg_status meg_warm_start_many(const meg_handle* solves, int count, int products
 meg_status meg_step(meg_handle h, int nsteps);
 
 /* meg_solve -- iterate until the relative objective gap
- * (f(X_t) - fstar)/(f(X_1) - fstar) <= tol or max_iters iterations;
- * fstar = 0 unless meg_set_fstar gave one.  f is evaluated every 10
- * iterations with meg_objective's accurate pass.  *iters_out (may be
- * NULL) receives the iterations run.  Returns MEG_ERR_NOT_CONVERGED when
- * max_iters is reached first. */
+ * (f(X_t) - fstar)/(f(X_1) - fstar) <= tol or max_iters iterations
+ * (problem statement, eq. Model; Algorithm 2 run to a tolerance).
+ * fstar = 0 unless meg_set_fstar gave one.  f(X_1) is the objective at
+ * the solve's first iterate, recorded when X_1 and the objective are both
+ * set (meg_create with V0, meg_set_objective, meg_warm_start) and kept in
+ * the checkpoint state.  f is evaluated every 10 iterations with
+ * meg_objective's accurate pass and tested on the device: the iterations,
+ * the objective pass and the test run as one CUDA graph with a
+ * conditional while-node, launched once; the host waits once (and once
+ * more for a final max_iters % 10 iterations).  *iters_out (may be NULL)
+ * receives the iterations run by this call.
+ * Errors: MEG_ERR_INVALID_ARG for tol <= 0, max_iters < 0, or
+ * f(X_1) - fstar <= 0 (the gap is undefined: give f* below f(X_1) with
+ * meg_set_fstar, e.g. for a linear objective whose f can be negative);
+ * MEG_ERR_STATE when f(X_1) is unknown (objective set after the first
+ * step) or the solve belongs to a group; MEG_ERR_NUMERIC when f is not
+ * finite; MEG_ERR_NOT_CONVERGED when max_iters is reached first. */
 meg_status meg_solve(meg_handle h, double tol, int max_iters, int* iters_out);
 
 /* meg_set_fstar -- known optimal value for meg_solve's relative gap. */
@@ -194,7 +212,10 @@ meg_status meg_objective(meg_handle h, double* f);
  * same n, r, p and precision (objective data are not part of the state).
  * The buffer starts with eight int64 header words: a magic number, n, r,
  * k, precision, objective kind, 1 if X_1 is set, and 1 if the dense
- * product runs on the tensor cores (tcgen05) for this solve.
+ * product runs on the tensor cores (tcgen05) for this solve.  A solve
+ * that has an objective accepts only a state saved under the same
+ * objective kind and product path (MEG_ERR_INVALID_ARG otherwise): the
+ * small state carries constants of the objective data.
  * Iterating T steps, saving, restoring and iterating T more gives the
  * same bits as 2T steps.  Both calls synchronise the stream. */
 int64_t meg_state_size(meg_handle h);
@@ -284,8 +305,10 @@ typedef struct {
                                  objective reads all m measurements) */
 } meg_server_options;
 
-/* One request.  Host pointers (data, y, V0, lam0) are copied when the
- * request is admitted and must stay valid until its result is returned;
+/* One request.  meg_server_submit copies this struct, not the arrays it
+ * points to: the host arrays data, y, V0 and lam0 are read later, when
+ * the worker thread admits the request, so they must stay valid and
+ * unchanged until the request's result comes back from meg_server_poll;
  * out_V (n x r), out_mu (r) and out_s (1) are written before the result
  * is returned (each may be NULL). */
 typedef struct {
@@ -347,7 +370,12 @@ meg_status meg_server_destroy(meg_server s);
  * per GPU that loads it, kept until the process exits), so n is limited
  * to MEG_NOALLOC_MAX_N; larger n returns MEG_ERR_INVALID_ARG.  The first
  * call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.
+ * device current) and caches it with the current CUDA context; a call
+ * under another context (after a device reset) looks it up again.  Make
+ * the first call, and the first after a reset, before any stream capture.
+ * Each call enqueues two operations on `stream`: a memset that zeroes the
+ * array's counters, then the reduction kernel (a captured call records
+ * two graph nodes); *f_out is valid once both have run.
  * Every call shares the array: calls whose work overlaps on the GPU
  * (different streams, or different host threads) race -- order them.
  * The result equals meg_objective's for the same iterate and data.

@@ -23,7 +23,8 @@ MEG_DENSE_QUAD, MEG_CSR_QUAD, MEG_MEAS_STOCH, MEG_LINEAR = 0, 1, 2, 3
 PRECISION = {"fp64": MEG_FP64, "fp32": MEG_FP32, "bf16": MEG_MIXED_BF16}
 # slots of the small state (csrc/meg_dev.cuh, SmallSlot)
 SM_T, SM_EPS, SM_S, SM_LOGS, SM_SHIFT, SM_C0, SM_ALPHA, SM_GNORM, SM_FEST, SM_CERT, SM_HOLDS, \
-    SM_FIRST_HOLD, SM_STATUS, SM_TRD, SM_FROD2, SM_LAST_T, SM_LSE, SM_RSS, SM_RESID_BOUND, SM_ETA = range(20)
+    SM_FIRST_HOLD, SM_STATUS, SM_TRD, SM_FROD2, SM_LAST_T, SM_LSE, SM_RSS, SM_RESID_BOUND, SM_ETA, \
+    SM_JSWEEPS, SM_F1 = range(22)
 SM_MU, SM_DCOEF, SM_SIGMA = 32, 64, 96
 SM_TOTAL = 128 + 7 * 1024
 

@@ -354,15 +354,22 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
     if (tid < k) {
         int rank = 0;
         const double v = wv[tid];
-        for (int j = 0; j < k; ++j) rank += (wv[j] > v) || (wv[j] == v && j < tid);
+        for (int j = 0; j < k; ++j) rank += ranks_before(wv[j], j, v, tid);
         perm[rank] = tid;
     }
     __syncthreads();
     if (tid < k) sig[tid] = wv[perm[tid]] + shift;
-    // 5. first-order correction of the top r vectors: coefficients in Bh (k x r)
-    for (int e = tid; e < k * r; e += nt) {
-        const int j = e / r, i = e % r, ci = perm[i];
-        float cf = 0.f;
+    // 5. perturbation theory in the Jacobi basis, h_ji = q_j^T Ht q_i (exact
+    //    products): first-order correction of the top r vectors, coefficients
+    //    h_ji / (theta_i - theta_j) in Bh (k x r); second-order correction of
+    //    the top r + 1 Ritz values, sum_j h_ji^2 / (theta_i - theta_j), its terms
+    //    in Bl (the Rayleigh quotient of a vector that Jacobi left a relative
+    //    1e-5 off is low by up to that squared times the spread; without this
+    //    term the Ritz values carry that bias from one iteration to the next)
+    const int rc = min(r + 1, k);
+    for (int e = tid; e < k * rc; e += nt) {
+        const int j = e / rc, i = e % rc, ci = perm[i];
+        float cf = 0.f, c2 = 0.f;
         if (j != ci) {
             dw h = {0.f, 0.f};
             for (int a = 0; a < k; ++a) {
@@ -371,9 +378,19 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
                 dot2_acc(h, q, F3[a * MEG_LDK + ci]);
             }
             const double hv = dw_value(h), gap = wv[ci] - wv[j];
-            if (fabs(gap) > 100.0 * fabs(hv)) cf = (float)(hv / gap);
+            if (fabs(gap) > 100.0 * fabs(hv)) {
+                cf = (float)(hv / gap);
+                c2 = (float)(hv * hv / gap);
+            }
         }
-        Bh[j * MEG_LDK + i] = cf;
+        if (i < r) Bh[j * MEG_LDK + i] = cf;
+        Bl[j * MEG_LDK + i] = c2;
+    }
+    __syncthreads();
+    if (tid < rc) {
+        double c = 0.0;
+        for (int j = 0; j < k; ++j) c += (double)Bl[j * MEG_LDK + tid];
+        sig[tid] += c;
     }
     __syncthreads();
     mm_f32(F2, false, Bh, Bl, k, k, r);                        // corr = Q coef  (k x r)
@@ -2062,6 +2079,30 @@ cudaError_t launch_objective(const GroupLaunch& g, double* out_f) {
     const bool fits = need > 0 && need <= OBJ_SMEM_MAX;
     return launch_k(k_objective<float>, grid, blk, fits ? need : 0, g.stream, 1, g.d_solves, g.ns, out_f,
                     fits ? (int)(need / 4) : 0);
+}
+
+// ==========================================================================
+// meg_solve's stopping test (problem statement: the relative objective gap
+// (f(X_t) - f*) / (f(X_1) - f*) <= tol), one thread, after each chunk of
+// iterations of the device loop.  It counts the chunk, records f, and ends
+// the loop (conditional graph node) when the test holds, when f is not
+// finite, when a kernel recorded an error, or when the chunk limit is reached,
+// so the loop always ends after at most SM_SOLVE_LIMIT chunks.
+__global__ void k_solve_check(double* sm, const double* f, cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double fv = *f, fstar = sm[SM_SOLVE_FSTAR];
+    const double chunks = sm[SM_SOLVE_CHUNKS] + 1.0;
+    sm[SM_SOLVE_CHUNKS] = chunks;
+    sm[SM_SOLVE_F] = fv;
+    const bool conv = (fv - fstar) <= sm[SM_SOLVE_TOL] * (sm[SM_F1] - fstar);
+    if (conv) sm[SM_SOLVE_DONE] = 1.0;
+    if (conv || !isfinite(fv) || sm[SM_STATUS] != 0.0 || chunks >= sm[SM_SOLVE_LIMIT])
+        cudaGraphSetConditional(cond, 0u);
+}
+
+cudaError_t launch_solve_check(double* sm, const double* f, cudaGraphConditionalHandle cond, cudaStream_t st) {
+    k_solve_check<<<1, 32, 0, st>>>(sm, f, cond);
+    return cudaGetLastError();
 }
 
 // Programmatic dependent launch is opt-in (MEG_PDL=1): on the n = 4096 batch

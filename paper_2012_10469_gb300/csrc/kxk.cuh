@@ -4,6 +4,16 @@
 // All routines must be called by every thread of the block.
 #pragma once
 
+// Order of a non-increasing sort by rank: element (u, j) comes before (v, i)
+// when u > v, or u == v and j < i.  NaN counts as -infinity, so the relation
+// is a strict total order and the ranks of k values are a permutation of
+// 0..k-1 even when the values are not finite.
+__device__ __forceinline__ int ranks_before(double u, int j, double v, int i) {
+    u = isnan(u) ? -INFINITY : u;
+    v = isnan(v) ? -INFINITY : v;
+    return (u > v) || (u == v && j < i);
+}
+
 #include "meg_dev.cuh"
 
 // A (k x k, SPD) -> lower Cholesky factor L in place (upper part zeroed).
@@ -140,14 +150,12 @@ __device__ inline void kxk_jacobi(double* A, double* Q, double* B, double* w, do
             __syncthreads();
         }
     }
-    // sort eigenpairs, non-increasing (selection by rank; ties by index)
+    // sort eigenpairs, non-increasing (selection by rank; ties by index, NaN
+    // last, so the ranks always form a permutation)
     if (tid < k) {
         double v = A[tid * MEG_LDK + tid];
         int rank = 0;
-        for (int j = 0; j < k; ++j) {
-            double u = A[j * MEG_LDK + j];
-            rank += (u > v) || (u == v && j < tid);
-        }
+        for (int j = 0; j < k; ++j) rank += ranks_before(A[j * MEG_LDK + j], j, v, tid);
         partner[tid] = rank;
         w[rank] = v;
     }

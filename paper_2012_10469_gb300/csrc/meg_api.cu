@@ -122,6 +122,12 @@ struct meg_solve_s {
     double fstar = 0.0;
     // solo graph of one iteration
     cudaGraphExec_t gexec = nullptr;
+    // meg_solve's device loop: a conditional (while) node whose body runs a
+    // chunk of iterations, the objective pass and the stopping test
+    cudaGraphExec_t solve_gexec = nullptr;
+    // set once the device reported an error (MEG_ERR_NUMERIC / TIMEOUT): every
+    // later call except meg_destroy answers MEG_ERR_STATE
+    bool failed = false;
     bool in_group = false;
     cudaStream_t group_stream = nullptr;   // stream of the group while in one
     bool own_stream = false;               // created by the library (caller gave NULL)
@@ -244,11 +250,13 @@ meg_status join_group_stream(meg_solve_s* h) {
 }
 
 meg_status check_device_status(meg_solve_s* h) {
+    if (h->failed) return fail(MEG_ERR_STATE, "the solve failed earlier on the device; only meg_destroy remains");
     if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
     double st = 0.0;
     CU(cudaMemcpyAsync(&st, h->sm + SM_STATUS, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     if (st != 0.0) {
+        h->failed = true;
         char msg[128];
         snprintf(msg, sizeof msg, "device reported status %d (numeric breakdown in a k x k step)", (int)st);
         return fail((meg_status)(int)st, msg);
@@ -264,6 +272,23 @@ meg_status eval_objective(meg_solve_s* h, double* f) {
     CU(cudaMemcpyAsync(&v, h->d_f, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     *f = v;
+    return MEG_OK;
+}
+
+// f(X_1), the denominator of meg_solve's relative gap, kept in the small state
+// (so it travels with a checkpoint): evaluated when X_1 and the objective are
+// both known and the solve has not stepped yet (t = 1).
+meg_status record_f1(meg_solve_s* h) {
+    if (!h->has_obj || !h->has_x) return MEG_OK;
+    double t = 0.0;
+    CU(cudaMemcpyAsync(&t, h->sm + SM_T, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (t != 1.0) return MEG_OK;
+    double f = 0.0;
+    meg_status st = eval_objective(h, &f);
+    if (st != MEG_OK) return st;
+    CU(cudaMemcpyAsync(h->sm + SM_F1, &f, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     return MEG_OK;
 }
 
@@ -334,8 +359,8 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
     if (!opt || !out) return fail(MEG_ERR_INVALID_ARG, "meg_create: null argument");
     *out = nullptr;
     const int n = opt->n, r = opt->r, p = opt->p, q = opt->q;
-    if (n < 2 || r < 1 || r > MEG_RMAX || r > n - 1)
-        return fail(MEG_ERR_INVALID_ARG, "meg_create: need 1 <= r <= min(n - 1, 30)");
+    if (n < 2 || n > MEG_NMAX || r < 1 || r > MEG_RMAX || r > n - 1)
+        return fail(MEG_ERR_INVALID_ARG, "meg_create: need 2 <= n <= 2^28 and 1 <= r <= min(n - 1, 30)");
     if (p < 1 || r + p > MEG_KMAX || r + p > n)
         return fail(MEG_ERR_INVALID_ARG, "meg_create: need p >= 1 and r + p <= min(n, 32)");
     if (q < 1 || q > 8) return fail(MEG_ERR_INVALID_ARG, "meg_create: need 1 <= q <= 8");
@@ -359,6 +384,16 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
     }
     if (cudaError_t e = ensure_attributes(); e != cudaSuccess)
         return fail(MEG_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    // a solve whose own buffers cannot fit the device's free memory is refused
+    // before anything is allocated
+    {
+        size_t freeb = 0, totb = 0;
+        const int64_t need = meg_footprint(n, r, p, opt->precision, -1);
+        if (cudaMemGetInfo(&freeb, &totb) == cudaSuccess && need > (int64_t)freeb)
+            return fail(MEG_ERR_OOM, "meg_create: the solve needs " + std::to_string(need) +
+                                         " device bytes, " + std::to_string(freeb) + " are free");
+        cudaGetLastError();
+    }
 
     meg_solve_s* h = new meg_solve_s();
     h->opt = *opt;
@@ -386,8 +421,9 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
     auto alloc = [&](void** ptr, size_t bytes) -> bool {
         return cudaMallocAsync(ptr, std::max<size_t>(bytes, 16), h->stream) == cudaSuccess;
     };
-    bool ok = alloc(&h->V, 8 * n * r) && alloc(&h->Vn, 8 * n * r) && alloc(&h->W, ts * n * k) &&
-              alloc(&h->Wp, ts * n * k) && alloc(&h->Z, ts * n * k) && alloc(&h->Y, ts * n * k) &&
+    const size_t nr8 = (size_t)8 * n * r, nkt = ts * n * k;    // sizes in size_t: n * r * 8 can pass 2^31
+    bool ok = alloc(&h->V, nr8) && alloc(&h->Vn, nr8) && alloc(&h->W, nkt) &&
+              alloc(&h->Wp, nkt) && alloc(&h->Z, nkt) && alloc(&h->Y, nkt) &&
               alloc((void**)&h->part, sizeof(float) * (d.nb_red + groups) * 2 * RED_MAX_ENTRIES) &&
               alloc((void**)&h->ctr, sizeof(unsigned) * (groups + 3)) &&
               alloc((void**)&h->sm, sizeof(double) * SM_TOTAL) && alloc((void**)&h->d_f, sizeof(double)) &&
@@ -416,13 +452,14 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
     std::vector<double> smh(SM_TOTAL, 0.0);
     smh[SM_T] = 1.0;
     smh[SM_ETA] = opt->eta;
+    smh[SM_F1] = std::nan("");
     if (V0) {
         for (int i = 0; i < r; ++i) smh[SM_MU + i] = (1.0 - eps0) * lam0[i] + eps0 / n;
         smh[SM_S] = eps0 / n;
     }
     if (cudaMemsetAsync(h->ctr, 0, sizeof(unsigned) * (groups + 3), h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->V, 0, 8 * n * r, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->W, 0, ts * n * k, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->V, 0, nr8, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->W, 0, nkt, h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->sm, smh.data(), sizeof(double) * SM_TOTAL, cudaMemcpyHostToDevice, h->stream) !=
             cudaSuccess) {
         meg_destroy(h);
@@ -451,6 +488,7 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
 
 meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     if (!h || !o) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: null argument");
+    if (h->failed) return fail(MEG_ERR_STATE, "meg_set_objective: the solve failed earlier on the device");
     if (h->in_group) return fail(MEG_ERR_STATE, "meg_set_objective: solve belongs to a group");
     SolveDev& d = h->desc;
     const int n = h->n, k = h->k;
@@ -466,6 +504,14 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
             return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: rowptr[0] must be 0 and rowptr[n] == nnz");
         for (int i = 0; i < n; ++i)
             if (rp[i + 1] < rp[i]) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: rowptr not monotone");
+        // column indices address rows of V and W in the kernels: all must lie in [0, n)
+        std::vector<int> cols((size_t)o->nnz);
+        if (o->nnz > 0) {
+            CU(cudaMemcpyAsync(cols.data(), o->col, sizeof(int) * (size_t)o->nnz, cudaMemcpyDeviceToHost, h->stream));
+            CU(cudaStreamSynchronize(h->stream));
+        }
+        for (int64_t e = 0; e < o->nnz; ++e)
+            if (cols[e] < 0 || cols[e] >= n) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: column index out of range");
     } else if (o->kind == MEG_MEAS_STOCH) {
         if (!o->A || !o->y || o->m < 1 || o->L < 1)
             return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: measurement arrays missing");
@@ -552,11 +598,14 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     }
     h->has_obj = true;
     if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
-    return refresh_bounds(h);
+    if (h->solve_gexec) { cudaGraphExecDestroy(h->solve_gexec); h->solve_gexec = nullptr; }
+    if ((st = refresh_bounds(h)) != MEG_OK) return st;
+    return record_f1(h);
 }
 
 meg_status meg_warm_start(meg_handle h, int products) {
     if (!h) return fail(MEG_ERR_INVALID_ARG, "meg_warm_start: null handle");
+    if (h->failed) return fail(MEG_ERR_STATE, "meg_warm_start: the solve failed earlier on the device");
     if (!h->has_obj) return fail(MEG_ERR_STATE, "meg_warm_start: objective not set");
     if (products < 1) return fail(MEG_ERR_INVALID_ARG, "meg_warm_start: products >= 1");
     if (h->in_group) return fail(MEG_ERR_STATE, "meg_warm_start: solve belongs to a group");
@@ -600,11 +649,13 @@ meg_status meg_warm_start(meg_handle h, int products) {
     CU(cudaStreamSynchronize(h->stream));
     h->has_x = true;
     if ((st = check_device_status(h)) != MEG_OK) return st;
-    return refresh_bounds(h);
+    if ((st = refresh_bounds(h)) != MEG_OK) return st;
+    return record_f1(h);
 }
 
 static meg_status ready(meg_handle h, const char* who) {
     if (!h) return fail(MEG_ERR_INVALID_ARG, std::string(who) + ": null handle");
+    if (h->failed) return fail(MEG_ERR_STATE, std::string(who) + ": the solve failed earlier on the device");
     if (!h->has_obj || !h->has_x) return fail(MEG_ERR_STATE, std::string(who) + ": objective or X_1 not set");
     return MEG_OK;
 }
@@ -645,23 +696,94 @@ meg_status meg_objective(meg_handle h, double* f) {
     return eval_objective(h, f);
 }
 
+namespace {
+// The device loop of meg_solve: a graph whose only node is a conditional
+// while-loop; its body runs SOLVE_CHUNK iterations, the accurate objective
+// pass and k_solve_check, which ends the loop.  Parameters (tol, f*, chunk
+// limit) live in the small state, so one instantiated graph serves every call.
+constexpr int SOLVE_CHUNK = 10;
+
+meg_status build_solve_graph(meg_solve_s* h) {
+    cudaGraph_t graph = nullptr;
+    CU(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    meg_status st = MEG_OK;
+    if (e == cudaSuccess) {
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const int kind = h->desc.kind;
+            const GroupLaunch g = solo_launch(h);
+            for (int i = 0; i < SOLVE_CHUNK && st == MEG_OK; ++i)
+                st = enqueue_iteration(g, kind == MEG_DENSE_QUAD || kind == MEG_LINEAR, kind == MEG_CSR_QUAD,
+                                       kind == MEG_MEAS_STOCH, h->q);
+            cudaError_t le = cudaSuccess;
+            if (st == MEG_OK) le = launch_objective(g, h->d_f);
+            if (st == MEG_OK && le == cudaSuccess) le = launch_solve_check(h->sm, h->d_f, cond, h->stream);
+            cudaGraph_t out = nullptr;
+            e = cudaStreamEndCapture(h->stream, &out);
+            if (e == cudaSuccess) e = le;
+        }
+    }
+    if (e == cudaSuccess && st == MEG_OK) e = cudaGraphInstantiate(&h->solve_gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (st != MEG_OK) return st;
+    if (e != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("meg_solve graph: ") + cudaGetErrorString(e));
+    return MEG_OK;
+}
+}  // namespace
+
 meg_status meg_solve(meg_handle h, double tol, int max_iters, int* iters_out) {
     meg_status st = ready(h, "meg_solve");
     if (st != MEG_OK) return st;
     if (iters_out) *iters_out = 0;
+    if (h->in_group) return fail(MEG_ERR_STATE, "meg_solve: solve belongs to a group");
+    if (!(tol > 0.0) || max_iters < 0) return fail(MEG_ERR_INVALID_ARG, "meg_solve: need tol > 0, max_iters >= 0");
+    if ((st = check_device_status(h)) != MEG_OK) return st;
     double f1 = 0.0;
-    if ((st = meg_objective(h, &f1)) != MEG_OK) return st;
+    CU(cudaMemcpyAsync(&f1, h->sm + SM_F1, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (!std::isfinite(f1))
+        return fail(MEG_ERR_STATE, "meg_solve: f(X_1) unknown (the objective was set after the first step)");
     const double denom = f1 - h->fstar;
-    int done = 0;
-    while (done < max_iters) {
-        int chunk = std::min(10, max_iters - done);
-        if ((st = meg_step(h, chunk)) != MEG_OK) return st;
-        done += chunk;
+    if (!(denom > 0.0))
+        return fail(MEG_ERR_INVALID_ARG, "meg_solve: f* must lie below f(X_1); give it with meg_set_fstar");
+    const int full = max_iters / SOLVE_CHUNK, rem = max_iters % SOLVE_CHUNK;
+    double par[6] = {tol, h->fstar, (double)full, 0.0, 0.0, 0.0};   // SM_SOLVE_TOL .. SM_SOLVE_F
+    int done_iters = 0;
+    bool converged = false;
+    if (full > 0) {
+        if (!h->solve_gexec && (st = build_solve_graph(h)) != MEG_OK) return st;
+        CU(cudaMemcpyAsync(h->sm + SM_SOLVE_TOL, par, sizeof(par), cudaMemcpyHostToDevice, h->stream));
+        CU(cudaGraphLaunch(h->solve_gexec, h->stream));
+        CU(cudaMemcpyAsync(par, h->sm + SM_SOLVE_TOL, sizeof(par), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        done_iters = SOLVE_CHUNK * (int)par[3];
+        converged = par[4] != 0.0;
+        if (iters_out) *iters_out = done_iters;
+        if ((st = check_device_status(h)) != MEG_OK) return st;
+        if (!std::isfinite(par[5])) {
+            h->failed = true;
+            return fail(MEG_ERR_NUMERIC, "meg_solve: the objective is not finite");
+        }
+    }
+    if (!converged && rem > 0) {
+        if ((st = meg_step(h, rem)) != MEG_OK) return st;
+        done_iters += rem;
+        if (iters_out) *iters_out = done_iters;
         double f = 0.0;
         if ((st = meg_objective(h, &f)) != MEG_OK) return st;
-        if (iters_out) *iters_out = done;
-        if (!(denom > 0.0) || (f - h->fstar) <= tol * denom) return MEG_OK;
+        converged = (f - h->fstar) <= tol * denom;
     }
+    if (converged) return MEG_OK;
     return fail(MEG_ERR_NOT_CONVERGED, "meg_solve: max_iters reached");
 }
 
@@ -692,6 +814,7 @@ meg_status meg_get_ritz(meg_handle h, double* sigma, int* t) {
 
 meg_status meg_get_iterate(meg_handle h, double* V, double* mu, double* s) {
     if (!h) return fail(MEG_ERR_INVALID_ARG, "meg_get_iterate: null handle");
+    if (h->failed) return fail(MEG_ERR_STATE, "meg_get_iterate: the solve failed earlier on the device");
     if (!h->has_x) return fail(MEG_ERR_STATE, "meg_get_iterate: X_1 not set");
     if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
     const int n = h->n, r = h->r;
@@ -717,6 +840,7 @@ int64_t meg_state_size(meg_handle h) {
 
 meg_status meg_get_state(meg_handle h, void* buf, int64_t bytes) {
     if (!h || !buf) return fail(MEG_ERR_INVALID_ARG, "meg_get_state: null argument");
+    if (h->failed) return fail(MEG_ERR_STATE, "meg_get_state: the solve failed earlier on the device");
     if (bytes < meg_state_size(h)) return fail(MEG_ERR_INVALID_ARG, "meg_get_state: buffer too small");
     if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
     int64_t* hdr = (int64_t*)buf;
@@ -736,8 +860,14 @@ meg_status meg_set_state(meg_handle h, const void* buf, int64_t bytes) {
     if (!h || !buf) return fail(MEG_ERR_INVALID_ARG, "meg_set_state: null argument");
     if (bytes < meg_state_size(h)) return fail(MEG_ERR_INVALID_ARG, "meg_set_state: buffer too small");
     const int64_t* hdr = (const int64_t*)buf;
+    if (h->failed) return fail(MEG_ERR_STATE, "meg_set_state: the solve failed earlier on the device");
     if (hdr[0] != STATE_MAGIC || hdr[1] != h->n || hdr[2] != h->r || hdr[3] != h->k || hdr[4] != h->prec)
         return fail(MEG_ERR_INVALID_ARG, "meg_set_state: state of a different solve shape or precision");
+    // the small state carries constants of the objective (Tr D, ||D||_F^2, shift
+    // bounds) and of the product path: a solve with an objective accepts only a
+    // state saved under the same objective kind and dense-product path
+    if (h->has_obj && (hdr[5] != h->desc.kind || hdr[7] != h->desc.tc))
+        return fail(MEG_ERR_INVALID_ARG, "meg_set_state: state saved under another objective kind or product path");
     if (meg_status js = join_group_stream(h); js != MEG_OK) return js;
     const char* p = (const char*)buf + 8 * STATE_HDR;
     CU(cudaMemcpyAsync(h->sm, p, 8 * SM_TOTAL, cudaMemcpyHostToDevice, h->stream));
@@ -755,6 +885,7 @@ meg_status meg_destroy(meg_handle h) {
     cudaStreamSynchronize(h->stream);
     if (h->in_group) cudaStreamSynchronize(h->group_stream);
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->solve_gexec) cudaGraphExecDestroy(h->solve_gexec);
     void* bufs[] = {h->V, h->Vn, h->W, h->Wp, h->Z, h->Y, h->Ys, h->Wsp, h->part, h->ctr,
                     h->sm, h->meas, h->bidx, h->d_f, h->d_desc};
     for (void* b : bufs)
@@ -785,6 +916,7 @@ meg_status group_create_impl(const meg_handle* solves, int count, void* stream, 
     for (int i = 0; i < count; ++i) {
         meg_solve_s* h = solves[i];
         if (!h || !h->has_obj || (!warm && !h->has_x)) return fail(MEG_ERR_STATE, "meg_group_create: solve not ready");
+        if (h->failed) return fail(MEG_ERR_STATE, "meg_group_create: a solve failed earlier on the device");
         if (h->in_group) return fail(MEG_ERR_STATE, "meg_group_create: solve already in a group");
         if (h->prec != prec || h->q != q)
             return fail(MEG_ERR_INVALID_ARG, "meg_group_create: solves must share precision and q");
@@ -917,6 +1049,7 @@ meg_status meg_warm_start_many(const meg_handle* solves, int count, int products
         if (!h) return fail(MEG_ERR_INVALID_ARG, "meg_warm_start_many: null handle");
         if (!h->has_obj) return fail(MEG_ERR_STATE, "meg_warm_start_many: objective not set");
         if (h->in_group) return fail(MEG_ERR_STATE, "meg_warm_start_many: solve belongs to a group");
+        if (h->failed) return fail(MEG_ERR_STATE, "meg_warm_start_many: a solve failed earlier on the device");
     }
     // random start block, as meg_warm_start draws it
     for (int i = 0; i < count; ++i) {
@@ -950,6 +1083,12 @@ meg_status meg_warm_start_many(const meg_handle* solves, int count, int products
         h->has_x = true;
         if ((st = check_device_status(h)) != MEG_OK) return st;
         if ((st = refresh_bounds(h)) != MEG_OK) return st;
+        if (f1) {
+            CU(cudaMemcpyAsync(h->sm + SM_F1, f1 + i, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            CU(cudaStreamSynchronize(h->stream));
+        } else if ((st = record_f1(h)) != MEG_OK) {
+            return st;
+        }
     }
     return MEG_OK;
 }

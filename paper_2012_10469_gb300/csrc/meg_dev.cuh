@@ -16,6 +16,7 @@
 
 #define MEG_KMAX 32
 #define MEG_RMAX 30
+#define MEG_NMAX (1 << 28)      // largest n of a solve (sizes stay within int arithmetic)
 #define MEG_LDK 33              // leading dimension of k x k matrices in shared memory
 
 // ---------------------------------------------------------------------------
@@ -42,6 +43,13 @@ enum SmallSlot : int {
     SM_RESID_BOUND,    // MEAS: spectral estimate of the minibatch gradient (see k_meas_batch)
     SM_ETA,            // eta
     SM_JSWEEPS,        // Jacobi sweeps of the last Rayleigh-Ritz step (diagnostic)
+    SM_F1,             // f(X_1), the denominator of meg_solve's relative gap (NaN = unknown)
+    SM_SOLVE_TOL,      // meg_solve: gap tolerance
+    SM_SOLVE_FSTAR,    //   known optimal value f*
+    SM_SOLVE_LIMIT,    //   chunks of iterations the device loop may run
+    SM_SOLVE_CHUNKS,   //   chunks run so far
+    SM_SOLVE_DONE,     //   1 once the gap test held
+    SM_SOLVE_F,        //   f(X_t) at the last check
     SM_MU = 32,        // [32] mu of X_t
     SM_DCOEF = 64,     // [32] coefficients of V diag(.) V^T in M_t
     SM_SIGMA = 96,     // [32] Ritz values of the last Rayleigh-Ritz, unshifted
@@ -314,4 +322,7 @@ cudaError_t launch_combine(const GroupLaunch& g, int phase);
 cudaError_t launch_orthonormalise(const GroupLaunch& g, int phase);
 cudaError_t launch_chain_kernel(const GroupLaunch& g, int which, int phase);
 cudaError_t launch_objective(const GroupLaunch& g, double* out_f);
+// meg_solve's stopping test after a chunk of iterations (one solve); ends the
+// enclosing conditional (while) graph node through `cond`
+cudaError_t launch_solve_check(double* sm, const double* f, cudaGraphConditionalHandle cond, cudaStream_t st);
 cudaError_t init_kernel_attributes();

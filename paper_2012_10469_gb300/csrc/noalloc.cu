@@ -14,7 +14,11 @@
 // loads the library holds it until the process exits.  In host code its
 // name is only a stand-in, so the device address is looked up with
 // cudaGetSymbolAddress once per device (on the first call made on that
-// device, with the device current) and cached.
+// device, with the device current) and cached together with the CUDA
+// context it belongs to.  A device reset or a new primary context reloads
+// the module, which may move the array: a call that finds another current
+// context than the cached one looks the address up again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -124,6 +128,23 @@ k_objective_noalloc(const double* __restrict__ V, MuArg coef, int n, int r, cons
 
 std::mutex g_na_mu;
 void* g_na_ptr[128] = {nullptr};
+CUcontext g_na_ctx[128] = {nullptr};
+
+// the calling thread's current context (driver entry point, looked up once)
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+CUcontext current_context() {
+    static PfnCtxGetCurrent fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return (PfnCtxGetCurrent)p;
+    }();
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
 
 }  // namespace
 
@@ -148,11 +169,13 @@ extern "C" meg_status meg_objective_dense_noalloc(const double* V, const double*
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_ptr[dev]) {
+        CUcontext ctx = g_na_ptr[dev] ? current_context() : nullptr;
+        if (!g_na_ptr[dev] || ctx != g_na_ctx[dev]) {
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess) return na_fail(MEG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
             g_na_ptr[dev] = p;
+            g_na_ctx[dev] = current_context();   // the lookup made the device's context current
         }
         scratch = g_na_ptr[dev];
     }
