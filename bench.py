@@ -135,7 +135,7 @@ def autotune_pq(prob, device, stream):
     from paper_2012_10469_gb300 import binding as B
     global P, Q
     bits = torch.from_numpy(np.ascontiguousarray(prob.bits().view(np.int16))).to(device)
-    p, q, err, ok = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, prob.U, prob.w, dense=bits,
+    p, q, err, ok, _eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, prob.U, prob.w, dense=bits,
                                    seed=SEED0, stream=stream, **AUTOTUNE)
     P, Q = p, q
     return {"p": p, "q": q, "pilot_distance": err, "met_target": ok, **{k: v for k, v in AUTOTUNE.items()}}

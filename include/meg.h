@@ -63,6 +63,17 @@ enum {
                             product on tcgen05 tensor cores (fp32 accumulate) */
 };
 
+/* Eigensolver of the top-r eigenpairs of M_t (meg_options.eigensolver),
+ * both warm-started from the previous iteration's Ritz vectors (Section 3:
+ * block subspace iteration, or the faster Lanczos-type methods it names). */
+enum {
+    MEG_EIG_SUBSPACE = 0,      /* q products, each followed by CholeskyQR; the
+                                  Rayleigh-Ritz step on the last block */
+    MEG_EIG_BLOCK_KRYLOV = 1   /* q = 2 products: Rayleigh-Ritz on the block
+                                  Krylov space span [W, (M_t - cI) W] (2k <= 32
+                                  columns); float-storage precisions only */
+};
+
 /* Objective kinds (meg_objective_desc.kind). */
 enum {
     MEG_DENSE_QUAD = 0,  /* f = 1/2 ||X - M||_F^2,  grad f = X - M            */
@@ -88,6 +99,9 @@ enum {
  *   max_iters, tol : defaults for meg_solve.
  *   seed       : seeds the extra subspace vectors and the minibatch stream.
  *   stream     : cudaStream_t (NULL = default stream).
+ *   eigensolver: MEG_EIG_SUBSPACE (0, the default of a zeroed struct) or
+ *                MEG_EIG_BLOCK_KRYLOV (needs q = 2, 2 (r + p) <= 32 and
+ *                MEG_FP32 or MEG_MIXED_BF16; MEG_ERR_INVALID_ARG otherwise).
  */
 typedef struct {
     int n, r, p, q;
@@ -98,6 +112,7 @@ typedef struct {
     double tol;
     uint64_t seed;
     void* stream;
+    int eigensolver;
 } meg_options;
 
 /*
@@ -396,7 +411,12 @@ meg_status meg_objective_dense_noalloc(const double* V, const double* mu, double
  * (relative Frobenius distance) is returned in *p_out, *q_out, its
  * distance in *err_out (may be NULL).  The choice depends on results, not
  * timings.  If none qualifies the most accurate candidate is returned with
- * MEG_ERR_NOT_CONVERGED.  The paper has no counterpart.
+ * MEG_ERR_NOT_CONVERGED.  With ao->krylov set (float storage), the block
+ * Krylov eigensolver is a candidate too: at q = 2 it is tried after
+ * subspace iteration and before q = 3 (two products and a 2k x 2k
+ * Rayleigh-Ritz step; p with 2 (r + p) <= 32);
+ * *eig_out (may be NULL) receives the chosen eigensolver.  The reference
+ * solve always uses subspace iteration.  The paper has no counterpart.
  */
 typedef struct {
     int q_max;            /* largest q tried, 1..7 (the reference uses q_max + 2, at most 8) */
@@ -405,11 +425,12 @@ typedef struct {
     int pilot_iters;      /* iterations of each pilot run */
     int horizon;          /* iterations the solve will run */
     double tol_x;         /* target relative Frobenius error of X_t at the horizon */
+    int krylov;           /* 1: also try MEG_EIG_BLOCK_KRYLOV (q = 2) */
 } meg_autotune_options;
 
 meg_status meg_autotune(const meg_options* base, const meg_objective_desc* obj, const double* V0,
                         const double* lam0, const meg_autotune_options* ao, int* p_out, int* q_out,
-                        double* err_out);
+                        double* err_out, int* eig_out);
 
 /* Device-memory footprint in bytes of one solve (library-owned buffers,
  * not the caller's objective data), for admission control. */

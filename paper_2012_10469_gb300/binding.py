@@ -20,20 +20,21 @@ MEG_OK, MEG_ERR_INVALID_ARG, MEG_ERR_OOM, MEG_ERR_CUDA, MEG_ERR_NUMERIC, MEG_ERR
     MEG_ERR_TIMEOUT, MEG_ERR_STATE = range(8)
 MEG_FP64, MEG_FP32, MEG_MIXED_BF16 = 0, 1, 2
 MEG_DENSE_QUAD, MEG_CSR_QUAD, MEG_MEAS_STOCH, MEG_LINEAR = 0, 1, 2, 3
+MEG_EIG_SUBSPACE, MEG_EIG_BLOCK_KRYLOV = 0, 1
 PRECISION = {"fp64": MEG_FP64, "fp32": MEG_FP32, "bf16": MEG_MIXED_BF16}
 # slots of the small state (csrc/meg_dev.cuh, SmallSlot)
 SM_T, SM_EPS, SM_S, SM_LOGS, SM_SHIFT, SM_C0, SM_ALPHA, SM_GNORM, SM_FEST, SM_CERT, SM_HOLDS, \
     SM_FIRST_HOLD, SM_STATUS, SM_TRD, SM_FROD2, SM_LAST_T, SM_LSE, SM_RSS, SM_RESID_BOUND, SM_ETA, \
     SM_JSWEEPS, SM_F1 = range(22)
 SM_MU, SM_DCOEF, SM_SIGMA = 32, 64, 96
-SM_TOTAL = 128 + 7 * 1024
+SM_TOTAL = 128 + 13 * 1024
 
 
 class meg_options(C.Structure):
     _fields_ = [("n", C.c_int), ("r", C.c_int), ("p", C.c_int), ("q", C.c_int),
                 ("precision", C.c_int), ("eta", C.c_double), ("eps_a", C.c_double),
                 ("eps_c", C.c_double), ("eps_pow", C.c_double), ("max_iters", C.c_int),
-                ("tol", C.c_double), ("seed", C.c_uint64), ("stream", C.c_void_p)]
+                ("tol", C.c_double), ("seed", C.c_uint64), ("stream", C.c_void_p), ("eigensolver", C.c_int)]
 
 
 class meg_objective_desc(C.Structure):
@@ -44,7 +45,7 @@ class meg_objective_desc(C.Structure):
 
 class meg_autotune_options(C.Structure):
     _fields_ = [("q_max", C.c_int), ("p_cand", C.c_void_p), ("n_p", C.c_int), ("pilot_iters", C.c_int),
-                ("horizon", C.c_int), ("tol_x", C.c_double)]
+                ("horizon", C.c_int), ("tol_x", C.c_double), ("krylov", C.c_int)]
 
 
 class meg_server_options(C.Structure):
@@ -121,7 +122,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                                   C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
         "meg_group_launch": (C.c_int, [H, C.c_int]),
         "meg_autotune": (C.c_int, [_P(meg_options), _P(meg_objective_desc), _P(C.c_double), _P(C.c_double),
-                                   _P(meg_autotune_options), _P(C.c_int), _P(C.c_int), _P(C.c_double)]),
+                                   _P(meg_autotune_options), _P(C.c_int), _P(C.c_int), _P(C.c_double),
+                                   _P(C.c_int)]),
         "meg_warm_start_many": (C.c_int, [_P(H), C.c_int, C.c_int, C.c_void_p, _P(C.c_double)]),
         "meg_group_objective": (C.c_int, [H, _P(C.c_double)]),
         "meg_server_create": (C.c_int, [_P(meg_server_options), _P(H)]),
@@ -180,14 +182,14 @@ class Solve:
 
     def __init__(self, n: int, r: int, p: int = 4, q: int = 2, precision: int = MEG_FP64,
                  eta: float = 1.0, eps=(0.8, 10.0, 2.0), seed: int = 1, V0=None, lam0=None,
-                 stream=None, max_iters: int = 1000, tol: float = 1e-6):
+                 stream=None, max_iters: int = 1000, tol: float = 1e-6, eigensolver: int = MEG_EIG_SUBSPACE):
         lib = load()
         self.n, self.r, self.k = n, r, r + p
         self.precision = precision
         self._keep = []
         opt = meg_options(n=n, r=r, p=p, q=q, precision=precision, eta=eta, eps_a=eps[0], eps_c=eps[1],
                           eps_pow=eps[2], max_iters=max_iters, tol=tol, seed=seed,
-                          stream=None if stream is None else int(stream))
+                          stream=None if stream is None else int(stream), eigensolver=eigensolver)
         h = C.c_void_p()
         if V0 is not None:
             V0 = np.ascontiguousarray(V0, dtype=np.float64)
@@ -330,9 +332,9 @@ class Group:
 
 def meg_autotune(n, r, precision, kind, V0, lam0, dense=None, A=None, y=None, L=0, rowptr=None, col=None,
                  val=None, eta=1.0, eps=(0.8, 10.0, 2.0), seed=1, q_max=4, p_cand=None, pilot_iters=20,
-                 horizon=500, tol_x=1e-5, stream=None):
-    """(p, q, distance to the reference, met_target) for one problem; device tensors as in
-    Solve.meg_set_objective."""
+                 horizon=500, tol_x=1e-5, stream=None, krylov=False):
+    """(p, q, distance to the reference, met_target, eigensolver) for one problem; device
+    tensors as in Solve.meg_set_objective.  krylov: also try the block Krylov eigensolver."""
     lib = load()
     opt = meg_options(n=n, r=r, p=1, q=1, precision=precision, eta=eta, eps_a=eps[0], eps_c=eps[1],
                       eps_pow=eps[2], max_iters=horizon, tol=1e-6, seed=seed,
@@ -344,15 +346,16 @@ def meg_autotune(n, r, precision, kind, V0, lam0, dense=None, A=None, y=None, L=
     if p_cand is not None:
         pc = np.ascontiguousarray(p_cand, dtype=np.int32)
     ao = meg_autotune_options(q_max=q_max, p_cand=None if pc is None else pc.ctypes.data,
-                              n_p=0 if pc is None else len(pc), pilot_iters=pilot_iters, horizon=horizon, tol_x=tol_x)
+                              n_p=0 if pc is None else len(pc), pilot_iters=pilot_iters, horizon=horizon, tol_x=tol_x,
+                              krylov=1 if krylov else 0)
     V0 = np.ascontiguousarray(V0, dtype=np.float64)
     lam0 = np.ascontiguousarray(lam0, dtype=np.float64)
-    p, q, e = C.c_int(), C.c_int(), C.c_double()
+    p, q, e, eig = C.c_int(), C.c_int(), C.c_double(), C.c_int()
     st = lib.meg_autotune(C.byref(opt), C.byref(d), _f64p(V0), _f64p(lam0), C.byref(ao), C.byref(p), C.byref(q),
-                          C.byref(e))
+                          C.byref(e), C.byref(eig))
     if st not in (MEG_OK, MEG_ERR_NOT_CONVERGED):
         _check(st, "meg_autotune")
-    return p.value, q.value, e.value, st == MEG_OK
+    return p.value, q.value, e.value, st == MEG_OK, eig.value
 
 
 def meg_warm_start_many(solves, products: int = 40, stream=None) -> np.ndarray:
@@ -382,13 +385,14 @@ class Server:
                           precision: int = MEG_FP64, eta: float = 1.0, eps=(0.8, 10.0, 2.0), seed: int = 1,
                           y: Optional[np.ndarray] = None, L: int = 0, warm_start_products: int = 40,
                           V0=None, lam0=None, fstar: float = float("nan"), tol: float = 1e-6,
-                          max_iters: int = 5000) -> int:
+                          max_iters: int = 5000, eigensolver: int = MEG_EIG_SUBSPACE) -> int:
         """data: host array (dense n x n, or A m x n) in the precision's storage
         type (float64, float32, or uint16 bfloat16 bits); y: float64 (m)."""
         data = np.ascontiguousarray(data)
         keep = [data]
         opt = meg_options(n=n, r=r, p=p, q=q, precision=precision, eta=eta, eps_a=eps[0], eps_c=eps[1],
-                          eps_pow=eps[2], max_iters=max_iters, tol=tol, seed=seed, stream=None)
+                          eps_pow=eps[2], max_iters=max_iters, tol=tol, seed=seed, stream=None,
+                          eigensolver=eigensolver)
         outV = np.zeros((n, r), dtype=np.float64)
         outmu = np.zeros(r, dtype=np.float64)
         outs = np.zeros(1, dtype=np.float64)

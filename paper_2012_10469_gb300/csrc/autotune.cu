@@ -1,5 +1,6 @@
-// meg_autotune: choose the oversampling p and the products per iteration q
-// of the subspace iteration (Section 3) for one problem.
+// meg_autotune: choose the oversampling p, the products per iteration q and
+// (optionally) the eigensolver -- subspace iteration or block Krylov, both
+// of Section 3 -- for one problem.
 //
 // The subspace iteration is warm-started from the previous iteration's Ritz
 // vectors, so each MEG iteration only has to follow the rotation of the
@@ -117,7 +118,7 @@ meg_status run_pilot(const meg_options& o, const meg_objective_desc* obj, const 
 
 extern "C" meg_status meg_autotune(const meg_options* base, const meg_objective_desc* obj, const double* V0,
                                    const double* lam0, const meg_autotune_options* ao, int* p_out, int* q_out,
-                                   double* err_out) {
+                                   double* err_out, int* eig_out) {
     if (!base || !obj || !V0 || !lam0 || !ao || !p_out || !q_out) return afail(MEG_ERR_INVALID_ARG, "null argument");
     const int n = base->n, r = base->r;
     const int kmax = std::min(32, n);
@@ -133,31 +134,42 @@ extern "C" meg_status meg_autotune(const meg_options* base, const meg_objective_
     meg_options ro = *base;
     ro.p = std::min(kmax - r, std::max(ps.back(), 2 * ps.back()));
     ro.q = std::min(8, ao->q_max + 2);
+    ro.eigensolver = MEG_EIG_SUBSPACE;
     Iter ref;
     meg_status st = run_pilot(ro, obj, V0, lam0, ao->pilot_iters, &ref);
     if (st != MEG_OK) return st;
     const double accept = ao->tol_x * std::sqrt((double)ao->pilot_iters / (double)ao->horizon);
     double best_err = INFINITY;
-    int best_p = ps.back(), best_q = ao->q_max;
+    int best_p = ps.back(), best_q = ao->q_max, best_eig = MEG_EIG_SUBSPACE;
+    // with two products the block Krylov eigensolver (Rayleigh-Ritz on
+    // [W, A W]) costs a little more than subspace iteration (its 2k x 2k
+    // island) and less than a third product: it is tried after subspace
+    // iteration at q = 2 and before q = 3
+    const bool kry = ao->krylov && base->precision != MEG_FP64;
     for (int q = 1; q <= ao->q_max; ++q)
-        for (int p : ps) {
-            meg_options o = *base;
-            o.p = p;
-            o.q = q;
-            Iter it;
-            if ((st = run_pilot(o, obj, V0, lam0, ao->pilot_iters, &it)) != MEG_OK) return st;
-            const double e = rel_dist(it, ref);
-            if (e < best_err) { best_err = e; best_p = p; best_q = q; }
-            if (e <= accept) {
-                *p_out = p;
-                *q_out = q;
-                if (err_out) *err_out = e;
-                return MEG_OK;
+        for (int eig = MEG_EIG_SUBSPACE; eig <= ((kry && q == 2) ? MEG_EIG_BLOCK_KRYLOV : MEG_EIG_SUBSPACE); ++eig)
+            for (int p : ps) {
+                if (eig == MEG_EIG_BLOCK_KRYLOV && 2 * (r + p) > 32) continue;
+                meg_options o = *base;
+                o.p = p;
+                o.q = q;
+                o.eigensolver = eig;
+                Iter it;
+                if ((st = run_pilot(o, obj, V0, lam0, ao->pilot_iters, &it)) != MEG_OK) return st;
+                const double e = rel_dist(it, ref);
+                if (e < best_err) { best_err = e; best_p = p; best_q = q; best_eig = eig; }
+                if (e <= accept) {
+                    *p_out = p;
+                    *q_out = q;
+                    if (err_out) *err_out = e;
+                    if (eig_out) *eig_out = eig;
+                    return MEG_OK;
+                }
             }
-        }
     // nothing met the target: the most accurate candidate, and say so
     *p_out = best_p;
     *q_out = best_q;
     if (err_out) *err_out = best_err;
+    if (eig_out) *eig_out = best_eig;
     return afail(MEG_ERR_NOT_CONVERGED, "no candidate met the target; the most accurate one is returned");
 }

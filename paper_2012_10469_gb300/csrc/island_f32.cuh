@@ -191,6 +191,107 @@ __device__ inline int jacobi_warp_f32(float** pA, float* B, float* Q, float* pr,
 }
 
 // ---------------------------------------------------------------------------
+// The same Jacobi sweeps (round-robin ordering, the same 2 x 2 Schur steps,
+// the same stopping rule) with the whole block updating the matrix: for the
+// 2k x 2k pencils of the block Krylov Rayleigh-Ritz step, where one warp's
+// k-cubed work per sweep would dominate the iteration.  Each round computes
+// the k/2 rotations, then every thread updates its entries of A (into B) and
+// of Q (through registers).  Requires blockDim.x * 4 >= k * k.
+__device__ inline int jacobi_block_f32(float** pA, float* B, float* Q, float* pr, int k, int max_sweeps,
+                                       float tol) {
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    const int kk = (k + 1) & ~1;
+    int* partner = (int*)(pr + 2 * MEG_KMAX);
+    float* cs = pr;
+    float* sg = pr + MEG_KMAX;
+    __shared__ float red[2][32];
+    __shared__ int s_stop;
+    __shared__ float s_prev;
+    // the (up to four) entries this thread owns, fixed for the whole run
+    int ei[4], ej[4];
+    bool ev[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const int e = tid + m * nt;
+        ev[m] = e < k * k;
+        ei[m] = ev[m] ? e / k : 0;
+        ej[m] = ev[m] ? e - (e / k) * k : 0;
+    }
+    float* A = *pA;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (ev[m]) Q[ei[m] * MEG_LDK + ej[m]] = (ei[m] == ej[m]) ? 1.f : 0.f;
+    if (tid == 0) s_prev = 3.4e38f;
+    __syncthreads();
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        float off = 0.f, dia = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (ev[m]) {
+                const float v = A[ei[m] * MEG_LDK + ej[m]];
+                if (ei[m] == ej[m]) dia += v * v; else off += v * v;
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            dia += __shfl_xor_sync(0xffffffffu, dia, o);
+        }
+        if (lane == 0) { red[0][wid] = off; red[1][wid] = dia; }
+        __syncthreads();
+        if (tid == 0) {
+            float o2 = 0.f, d2 = 0.f;
+            for (int w = 0; w < (nt + 31) / 32; ++w) { o2 += red[0][w]; d2 += red[1][w]; }
+            s_stop = (o2 <= tol * tol * d2 || o2 >= s_prev);
+            s_prev = o2;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        for (int round = 0; round < kk - 1; ++round) {
+            if (tid < kk / 2) {
+                const int a = tid == 0 ? 0 : 1 + (tid - 1 + round) % (kk - 1);
+                const int bpos = kk - 1 - tid;
+                const int b = bpos == 0 ? 0 : 1 + (bpos - 1 + round) % (kk - 1);
+                const int p = min(a, b), q = max(a, b);
+                float c = 1.f, sn = 0.f;
+                if (q < k) {
+                    const float apq = A[p * MEG_LDK + q];
+                    if (apq != 0.f) {
+                        const float th = (A[q * MEG_LDK + q] - A[p * MEG_LDK + p]) / (2.f * apq);
+                        const float t = (th >= 0.f ? 1.f : -1.f) / (fabsf(th) + sqrtf(1.f + th * th));
+                        c = rsqrtf(1.f + t * t);
+                        sn = t * c;
+                    }
+                }
+                if (p < k) { partner[p] = q < k ? q : p; cs[p] = c; sg[p] = q < k ? -sn : 0.f; }
+                if (q < k) { partner[q] = p; cs[q] = c; sg[q] = sn; }
+            }
+            __syncthreads();
+            float qn[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                qn[m] = 0.f;
+                if (ev[m]) {
+                    const int i = ei[m], j = ej[m], pi = partner[i], pj = partner[j];
+                    const float ci = cs[i], si = sg[i], cj = cs[j], sj = sg[j];
+                    B[i * MEG_LDK + j] = ci * (cj * A[i * MEG_LDK + j] + sj * A[i * MEG_LDK + pj]) +
+                                         si * (cj * A[pi * MEG_LDK + j] + sj * A[pi * MEG_LDK + pj]);
+                    qn[m] = cj * Q[i * MEG_LDK + j] + sj * Q[i * MEG_LDK + pj];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (ev[m]) Q[ei[m] * MEG_LDK + ej[m]] = qn[m];
+            float* t = A; A = B; B = t;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) *pA = A;
+    __syncthreads();
+    return sweep;
+}
+
+// ---------------------------------------------------------------------------
 // Double-word helpers for exact products of float32 operands with a
 // float64 matrix held as hi/lo floats.
 __device__ __forceinline__ void dw_split(double v, float& hi, float& lo) {

@@ -275,11 +275,14 @@ __global__ void k_begin(const SolveDev* sds, int ns) {
 //        Lowdin re-orthonormalisation, map back x = (I - E/2 + 3 E^2/8) q
 // Scratch: F (4 float matrices), the double regions C, JB, Bm (G), H.
 // Writes sigma, mu, s, t, certificate, objective estimate, QV, M1 like the
-// float64 island.
+// float64 island.  kk is the dimension of the pencil: the block size k for
+// subspace iteration, 2k for the block Krylov space [W0 W1], whose tail
+// (krylov = true) writes the next block's coordinates QW (kk x k: the top-k
+// Ritz vectors, the first r of them as in QV) instead of a CholeskyQR factor.
 __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, const double* P, double* G,
                             double* H, double* C, double* JB, float* F, double* wv, double* pr, double* pdg,
-                            double* sig, double* mun, double shift) {
-    const int tid = threadIdx.x, nt = blockDim.x, k = s.k, r = s.r, n = s.n;
+                            double* sig, double* mun, double shift, int kk, bool krylov) {
+    const int tid = threadIdx.x, nt = blockDim.x, k = kk, r = s.r, n = s.n;
     constexpr int FM = 32 * MEG_LDK;        // floats per float matrix
     float* F0 = F;
     float* F1 = F + FM;
@@ -316,7 +319,9 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
     __shared__ float* jA;
     if (tid == 0) jA = F1;
     __syncthreads();
-    const int nsw = jacobi_warp_f32(&jA, F3, F2, (float*)pr, k, 4, 1e-5f);   // Q in F2; F1/F3 free
+    // the 2k x 2k pencils of the block Krylov step are swept by the whole block
+    const int nsw = k > 16 ? jacobi_block_f32(&jA, F3, F2, (float*)pr, k, 4, 1e-5f)
+                           : jacobi_warp_f32(&jA, F3, F2, (float*)pr, k, 4, 1e-5f);   // Q in F2; F1/F3 free
     if (tid == 0) smw[SM_JSWEEPS] = nsw;
     // 3. Ht as hi/lo floats; Tq = Ht Q exactly (Dot2), as hi/lo floats in F1/F3
     for (int e = tid; e < k * k; e += nt) {
@@ -435,11 +440,20 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
         pdg[tid] = acc;
     }
     // 9. scalars: exp-map (Definition 2), certificate (Lemma 2), objective estimate.
-    //    The transcendental functions run side by side on different lanes.
+    //    The transcendental functions run side by side on different lanes; the
+    //    state they read is loaded at once (one lane per slot), and float64
+    //    operations are kept few: GB300 issues a warp's float64 instruction at
+    //    about 1/60 of the float32 rate.
     if (tid < 32) {
         const int lane = tid;
-        const double t = smw[SM_T];
-        const double eps = smw[SM_EPS];
+        const int slot = lane == 0 ? SM_T : lane == 1 ? SM_EPS : lane == 2 ? SM_FIRST_HOLD : lane == 3 ? SM_TRD
+                                                                                          : SM_FROD2;
+        const double ld = lane < 5 ? smw[slot] : 0.0;
+        const double t = __shfl_sync(0xffffffffu, ld, 0);
+        const double eps = __shfl_sync(0xffffffffu, ld, 1);
+        const double first_hold = __shfl_sync(0xffffffffu, ld, 2);
+        const double trd = __shfl_sync(0xffffffffu, ld, 3);
+        const double frod2 = __shfl_sync(0xffffffffu, ld, 4);
         double m = (lane <= r && lane < k) ? sig[lane] : -1e300;
         for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
         const double ex = (lane <= r && lane < k) ? exp(sig[lane] - m) : 0.0;
@@ -468,7 +482,8 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
             }
         } else {
             const double s_new = eps / (double)(n - r);
-            const double mu = lane < r ? (1.0 - eps) * exp(sig[lane] - lse_r) : 0.0;
+            // mu_i = (1 - eps) e^{sigma_i - m} / a_r: the exponentials already formed
+            const double mu = lane < r ? (1.0 - eps) * ex / a_r : 0.0;
             double xd = lane < r ? (mu - s_new) * pdg[lane] : 0.0, x2 = mu * mu;
             for (int o = 16; o > 0; o >>= 1) {
                 xd += __shfl_xor_sync(0xffffffffu, xd, o);
@@ -481,13 +496,13 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
                 smw[SM_LSE] = lse_r;
                 smw[SM_CERT] = cert;
                 smw[SM_HOLDS] = holds;
-                if (holds && smw[SM_FIRST_HOLD] == 0.0) smw[SM_FIRST_HOLD] = t;
+                if (holds && first_hold == 0.0) smw[SM_FIRST_HOLD] = t;
                 smw[SM_LAST_T] = t;
                 if (s.kind == MEG_DENSE_QUAD || s.kind == MEG_LINEAR) {
-                    xd += s_new * smw[SM_TRD];
+                    xd += s_new * trd;
                     x2 += (double)(n - r) * s_new * s_new;
                     if (s.kind == MEG_DENSE_QUAD) {
-                        const double f = 0.5 * x2 - xd + 0.5 * smw[SM_FROD2];
+                        const double f = 0.5 * x2 - xd + 0.5 * frod2;
                         smw[SM_FEST] = f;
                         smw[SM_GNORM] = 1.25 * sqrt(fmax(2.0 * f, 0.0));
                     } else {
@@ -504,6 +519,27 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
         }
     }
     __syncthreads();
+    if (krylov) {
+        // 10'. next block [W0 W1] QW: the top k = s.k Ritz vectors, columns r.. as
+        //      the sorted Jacobi vectors mapped back, x = (I - E/2 + 3 E^2/8) q
+        //      (orthonormal to float accuracy; the next Rayleigh-Ritz step uses
+        //      the exact Gram of the stored block)
+        const int kb = s.k;
+        for (int e = tid; e < k * kb; e += nt) {
+            const int a = e / kb, i = e % kb;
+            Bh[a * MEG_LDK + i] = i < r ? 0.f : F2[a * MEG_LDK + perm[i]];
+        }
+        __syncthreads();
+        mm_f32(F0, false, Bh, Bl, k, k, kb);                   // E q
+        mm_f32(F0, false, Bl, F1, k, k, kb);                   // E^2 q
+        for (int e = tid; e < k * kb; e += nt) {
+            const int a = e / kb, i = e % kb;
+            smw[SM_QW + a * 32 + i] = i < r ? smw[SM_QV + a * 32 + i]
+                                            : (double)Bh[a * MEG_LDK + i] - 0.5 * (double)Bl[a * MEG_LDK + i] +
+                                                  0.375 * (double)F1[a * MEG_LDK + i];
+        }
+        return;
+    }
     // 10. next block W = Z Q M (Ritz-ordered), M^T (Q^T S1 Q) M = I.  With q > 1
     //     the next product's CholeskyQR pass restores orthonormality before any
     //     Rayleigh-Ritz step, so a float32 factor suffices (it changes how
@@ -604,6 +640,9 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
     const double* V = s.V;
     T* Z = (T*)s.Z;
     const bool dense = (s.kind == MEG_DENSE_QUAD || s.kind == MEG_LINEAR);
+    // block Krylov, second product: Z is not needed, its row buffer holds W0
+    const bool kry2 = (phase == PH_KRY2);
+    const T* W0 = (const T*)s.Wp;
     __shared__ T sVt[ROWS_MAX * MEG_RMAX];     // this block's rows of V in storage precision
     if (!init)
         for (int e = tid; e < nr * r; e += NT) sVt[e] = (T)V[(size_t)(row0 + e / r) * r + e % r];
@@ -626,28 +665,46 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
             } else {
                 y = ((const T*)s.Y)[(size_t)i * k + j];
             }
-            z = c_al.mul(y);
-            z = c_id.fma_(w, z);
-            for (int l = 0; l < r; ++l) z = Bc[l * k + j].fma_(sVt[(idx / k) * r + l], z);
+            if (kry2) {
+                z = W0[(size_t)i * k + j];
+            } else {
+                z = c_al.mul(y);
+                z = c_id.fma_(w, z);
+                for (int l = 0; l < r; ++l) z = Bc[l * k + j].fma_(sVt[(idx / k) * r + l], z);
+            }
         }
-        Z[(size_t)i * k + j] = z;
+        if (!kry2) Z[(size_t)i * k + j] = z;
         sW[idx] = w;
         sZ[idx] = z;
         sY[idx] = y;
     }
     __syncthreads();
 
+    // Gram entries, by phase:
+    //   advance / init : Z^T Z
+    //   final          : Z^T Z, W^T Y
+    //   block Krylov 1 : W^T Y, W^T Z (k x k, for the projection on W)
+    //   block Krylov 2 : W1^T Y, W0^T Y (k x k)
     const int nsym = k * (k + 1) / 2;
-    const bool fin = (phase == PH_FINAL);
-    const int E = fin ? 2 * nsym : nsym;
+    const bool fin = (phase == PH_FINAL), kry1 = (phase == PH_KRY1);
+    const int E = (kry1 || kry2) ? nsym + k * k : fin ? 2 * nsym : nsym;
     for (int e = tid; e < E; e += NT) {
-        int m = e / nsym, i, j;
-        tri_decode(e % nsym, i, j);
+        int i, j;
+        const T* X;
+        const T* Yv;
+        if (kry1 || kry2) {
+            if (e < nsym) { tri_decode(e, i, j); X = sW; Yv = sY; }
+            else { i = (e - nsym) / k; j = (e - nsym) % k; X = kry1 ? sW : sZ; Yv = kry1 ? sZ : sY; }
+        } else if (e < nsym) {
+            tri_decode(e, i, j); X = sZ; Yv = sZ;
+        } else if (e < 2 * nsym) {
+            tri_decode(e - nsym, i, j); X = sW; Yv = sY;
+        } else {
+            i = (e - 2 * nsym) / k; j = (e - 2 * nsym) % k; X = sW; Yv = sZ;
+        }
         Acc<T> a, b;
         a.zero();
         b.zero();
-        const T* X = (m == 0) ? sZ : sW;
-        const T* Yv = (m == 0) ? sZ : sY;
         int q = 0;
         for (; q + 1 < nr; q += 2) {          // two independent chains for ILP
             a.add_prod(X[q * k + i], Yv[q * k + j]);
@@ -754,7 +811,7 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
         }
         __syncthreads();
         if (use_fast) {
-            rr_fast_f32(s, smw, S1, P, G, H, C, JB, (float*)smraw, wv, pr, pdg, sig, mun, shift);
+            rr_fast_f32(s, smw, S1, P, G, H, C, JB, (float*)smraw, wv, pr, pdg, sig, mun, shift, k, false);
             return;
         }
     }
@@ -844,6 +901,159 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
     kxk_inv_lower_T(A, C, k);             // L^{-T}
     kxk_mm(Qg, false, C, Bm, k, k, k);    // M1 = Qg L^{-T}
     store_kxk(smw + SM_M1, Bm, k, k);
+}
+
+// ==========================================================================
+// Block Krylov Rayleigh-Ritz (Section 3 names Lanczos-type methods as the
+// faster alternative to subspace iteration).  One MEG iteration makes two
+// products with A = M_t - c I: A W0 with the warm-started block W0, then
+// A W1 with W1 the orthonormalised part of Z = A W0 outside span W0; the
+// Rayleigh-Ritz step runs on the 2k-dimensional Krylov space span [W0 W1]
+// and the next block is its top-k Ritz vectors.  Float storage only.
+//
+// island after the block Krylov combines (one block per solve).
+//   PH_KRY1 (Z = A W0, entries W0^T Y, B = W0^T Z):
+//     H00 = W0^T A W0 = U0^T diag(d) U0 + (c0 - c) G0 + alpha W0^T Y (kept for
+//     the Rayleigh-Ritz step) and the projection coefficients C = G0^{-1} B
+//     (G0 = I + E0, |E0| a few float units: C = B - E0 B).  U0, G0 and W0^T Y
+//     move to their own slots (the reduction after the orth pass overwrites
+//     U, G with those of W1).  The rest of Z, Z' = Z - W0 C, is formed by the
+//     projection pass on the rows, and its Gram taken there: near convergence
+//     the columns of Z' shrink to the rounding of the stored Z, below what a
+//     Gram-space difference Z^T Z - B^T C resolves.
+//   PH_KRY2 (entries P2 = W1^T Y2, Q2 = W0^T Y2): the 2k x 2k pencil
+//     H = [H00 H01; H01^T H11], G = [G0 G01; G01^T G11] with
+//     H11 = U1^T diag(d) U1 + (c0 - c) G11 + alpha P2,
+//     H01 = U0^T diag(d) U1 + (c0 - c) G01 + alpha Q2,
+//     Rayleigh-Ritz (rr_fast_f32 on 2k), exp-map, certificate, and the next
+//     block's coordinates QW.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_island_kry(const SolveDev* sds, int ns, int phase) {
+    pdl_wait();
+    pdl_trigger();
+    const int si = blockIdx.x;
+    if (si >= ns) return;
+    const SolveDev& s = sds[si];
+    const int k = s.k, r = s.r, tid = threadIdx.x;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int FBYTES = 4 * 32 * MEG_LDK * (int)sizeof(float);
+    constexpr int FM = 32 * MEG_LDK;
+    dw* ent = (dw*)(smraw + FBYTES);
+    double* kx = (double*)(ent + RED_MAX_ENTRIES);
+    double* R0 = kx;                    // six double k x k regions
+    double* R1 = R0 + FM;
+    double* R2 = R1 + FM;
+    double* R3 = R2 + FM;
+    double* R4 = R3 + FM;
+    double* R5 = R4 + FM;
+    double* wv = R5 + FM;               // [32]
+    double* pr = wv + 32;               // [96]
+    double* pdg = pr + 96;              // [32]
+    __shared__ int flag;
+    __shared__ double dco[MEG_RMAX];
+    double* smw = s.sm;
+    const int nsym = k * (k + 1) / 2;
+    const bool kry1 = (phase == PH_KRY1);
+    const int E = kry1 ? 2 * nsym + k * k : nsym + k * k;
+    reduce_partials(s, ent, E, (dw*)smraw, FBYTES / (int)sizeof(dw));
+    if (tid < r) dco[tid] = smw[SM_DCOEF + tid];
+    const double d_id = smw[SM_C0] - smw[SM_SHIFT], alpha = smw[SM_ALPHA], shift = smw[SM_SHIFT];
+    __syncthreads();
+    if (kry1) {
+        double* P1 = R1;
+        double* B = R2;
+        double* G0 = R3;
+        double* U0 = R4;
+        unpack_sym(ent, P1, k);
+        for (int e = tid; e < k * k; e += NT) B[(e / k) * MEG_LDK + e % k] = dw_value(ent[nsym + e]);
+        load_kxk(smw + SM_G, G0, k, k);
+        load_kxk(smw + SM_U, U0, r, k);
+        for (int e = tid; e < k * k; e += NT) {
+            const int i = e / k, j = e % k;
+            double h = d_id * G0[i * MEG_LDK + j] + alpha * P1[i * MEG_LDK + j];
+            for (int l = 0; l < r; ++l) h += U0[l * MEG_LDK + i] * dco[l] * U0[l * MEG_LDK + j];
+            smw[SM_H00 + i * 32 + j] = h;
+            smw[SM_G0 + i * 32 + j] = G0[i * MEG_LDK + j];
+            smw[SM_P + i * 32 + j] = P1[i * MEG_LDK + j];
+        }
+        for (int e = tid; e < r * k; e += NT) smw[SM_U0 + (e / k) * 32 + e % k] = U0[(e / k) * MEG_LDK + e % k];
+        // C = B - E0 B  (E0 = G0 - I; the E0^2 term is below 1e-13 of B)
+        float* F = (float*)smraw;       // the reduction's scratch, free again
+        float* Fe = F;
+        float* Fb = F + FM;
+        float* Fc = F + 2 * FM;
+        for (int e = tid; e < k * k; e += NT) {
+            const int i = e / k, j = e % k;
+            Fe[i * MEG_LDK + j] = (float)(G0[i * MEG_LDK + j] - (i == j ? 1.0 : 0.0));
+            Fb[i * MEG_LDK + j] = (float)B[i * MEG_LDK + j];
+        }
+        __syncthreads();
+        mm_f32(Fe, false, Fb, Fc, k, k, k);
+        for (int e = tid; e < k * k; e += NT)
+            smw[SM_KC + (e / k) * 32 + e % k] = B[(e / k) * MEG_LDK + e % k] - (double)Fc[(e / k) * MEG_LDK + e % k];
+        return;
+    }
+    // ---- PH_KRY2: Rayleigh-Ritz on span [W0 W1]
+    const int kk = 2 * k;
+    double* H = R0;
+    double* G = R1;
+    double* P = R2;
+    double* U1 = R3;                    // scratch until the pencil is built
+    double* U0 = R4;
+    {
+        // P2 (sym) and Q2 = W0^T Y2 from the entries
+        for (int e = tid; e < nsym; e += NT) {
+            int i, j;
+            tri_decode(e, i, j);
+            const double v = dw_value(ent[e]);
+            P[(k + i) * MEG_LDK + k + j] = v;
+            P[(k + j) * MEG_LDK + k + i] = v;
+        }
+        for (int e = tid; e < k * k; e += NT) {
+            const int i = e / k, j = e % k;          // (W0^T Y2)_ij: row i of W0, column j of W1's product
+            const double v = dw_value(ent[nsym + e]);
+            P[i * MEG_LDK + k + j] = v;
+            P[(k + j) * MEG_LDK + i] = v;
+            P[i * MEG_LDK + j] = smw[SM_P + i * 32 + j];
+            G[i * MEG_LDK + j] = smw[SM_G0 + i * 32 + j];
+            G[(k + i) * MEG_LDK + k + j] = smw[SM_G + i * 32 + j];
+            const double g01 = smw[SM_G01 + i * 32 + j];
+            G[i * MEG_LDK + k + j] = g01;
+            G[(k + j) * MEG_LDK + i] = g01;
+            H[i * MEG_LDK + j] = smw[SM_H00 + i * 32 + j];
+        }
+        load_kxk(smw + SM_U, U1, r, k);
+        load_kxk(smw + SM_U0, U0, r, k);
+        for (int e = tid; e < k * k; e += NT) {
+            const int i = e / k, j = e % k;
+            double h11 = d_id * G[(k + i) * MEG_LDK + k + j] + alpha * P[(k + i) * MEG_LDK + k + j];
+            double h01 = d_id * G[i * MEG_LDK + k + j] + alpha * P[i * MEG_LDK + k + j];
+            for (int l = 0; l < r; ++l) {
+                h11 += U1[l * MEG_LDK + i] * dco[l] * U1[l * MEG_LDK + j];
+                h01 += U0[l * MEG_LDK + i] * dco[l] * U1[l * MEG_LDK + j];
+            }
+            H[(k + i) * MEG_LDK + k + j] = h11;
+            H[i * MEG_LDK + k + j] = h01;
+            H[(k + j) * MEG_LDK + i] = h01;
+        }
+        __syncthreads();
+    }
+    // E = G - I must be small for the second-order treatment of rr_fast_f32:
+    // W0 and W1 are orthonormal to a few float units, W0^T W1 to the
+    // rounding of Z' relative to its size
+    __shared__ float em_s;
+    if (tid < 32) {
+        float em = 0.f;
+        for (int e = tid; e < kk * kk; e += 32)
+            em = fmaxf(em, fabsf((float)(G[(e / kk) * MEG_LDK + e % kk] - ((e / kk == e % kk) ? 1.0 : 0.0))));
+        for (int o = 16; o > 0; o >>= 1) em = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, o));
+        if (tid == 0) em_s = em;
+    }
+    __syncthreads();
+    if (!(em_s < 1e-2f) && tid == 0) smw[SM_STATUS] = MEG_ERR_NUMERIC;
+    __shared__ double sig[MEG_KMAX];
+    __shared__ double mun[MEG_KMAX];
+    rr_fast_f32(s, smw, nullptr, P, G, H, R3, R4, (float*)smraw, wv, pr, pdg, sig, mun, shift, kk, true);
 }
 
 // ==========================================================================
@@ -1222,6 +1432,216 @@ __global__ void __launch_bounds__(NT) k_orth(const SolveDev* sds, int ns, int ph
 }
 
 // ==========================================================================
+// projection pass of the block Krylov iteration (float storage): the rest of
+// Z = A W0 outside span W0, Z' = Z - W0 C (C = G0^{-1} W0^T Z), with exact
+// products and one rounding, written over Z; Gram entries Z'^T Z' for its
+// CholeskyQR factor (k_island_c's single-pass factor).
+__global__ void __launch_bounds__(NT) k_kry_proj(const SolveDev* sds, int ns, int phase) {
+    pdl_wait();
+    pdl_trigger();
+    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_RED];
+    const int n = s.n, k = s.k, tid = threadIdx.x;
+    const int row0 = min(n, lb * s.rows_red), row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Coef<float>* Cc = (Coef<float>*)smraw;              // C (k x k)
+    float* sA = (float*)(Cc + MEG_KMAX * MEG_KMAX);     // rows of W0
+    float* sB = sA + ROWS_MAX * MEG_KMAX;               // rows of Z, then of Z'
+    dw* ent = (dw*)(sB + ROWS_MAX * MEG_KMAX);
+    const double* sm = s.sm;
+    for (int e = tid; e < k * k; e += NT) Cc[e].set(sm[SM_KC + (e / k) * 32 + e % k]);
+    const float* W = (const float*)s.W;
+    float* Z = (float*)s.Z;
+    for (int idx = tid; idx < nr * k; idx += NT) {
+        sA[idx] = W[(size_t)row0 * k + idx];
+        sB[idx] = Z[(size_t)row0 * k + idx];
+    }
+    __syncthreads();
+    float zp[(ROWS_MAX * MEG_KMAX + NT - 1) / NT];
+    int c = 0;
+    for (int idx = tid; idx < nr * k; idx += NT, ++c) {
+        const int q = idx / k, j = idx % k;
+        dw a2 = {sB[idx], 0.f};
+        float lo = 0.f;
+        for (int l = 0; l < k; ++l) {
+            const float w = sA[q * k + l];
+            dot2_acc(a2, -w, Cc[l * k + j].hi);
+            lo = fmaf(-w, Cc[l * k + j].lo, lo);
+        }
+        zp[c] = a2.hi + (a2.lo + lo);
+    }
+    __syncthreads();                                    // every row of Z is read
+    c = 0;
+    for (int idx = tid; idx < nr * k; idx += NT, ++c) {
+        sB[idx] = zp[c];
+        Z[(size_t)row0 * k + idx] = zp[c];
+    }
+    __syncthreads();
+    const int nsym = k * (k + 1) / 2;
+    for (int e = tid; e < nsym; e += NT) {
+        int i, j;
+        tri_decode(e, i, j);
+        Acc<float> a, b;
+        a.zero();
+        b.zero();
+        int q = 0;
+        for (; q + 1 < nr; q += 2) {
+            a.add_prod(sB[q * k + i], sB[q * k + j]);
+            b.add_prod(sB[(q + 1) * k + i], sB[(q + 1) * k + j]);
+        }
+        if (q < nr) a.add_prod(sB[q * k + i], sB[q * k + j]);
+        dw r0 = a.as_dw();
+        dw_add(r0, b.as_dw());
+        ent[e] = r0;
+    }
+    __syncthreads();
+    write_partial(s, lb, ent, nsym);
+}
+
+// ==========================================================================
+// orth pass of the block Krylov iteration (float storage), per row block:
+//   PH_KRY1: W1 = Z' M (Z' = Z - W0 C from the projection pass, M its refined
+//     CholeskyQR factor), exact products; W0 moves to Wp and W1 becomes the
+//     current block W; the bf16 split of W1 for the second product; Gram
+//     entries W1^T W1, V^T W1, W0^T W1.
+//   PH_KRY2: V_{t+1} = [W0 W1] QV (exact products, float64 result) and the
+//     next block W = [W0 W1] QW; its bf16 split; Gram entries W^T W and
+//     V_{t+1}^T W for the next iteration (as k_orth's final phase).
+__global__ void __launch_bounds__(NT) k_orth_kry(const SolveDev* sds, int ns, int phase) {
+    pdl_wait();
+    pdl_trigger();
+    const int si = find_solve(sds, ns, PK_RED, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_RED];     // blocks past nb_red pad the last cluster
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const int row0 = min(n, lb * s.rows_red), row1 = min(n, row0 + s.rows_red), nr = row1 - row0;
+    const bool kry1 = (phase == PH_KRY1);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Coef<float>* A1 = (Coef<float>*)smraw;             // KRY1: M (k x k)   KRY2: QW (2k x k)
+    Coef<float>* A2 = A1 + MEG_KMAX * MEG_KMAX;         //                   KRY2: QV (2k x r)
+    float* sA = (float*)(A2 + MEG_KMAX * MEG_KMAX);     // rows of W0
+    float* sB = sA + ROWS_MAX * MEG_KMAX;               // rows of Z (KRY1) / W1 (KRY2)
+    float* sC = sB + ROWS_MAX * MEG_KMAX;               // rows of the new block
+    float* sVh = sC + ROWS_MAX * MEG_KMAX;              // V as (hi, lo) floats
+    float* sVl = sVh + ROWS_MAX * MEG_RMAX;
+    dw* ent = (dw*)(sVl + ROWS_MAX * MEG_RMAX);
+    const double* sm = s.sm;
+    float* W = (float*)s.W;
+    float* Wp = (float*)s.Wp;
+    if (kry1) {
+        for (int e = tid; e < k * k; e += NT) A1[e].set(sm[SM_M1 + (e / k) * 32 + e % k]);
+    } else {
+        for (int e = tid; e < 2 * k * k; e += NT) A1[e].set(sm[SM_QW + (e / k) * 32 + e % k]);
+        for (int e = tid; e < 2 * k * r; e += NT) A2[e].set(sm[SM_QV + (e / r) * 32 + e % r]);
+    }
+    const float* Z = (const float*)s.Z;
+    for (int idx = tid; idx < nr * k; idx += NT) {
+        if (kry1) {
+            sA[idx] = W[(size_t)row0 * k + idx];
+            sB[idx] = Z[(size_t)row0 * k + idx];
+        } else {
+            sA[idx] = Wp[(size_t)row0 * k + idx];
+            sB[idx] = W[(size_t)row0 * k + idx];
+        }
+    }
+    __syncthreads();
+    double* V = s.V;
+    if (!kry1) {
+        // V_{t+1} = W0 QV[:k] + W1 QV[k:], exact products, float64 result
+        for (int idx = tid; idx < nr * r; idx += NT) {
+            const int q = idx / r, j = idx % r;
+            dw acc = {0.f, 0.f};
+            for (int l = 0; l < k; ++l) {
+                const float w0 = sA[q * k + l], w1 = sB[q * k + l];
+                dot2_acc(acc, w0, A2[l * r + j].hi);
+                dot2_acc(acc, w0, A2[l * r + j].lo);
+                dot2_acc(acc, w1, A2[(k + l) * r + j].hi);
+                dot2_acc(acc, w1, A2[(k + l) * r + j].lo);
+            }
+            V[(size_t)row0 * r + idx] = dw_value(acc);
+        }
+    }
+    // the new block, exact products over the high parts, low parts in float
+    for (int idx = tid; idx < nr * k; idx += NT) {
+        const int q = idx / k, j = idx % k;
+        dw a2 = {0.f, 0.f};
+        float lo = 0.f;
+        for (int l = 0; l < k; ++l) {
+            const float x0 = sA[q * k + l], x1 = sB[q * k + l];
+            if (kry1) {                         // Z' M
+                dot2_acc(a2, x1, A1[l * k + j].hi);
+                lo = fmaf(x1, A1[l * k + j].lo, lo);
+            } else {                            // W0 QW[:k] + W1 QW[k:]
+                dot2_acc(a2, x0, A1[l * k + j].hi);
+                lo = fmaf(x0, A1[l * k + j].lo, lo);
+                dot2_acc(a2, x1, A1[(k + l) * k + j].hi);
+                lo = fmaf(x1, A1[(k + l) * k + j].lo, lo);
+            }
+        }
+        const float w = a2.hi + (a2.lo + lo);
+        sC[idx] = w;
+        W[(size_t)row0 * k + idx] = w;
+        if (kry1) Wp[(size_t)row0 * k + idx] = sA[idx];
+    }
+    __syncthreads();
+    // V (the current one for KRY1, V_{t+1} for KRY2) as (hi, lo) floats
+    for (int idx = tid; idx < nr * r; idx += NT) {
+        const double v = V[(size_t)row0 * r + idx];
+        const float vh = (float)v;
+        sVh[idx] = vh;
+        sVl[idx] = (float)(v - (double)vh);
+    }
+    if (s.Wsp) {
+        // exact split W = hi + mid + lo in bf16, K-major, for the tensor-core product
+        const size_t kp = (size_t)s.tc_kpad;
+        const size_t P = (size_t)(s.tc_npad / 3);
+        for (int idx = tid; idx < nr * k; idx += NT) {
+            const int j = idx / nr, q = idx % nr, i = row0 + q;
+            const float w = sC[q * k + j];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const float r1 = w - __bfloat162float(hi);
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const float r2 = r1 - __bfloat162float(mid);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(r2);
+            s.Wsp[(size_t)j * kp + i] = __bfloat16_as_ushort(hi);
+            s.Wsp[(P + j) * kp + i] = __bfloat16_as_ushort(mid);
+            s.Wsp[(2 * P + j) * kp + i] = __bfloat16_as_ushort(lo);
+        }
+    }
+    __syncthreads();
+    const int nsym = k * (k + 1) / 2;
+    const int E = nsym + r * k + (kry1 ? k * k : 0);
+    for (int e = tid; e < E; e += NT) {
+        Acc<float> a;
+        a.zero();
+        if (e < nsym) {
+            int i, j;
+            tri_decode(e, i, j);
+            for (int q = 0; q < nr; ++q) a.add_prod(sC[q * k + i], sC[q * k + j]);
+        } else if (e < nsym + r * k) {
+            const int l = (e - nsym) / k, j = (e - nsym) % k;
+            float lo = 0.f;
+            for (int q = 0; q < nr; ++q) {
+                const float w = sC[q * k + j];
+                a.add_prod(sVh[q * r + l], w);
+                lo = fmaf(sVl[q * r + l], w, lo);
+            }
+            dw r0 = a.as_dw();
+            dw_add(r0, dw{lo, 0.f});
+            ent[e] = r0;
+            continue;
+        } else {
+            const int f = e - nsym - r * k, i = f / k, j = f % k;     // (W0^T W1)_ij
+            for (int q = 0; q < nr; ++q) a.add_prod(sA[q * k + i], sC[q * k + j]);
+        }
+        ent[e] = a.as_dw();
+    }
+    __syncthreads();
+    write_partial(s, lb, ent, E);
+}
+
+// ==========================================================================
 // island after orth2: G = W^T W and U = V^T W from the partials.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_island_o2(const SolveDev* sds, int ns, int phase) {
@@ -1235,7 +1655,8 @@ __global__ void __launch_bounds__(NT) k_island_o2(const SolveDev* sds, int ns, i
     constexpr int FBYTES = 4 * 32 * MEG_LDK * (int)sizeof(float);
     dw* ent = (dw*)(smraw + FBYTES);
     const int nsym = k * (k + 1) / 2;
-    const int E = nsym + r * k;
+    const bool kry1 = (phase == PH_KRY1);          // block Krylov: also W0^T W1
+    const int E = nsym + r * k + (kry1 ? k * k : 0);
     reduce_partials(s, ent, E, (dw*)smraw, FBYTES / (int)sizeof(dw));
     double* smw = s.sm;
     for (int e = tid; e < nsym; e += NT) {
@@ -1246,6 +1667,8 @@ __global__ void __launch_bounds__(NT) k_island_o2(const SolveDev* sds, int ns, i
         smw[SM_G + j * 32 + i] = v;
     }
     for (int e = tid; e < r * k; e += NT) smw[SM_U + (e / k) * 32 + e % k] = dw_value(ent[nsym + e]);
+    if (kry1)
+        for (int e = tid; e < k * k; e += NT) smw[SM_G01 + (e / k) * 32 + e % k] = dw_value(ent[nsym + r * k + e]);
 }
 
 // ==========================================================================
@@ -1946,6 +2369,13 @@ size_t orth_smem(int prec) {       // M1, Qv, rows of W, rows of V, entries (fir
     return 8 * MEG_KMAX * MEG_KMAX + 8 * MEG_KMAX * MEG_RMAX + ROWS_MAX * MEG_KMAX * tsz + 8 +
            ROWS_MAX * MEG_RMAX * 8 + 16 + std::max<size_t>(RED_MAX_ENTRIES * sizeof(dw), ROWS_MAX * MEG_KMAX * tsz);
 }
+size_t kry_proj_smem() {          // C (Coef k x k), rows of W0 and Z, entries
+    return 8 * MEG_KMAX * MEG_KMAX + 2 * ROWS_MAX * MEG_KMAX * 4 + 528 * sizeof(dw) + 16;
+}
+size_t orth_kry_smem() {          // two Coef k x k areas, three row blocks, V hi/lo, entries
+    return 2 * 8 * MEG_KMAX * MEG_KMAX + 3 * ROWS_MAX * MEG_KMAX * 4 + 2 * ROWS_MAX * MEG_RMAX * 4 +
+           RED_MAX_ENTRIES * sizeof(dw) + 16;
+}
 size_t island_smem() {
     return 4 * 32 * MEG_LDK * sizeof(float) + RED_MAX_ENTRIES * sizeof(dw) + (6 * 32 * MEG_LDK + 32 + 96 + 32) * sizeof(double);
 }
@@ -1973,6 +2403,9 @@ cudaError_t init_kernel_attributes() {
     if ((e = set_smem(k_island_o1<double>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_o2<double>, island_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_island_o2<float>, island_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_island_kry<float>, island_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_orth_kry, orth_kry_smem())) != cudaSuccess) return e;
+    if ((e = set_smem(k_kry_proj, kry_proj_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_objective<float>, OBJ_SMEM_MAX)) != cudaSuccess) return e;
     return cudaSuccess;
 }
@@ -2024,6 +2457,10 @@ cudaError_t launch_row_island(void (*row)(const SolveDev*, int, int), void (*isl
 }
 
 cudaError_t launch_combine(const GroupLaunch& g, int phase) {
+    if (phase == PH_KRY1 || phase == PH_KRY2) {
+        if (g.prec == MEG_FP64) return cudaErrorNotSupported;   // float storage only
+        return launch_row_island<float>(k_combine<float>, k_island_kry<float>, g, combine_smem(g.prec), phase);
+    }
     if (g.prec == MEG_FP64)
         return launch_row_island<double>(k_combine<double>, k_island_c<double>, g, combine_smem(g.prec), phase);
     return launch_row_island<float>(k_combine<float>, k_island_c<float>, g, combine_smem(g.prec), phase);
@@ -2035,6 +2472,16 @@ cudaError_t launch_combine(const GroupLaunch& g, int phase) {
 // (their factor refined in Gram space by combine's factor kernel); both end
 // with the reduction of U and G
 cudaError_t launch_orthonormalise(const GroupLaunch& g, int phase) {
+    if (phase == PH_KRY1 || phase == PH_KRY2) {
+        if (g.prec == MEG_FP64) return cudaErrorNotSupported;
+        if (phase == PH_KRY1) {
+            // Z' = Z - W0 C and its Gram, then the single-pass CholeskyQR factor of Z'
+            cudaError_t e = launch_row_island<float>(k_kry_proj, k_island_c<float>, g, kry_proj_smem(), PH_ADVANCE);
+            if (e != cudaSuccess) return e;
+        }
+        return launch_row_island<float>(k_orth_kry, k_island_o2<float>, g, orth_kry_smem(),
+                                        phase == PH_KRY1 ? PH_KRY1 : PH_FINAL);
+    }
     if (g.prec == MEG_FP64) {
         cudaError_t e =
             launch_row_island<double>(k_orth1<double>, k_island_o1<double>, g, orth1_smem(MEG_FP64), phase);

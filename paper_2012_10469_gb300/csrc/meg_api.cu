@@ -142,6 +142,7 @@ struct meg_group_s {
     GroupLaunch gl{};
     bool has_dense = false, has_csr = false, has_meas = false;
     int q = 0;
+    bool krylov = false;                   // block Krylov eigensolver (warm starts use subspace iteration)
     cudaStream_t stream = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool own_stream = false;
@@ -201,9 +202,14 @@ meg_status upload_desc(meg_solve_s* h, const SolveDev& d) {
 }
 
 // One iteration of Algorithm 2 (or one warm-start product set), enqueued.
-meg_status enqueue_iteration(const GroupLaunch& g, bool has_dense, bool has_csr, bool has_meas, int q) {
+// Subspace iteration: q products, each followed by the orthonormalisation of
+// its block, the last one by the Rayleigh-Ritz step.  Block Krylov (q = 2):
+// the first product's block is projected against W0 and orthonormalised, the
+// second ends in the Rayleigh-Ritz step on span [W0 W1].
+meg_status enqueue_iteration(const GroupLaunch& g, bool has_dense, bool has_csr, bool has_meas, int q,
+                             bool krylov = false) {
     for (int j = 0; j < q; ++j) {
-        const int phase = (j == q - 1) ? PH_FINAL : PH_ADVANCE;
+        const int phase = krylov ? (j == 0 ? PH_KRY1 : PH_KRY2) : (j == q - 1) ? PH_FINAL : PH_ADVANCE;
         if (has_meas) CU(launch_meas_batch(g));
         if (j == 0) CU(launch_begin(g));
         if (has_dense) CU(launch_dense(g));
@@ -395,6 +401,13 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
         cudaGetLastError();
     }
 
+    if (opt->eigensolver != MEG_EIG_SUBSPACE && opt->eigensolver != MEG_EIG_BLOCK_KRYLOV)
+        return fail(MEG_ERR_INVALID_ARG, "meg_create: unknown eigensolver");
+    if (opt->eigensolver == MEG_EIG_BLOCK_KRYLOV &&
+        (q != 2 || 2 * (r + p) > MEG_KMAX || opt->precision == MEG_FP64))
+        return fail(MEG_ERR_INVALID_ARG,
+                    "meg_create: block Krylov needs q = 2, 2 (r + p) <= 32 and float storage (MEG_FP32, MEG_MIXED_BF16)");
+
     meg_solve_s* h = new meg_solve_s();
     h->opt = *opt;
     h->n = n; h->r = r; h->k = r + p; h->q = q; h->prec = opt->precision;
@@ -410,6 +423,7 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
     }
     SolveDev& d = h->desc;
     d.n = n; d.r = r; d.k = h->k; d.kind = -1; d.prec = h->prec; d.q = q; d.mode = 0;
+    d.eig = opt->eigensolver;
     d.eta = opt->eta; d.eps_a = opt->eps_a; d.eps_c = opt->eps_c; d.eps_pow = opt->eps_pow; d.seed = opt->seed;
     d.log_nr = std::log((double)(n - r));
     compute_partition(h, d);
@@ -670,7 +684,8 @@ meg_status meg_step(meg_handle h, int nsteps) {
         CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         const int kind = h->desc.kind;
         st = enqueue_iteration(solo_launch(h), kind == MEG_DENSE_QUAD || kind == MEG_LINEAR,
-                               kind == MEG_CSR_QUAD, kind == MEG_MEAS_STOCH, h->q);
+                               kind == MEG_CSR_QUAD, kind == MEG_MEAS_STOCH, h->q,
+                               h->desc.eig == MEG_EIG_BLOCK_KRYLOV);
         cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
         if (st != MEG_OK) return st;
         if (ce != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -724,7 +739,7 @@ meg_status build_solve_graph(meg_solve_s* h) {
             const GroupLaunch g = solo_launch(h);
             for (int i = 0; i < SOLVE_CHUNK && st == MEG_OK; ++i)
                 st = enqueue_iteration(g, kind == MEG_DENSE_QUAD || kind == MEG_LINEAR, kind == MEG_CSR_QUAD,
-                                       kind == MEG_MEAS_STOCH, h->q);
+                                       kind == MEG_MEAS_STOCH, h->q, h->desc.eig == MEG_EIG_BLOCK_KRYLOV);
             cudaError_t le = cudaSuccess;
             if (st == MEG_OK) le = launch_objective(g, h->d_f);
             if (st == MEG_OK && le == cudaSuccess) le = launch_solve_check(h->sm, h->d_f, cond, h->stream);
@@ -918,8 +933,8 @@ meg_status group_create_impl(const meg_handle* solves, int count, void* stream, 
         if (!h || !h->has_obj || (!warm && !h->has_x)) return fail(MEG_ERR_STATE, "meg_group_create: solve not ready");
         if (h->failed) return fail(MEG_ERR_STATE, "meg_group_create: a solve failed earlier on the device");
         if (h->in_group) return fail(MEG_ERR_STATE, "meg_group_create: solve already in a group");
-        if (h->prec != prec || h->q != q)
-            return fail(MEG_ERR_INVALID_ARG, "meg_group_create: solves must share precision and q");
+        if (h->prec != prec || h->q != q || h->desc.eig != solves[0]->desc.eig)
+            return fail(MEG_ERR_INVALID_ARG, "meg_group_create: solves must share precision, q and eigensolver");
     }
     meg_group_s* g = new meg_group_s();
     g->stream = (cudaStream_t)stream;
@@ -931,6 +946,7 @@ meg_status group_create_impl(const meg_handle* solves, int count, void* stream, 
         g->own_stream = true;
     }
     g->q = q;
+    g->krylov = solves[0]->desc.eig == MEG_EIG_BLOCK_KRYLOV;
     std::vector<SolveDev> descs(count);
     int tot[PK_COUNT] = {};
     for (int i = 0; i < count; ++i) {
@@ -1098,7 +1114,7 @@ meg_status meg_group_step(meg_group g, int nsteps) {
     if (!g->gexec) {
         cudaGraph_t graph;
         CU(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-        meg_status st = enqueue_iteration(g->gl, g->has_dense, g->has_csr, g->has_meas, g->q);
+        meg_status st = enqueue_iteration(g->gl, g->has_dense, g->has_csr, g->has_meas, g->q, g->krylov);
         cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
         if (st != MEG_OK) return st;
         if (ce != cudaSuccess) return fail(MEG_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
@@ -1113,7 +1129,7 @@ meg_status meg_group_step(meg_group g, int nsteps) {
 meg_status meg_group_launch(meg_group g, int nsteps) {
     if (!g || nsteps < 0) return fail(MEG_ERR_INVALID_ARG, "meg_group_launch: arguments");
     for (int i = 0; i < nsteps; ++i) {
-        meg_status st = enqueue_iteration(g->gl, g->has_dense, g->has_csr, g->has_meas, g->q);
+        meg_status st = enqueue_iteration(g->gl, g->has_dense, g->has_csr, g->has_meas, g->q, g->krylov);
         if (st != MEG_OK) return st;
     }
     return MEG_OK;
@@ -1218,7 +1234,8 @@ int meg_group_kernels_per_step(meg_group g) {
     const int dense = g->gl.tc_chunks + (g->gl.blocks[PK_DENSE] > 0 ? 1 : 0);
     const int csr = g->has_csr ? (g->gl.prec == MEG_FP64 ? 1 : 2) : 0;   // float modes: V cast + product
     const int per = dense + csr + (g->has_meas ? 2 : 0) + (g->gl.prec == MEG_FP64 ? 6 : 4);
-    return g->q * per + 1;
+    // block Krylov: the projection pass and its factor kernel after the first product
+    return g->q * per + 1 + (g->krylov ? 2 : 0);
 }
 
 meg_status meg_group_destroy(meg_group g) {

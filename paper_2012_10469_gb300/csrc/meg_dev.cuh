@@ -60,7 +60,15 @@ enum SmallSlot : int {
     SM_M1 = SM_S1 + 1024,   // first CholQR right factor (k x k), W' = Z M1
     SM_M2 = SM_M1 + 1024,   // second CholQR right factor, W = W' M2
     SM_QV = SM_M2 + 1024,   // rotation to the Ritz vectors: V_{t+1} = W QV[:, :r]
-    SM_TOTAL = SM_QV + 1024
+    // block Krylov (two blocks W0, W1 of one iteration; W1 is current after the
+    // first product's orthonormalisation)
+    SM_U0 = SM_QV + 1024,   // V^T W0      (r x k)
+    SM_G0 = SM_U0 + 1024,   // W0^T W0     (k x k)
+    SM_G01 = SM_G0 + 1024,  // W0^T W1     (k x k)
+    SM_H00 = SM_G01 + 1024, // W0^T (M_t - c I) W0
+    SM_KC = SM_H00 + 1024,  // C M, C = G0^{-1} W0^T Z the projection of Z = (M_t - c I) W0 on W0
+    SM_QW = SM_KC + 1024,   // [W0 W1] QW = the next block (2k x k)
+    SM_TOTAL = SM_QW + 1024
 };
 
 // Work-partition kinds (one offset table per kind in a group).
@@ -102,6 +110,7 @@ struct SolveDev {
     int ks_len;          // K extent of one split (multiple of the K tile)
     int nb_csr, nb_meas; // blocks of the CSR / measurement kernels
     int tc;              // 1: dense product on tcgen05 (bf16 data, n % 8 == 0)
+    int eig;             // MEG_EIG_SUBSPACE or MEG_EIG_BLOCK_KRYLOV
     int nb_tm;           // tensor-core path: 128-row tiles
     int tc_npad, tc_kpad;// Wsp: (3k padded to 16) x (n padded to 64) bf16
     int tc_G;            // tensor-core launch holding this solve: CTAs
@@ -310,7 +319,10 @@ struct GroupLaunch {
 enum RedPhase : int {
     PH_INIT = 0,        // orthonormalise the initial block (W <- CholQR2(W))
     PH_ADVANCE = 1,     // a product that only advances the subspace
-    PH_FINAL = 2        // the product whose W gets the Rayleigh-Ritz step
+    PH_FINAL = 2,       // the product whose W gets the Rayleigh-Ritz step
+    // block Krylov, two products per iteration (float storage)
+    PH_KRY1 = 3,        // after A W0: project Z = A W0 on W0, CholeskyQR of the rest -> W1
+    PH_KRY2 = 4         // after A W1: Rayleigh-Ritz on span [W0 W1] (2k x 2k), next block
 };
 
 cudaError_t launch_begin(const GroupLaunch& g);

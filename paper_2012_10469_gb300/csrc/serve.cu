@@ -9,7 +9,7 @@
 //                 data are copied in on the request's own stream, X_1 is set
 //                 (given X_0 or the warm start of eq. exp:init) and f(X_1) is
 //                 evaluated;
-//   classes    -- admitted solves of one (precision, q, objective family)
+//   classes    -- admitted solves of one (precision, q, eigensolver, objective family)
 //                 form a group (grouped kernels, one launch per kernel for
 //                 all members) on the class's own stream, so classes overlap
 //                 on the device;
@@ -75,7 +75,7 @@ struct Req {
 };
 
 struct Class {
-    int precision = 0, q = 0, meas = 0, check = 10;
+    int precision = 0, q = 0, meas = 0, eig = 0, check = 10;
     std::vector<Req*> members;         // the running group, in member order
     std::vector<Req*> joining;         // admitted while a tick was running
     meg_group g = nullptr;
@@ -124,11 +124,13 @@ struct meg_server_s {
 int meg_server_s::class_of(const meg_request& rq) {
     const int meas = rq.kind == MEG_MEAS_STOCH;
     for (size_t i = 0; i < classes.size(); ++i)
-        if (classes[i].precision == rq.opt.precision && classes[i].q == rq.opt.q && classes[i].meas == meas)
+        if (classes[i].precision == rq.opt.precision && classes[i].q == rq.opt.q && classes[i].meas == meas &&
+            classes[i].eig == rq.opt.eigensolver)
             return (int)i;
     Class c;
     c.precision = rq.opt.precision;
     c.q = rq.opt.q;
+    c.eig = rq.opt.eigensolver;
     c.meas = meas;
     c.check = meas ? opt.meas_check_every : opt.check_every;
     cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
@@ -184,10 +186,11 @@ bool meg_server_s::admit(Req* q) {
 // product count), f(X_1) from the same grouped pass; then each request joins
 // its class at the next tick boundary.
 void meg_server_s::admit_batch(std::vector<Req*>& ready) {
-    std::map<std::tuple<int, int, int>, std::vector<Req*>> warm;
+    std::map<std::tuple<int, int, int, int>, std::vector<Req*>> warm;
     for (Req* q : ready)
         if (q->rq.warm_start_products > 0)
-            warm[std::make_tuple(q->rq.opt.precision, q->rq.opt.q, q->rq.warm_start_products)].push_back(q);
+            warm[std::make_tuple(q->rq.opt.precision, q->rq.opt.q, q->rq.warm_start_products, q->rq.opt.eigensolver)]
+                .push_back(q);
     for (auto& kv : warm) {
         std::vector<Req*>& v = kv.second;
         std::vector<meg_handle> hs;

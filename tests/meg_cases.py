@@ -32,12 +32,12 @@ def oracle_objective(kind, prob, seed=0):
     raise ValueError(kind)
 
 
-def make_gpu_solve(kind, prob, r, p, q, precision, eta, seed, V0=None, lam0=None):
+def make_gpu_solve(kind, prob, r, p, q, precision, eta, seed, V0=None, lam0=None, eigensolver=0):
     """Create a solve through the C ABI and attach the objective."""
     import torch
     from paper_2012_10469_gb300 import binding as B
     s = B.Solve(prob.n, r, p=p, q=q, precision=precision, eta=eta, seed=seed, V0=V0, lam0=lam0,
-                stream=torch.cuda.current_stream().cuda_stream)
+                stream=torch.cuda.current_stream().cuda_stream, eigensolver=eigensolver)
     if kind in ("dense_quadratic", "linear"):
         s.meg_set_objective(B.MEG_DENSE_QUAD if kind == "dense_quadratic" else B.MEG_LINEAR,
                             dense=to_device_dense(prob, precision))
@@ -66,7 +66,7 @@ def rel_frob(Xg: meg.Factored, Xo: meg.Factored) -> float:
 
 
 def run_pair(kind, prob, r, p, q, precision, eta, T, checkpoints, seed=7, method="exact",
-             warm=None):
+             warm=None, eigensolver=0):
     """Run oracle and GPU side by side from the same X_0; return per-checkpoint
     (t, X_gpu, X_oracle, sigma_gpu, sigma_oracle, f_gpu, f_oracle, cert pairs)."""
     obj = oracle_objective(kind, prob, seed=seed)
@@ -74,7 +74,7 @@ def run_pair(kind, prob, r, p, q, precision, eta, T, checkpoints, seed=7, method
         V0, lam0 = meg.warm_start(obj, r)
     else:
         V0, lam0 = warm
-    s = make_gpu_solve(kind, prob, r, p, q, precision, eta, seed, V0=V0, lam0=lam0)
+    s = make_gpu_solve(kind, prob, r, p, q, precision, eta, seed, V0=V0, lam0=lam0, eigensolver=eigensolver)
     X = meg.init_X1(V0, lam0, meg.eps_schedule(0))
     f1 = obj.value(X)
     out = []

@@ -49,7 +49,7 @@ def test_config1_full_batch_as_benchmarked():
     N, R = 4096, 10
     probs = [synth.dense_quadratic(N, R, seed=1001 + i, sigma=1e-5, storage="bf16") for i in range(8)]
     stream = torch.cuda.current_stream().cuda_stream
-    P, Q, _, ok = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, probs[0].U, probs[0].w,
+    P, Q, _, ok, _eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, probs[0].U, probs[0].w,
                                  dense=to_device_dense(probs[0], B.MEG_MIXED_BF16), seed=1001, stream=stream,
                                  **AUTOTUNE)
     assert ok
@@ -132,7 +132,7 @@ def test_config3_full_measurements():
     A = torch.from_numpy(np.ascontiguousarray(synth.bf16_bits(prob.A).view(np.int16))).cuda()
     y = torch.from_numpy(prob.y).cuda()
     # (p, q) for the workload's 2000 iterations, chosen by meg_autotune
-    P, Q, _, ok = B.meg_autotune(prob.n, 4, B.MEG_MIXED_BF16, B.MEG_MEAS_STOCH, V0, lam0, A=A, y=y,
+    P, Q, _, ok, _eig = B.meg_autotune(prob.n, 4, B.MEG_MIXED_BF16, B.MEG_MEAS_STOCH, V0, lam0, A=A, y=y,
                                   L=prob.L, eta=eta, seed=1003, q_max=7, pilot_iters=20, horizon=2000, tol_x=1e-5,
                                   stream=torch.cuda.current_stream().cuda_stream)
     assert ok, (P, Q)
@@ -158,7 +158,7 @@ def test_autotune_choice_is_cheapest_accurate():
     prob = synth.dense_quadratic(n, r, seed=1500, sigma=1e-5, storage="bf16")
     D = to_device_dense(prob, B.MEG_MIXED_BF16)
     ps, q_max, pilot, horizon, tol = (2, 4, 8), 3, 12, 400, 1e-5
-    p, q, err, ok = B.meg_autotune(n, r, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, prob.U, prob.w, dense=D, seed=3,
+    p, q, err, ok, _eig = B.meg_autotune(n, r, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, prob.U, prob.w, dense=D, seed=3,
                                    q_max=q_max, p_cand=ps, pilot_iters=pilot, horizon=horizon, tol_x=tol,
                                    stream=torch.cuda.current_stream().cuda_stream)
     accept = tol * np.sqrt(pilot / horizon)

@@ -59,7 +59,7 @@ def test_config1_batch_to_the_horizon():
     N, R = 4096, 10
     probs = [synth.dense_quadratic(N, R, seed=1001 + i, sigma=1e-5, storage="bf16") for i in range(8)]
     stream = torch.cuda.current_stream().cuda_stream
-    P, Q, _, ok = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, probs[0].U, probs[0].w,
+    P, Q, _, ok, _eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, probs[0].U, probs[0].w,
                                  dense=to_device_dense(probs[0], B.MEG_MIXED_BF16), seed=1001, stream=stream,
                                  **AUTOTUNE)
     assert ok
@@ -110,7 +110,7 @@ def test_config3_measurements_to_500():
     V0, lam0 = prob.U, np.full(4, 0.25)
     A = torch.from_numpy(np.ascontiguousarray(synth.bf16_bits(prob.A).view(np.int16))).cuda()
     y = torch.from_numpy(prob.y).cuda()
-    P, Q, _, ok = B.meg_autotune(prob.n, 4, B.MEG_MIXED_BF16, B.MEG_MEAS_STOCH, V0, lam0, A=A, y=y,
+    P, Q, _, ok, _eig = B.meg_autotune(prob.n, 4, B.MEG_MIXED_BF16, B.MEG_MEAS_STOCH, V0, lam0, A=A, y=y,
                                   L=prob.L, eta=eta, seed=1003, q_max=7, pilot_iters=20, horizon=2000, tol_x=1e-5,
                                   stream=torch.cuda.current_stream().cuda_stream)
     assert ok, (P, Q)
