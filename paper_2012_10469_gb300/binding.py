@@ -27,7 +27,7 @@ SM_T, SM_EPS, SM_S, SM_LOGS, SM_SHIFT, SM_C0, SM_ALPHA, SM_GNORM, SM_FEST, SM_CE
     SM_FIRST_HOLD, SM_STATUS, SM_TRD, SM_FROD2, SM_LAST_T, SM_LSE, SM_RSS, SM_RESID_BOUND, SM_ETA, \
     SM_JSWEEPS, SM_F1 = range(22)
 SM_MU, SM_DCOEF, SM_SIGMA = 32, 64, 96
-SM_TOTAL = 128 + 13 * 1024
+SM_TOTAL = 128 + 13 * 1024 + 32
 
 
 class meg_options(C.Structure):

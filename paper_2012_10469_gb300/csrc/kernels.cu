@@ -223,12 +223,12 @@ __global__ void k_begin(const SolveDev* sds, int ns) {
     const double t = sm[SM_T];
     const double sv = sm[SM_S];
     const double eta = s.eta;
-    // one logarithm per lane
-    const double logs = log(sv);
+    // log s and log mu were stored with s and mu (no logarithm here)
+    const double logs = sm[SM_LOGS];
     double lmu = logs;
     if (lane < r) {
         const double mu = sm[SM_MU + lane];
-        lmu = log(mu);
+        lmu = sm[SM_LOGMU + lane];
         double d = lmu - logs;
         if (s.kind == MEG_DENSE_QUAD) d -= eta * (mu - sv);
         sm[SM_DCOEF + lane] = d;
@@ -244,7 +244,6 @@ __global__ void k_begin(const SolveDev* sds, int ns) {
         else if (s.eps_pow == 3.0) xp = x * x * x;
         else xp = pow(x, s.eps_pow);
         sm[SM_EPS] = s.eps_a / xp;
-        sm[SM_LOGS] = logs;
         sm[SM_C0] = (s.kind == MEG_DENSE_QUAD) ? logs - eta * sv : logs;
         sm[SM_ALPHA] = (s.kind == MEG_DENSE_QUAD) ? eta : -eta;
         double g;
@@ -353,7 +352,7 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
             dot2_acc(num, q, F3[a * MEG_LDK + tid]);
             dot2_acc(den, q, q);
         }
-        wv[tid] = dw_value(num) / dw_value(den);
+        wv[tid] = dw_value(num) * rcp_newton(dw_value(den));
     }
     __syncthreads();
     if (tid < k) {
@@ -384,8 +383,10 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
             }
             const double hv = dw_value(h), gap = wv[ci] - wv[j];
             if (fabs(gap) > 100.0 * fabs(hv)) {
-                cf = (float)(hv / gap);
-                c2 = (float)(hv * hv / gap);
+                // float quotients: the coefficients are stored as floats
+                const float hf = (float)hv, gf = (float)gap;
+                cf = hf / gf;
+                c2 = hf * cf;
             }
         }
         if (i < r) Bh[j * MEG_LDK + i] = cf;
@@ -462,18 +463,24 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
             a_r += __shfl_xor_sync(0xffffffffu, a_r, o);
             a_r1 += __shfl_xor_sync(0xffffffffu, a_r1, o);
         }
-        // lane 0: log a_r, lane 1: log a_{r+1}, lane 2: log eps
-        const double lg = log(lane == 0 ? a_r : (lane == 1 ? a_r1 : (lane == 2 ? eps : 1.0)));
+        // lane 0: log a_r, lane 1: log a_{r+1}, lane 2: log eps, lane 3: log(1 - eps)
+        const double lg = log(lane == 0 ? a_r : (lane == 1 ? a_r1 : (lane == 2 ? eps : lane == 3 ? 1.0 - eps : 1.0)));
         const double lse_r = m + __shfl_sync(0xffffffffu, lg, 0);
         const double lse_r1 = m + __shfl_sync(0xffffffffu, lg, 1);
         const double log_eps = __shfl_sync(0xffffffffu, lg, 2);
+        const double log_1meps = __shfl_sync(0xffffffffu, lg, 3);
         if (s.mode == 1) {
             if (lane == 0) {
                 for (int i = 0; i < r; ++i) mun[i] = sig[i];
                 simplex_project(mun, r);
                 const double eps0 = eps_of(s, 0.0);
-                for (int i = 0; i < r; ++i) smw[SM_MU + i] = (1.0 - eps0) * mun[i] + eps0 / n;
+                for (int i = 0; i < r; ++i) {
+                    const double mu0 = (1.0 - eps0) * mun[i] + eps0 / n;
+                    smw[SM_MU + i] = mu0;
+                    smw[SM_LOGMU + i] = log(mu0);
+                }
                 smw[SM_S] = eps0 / n;
+                smw[SM_LOGS] = log(eps0 / n);
                 smw[SM_T] = 1.0;
                 smw[SM_LAST_T] = 0.0;
                 smw[SM_CERT] = 0.0;
@@ -481,9 +488,11 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
                 smw[SM_FIRST_HOLD] = 0.0;
             }
         } else {
-            const double s_new = eps / (double)(n - r);
-            // mu_i = (1 - eps) e^{sigma_i - m} / a_r: the exponentials already formed
-            const double mu = lane < r ? (1.0 - eps) * ex / a_r : 0.0;
+            const double s_new = eps * rcp_newton((double)(n - r));
+            // mu_i = (1 - eps) e^{sigma_i - m} / a_r: the exponentials already formed;
+            // log mu_i = log(1 - eps) + sigma_i - lse_r, log s = log eps - log(n - r)
+            const double mu = lane < r ? (1.0 - eps) * ex * rcp_newton(a_r) : 0.0;
+            if (lane < r) smw[SM_LOGMU + lane] = log_1meps + (sig[lane] - lse_r);
             double xd = lane < r ? (mu - s_new) * pdg[lane] : 0.0, x2 = mu * mu;
             for (int o = 16; o > 0; o >>= 1) {
                 xd += __shfl_xor_sync(0xffffffffu, xd, o);
@@ -510,6 +519,7 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
                     }
                 }
                 smw[SM_S] = s_new;
+                smw[SM_LOGS] = log_eps - s.log_nr;
                 smw[SM_T] = t + 1.0;
             }
         }
@@ -849,8 +859,13 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
             for (int i = 0; i < r; ++i) mun[i] = sig[i];
             simplex_project(mun, r);
             const double eps0 = eps_of(s, 0.0);
-            for (int i = 0; i < r; ++i) smw[SM_MU + i] = (1.0 - eps0) * mun[i] + eps0 / n;
+            for (int i = 0; i < r; ++i) {
+                const double mu0 = (1.0 - eps0) * mun[i] + eps0 / n;
+                smw[SM_MU + i] = mu0;
+                smw[SM_LOGMU + i] = log(mu0);
+            }
             smw[SM_S] = eps0 / n;
+            smw[SM_LOGS] = log(eps0 / n);
             smw[SM_T] = 1.0;
             smw[SM_LAST_T] = 0.0;
             smw[SM_CERT] = 0.0;
@@ -887,8 +902,13 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
                     smw[SM_FEST] = xd;
                 }
             }
-            for (int i = 0; i < r; ++i) smw[SM_MU + i] = mun[i];
+            const double log_1meps = log1p(-eps);
+            for (int i = 0; i < r; ++i) {
+                smw[SM_MU + i] = mun[i];
+                smw[SM_LOGMU + i] = log_1meps + (sig[i] - lse_r);
+            }
             smw[SM_S] = s_new;
+            smw[SM_LOGS] = log(eps) - log((double)(n - r));
             smw[SM_T] = t + 1.0;
         }
     }

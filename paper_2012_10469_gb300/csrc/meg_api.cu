@@ -468,8 +468,12 @@ meg_status meg_create(const meg_options* opt, const double* V0, const double* la
     smh[SM_ETA] = opt->eta;
     smh[SM_F1] = std::nan("");
     if (V0) {
-        for (int i = 0; i < r; ++i) smh[SM_MU + i] = (1.0 - eps0) * lam0[i] + eps0 / n;
+        for (int i = 0; i < r; ++i) {
+            smh[SM_MU + i] = (1.0 - eps0) * lam0[i] + eps0 / n;
+            smh[SM_LOGMU + i] = std::log(smh[SM_MU + i]);
+        }
         smh[SM_S] = eps0 / n;
+        smh[SM_LOGS] = std::log(smh[SM_S]);
     }
     if (cudaMemsetAsync(h->ctr, 0, sizeof(unsigned) * (groups + 3), h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->V, 0, nr8, h->stream) != cudaSuccess ||

@@ -25,7 +25,7 @@ enum SmallSlot : int {
     SM_T = 0,          // index t of the next iteration (X_t is the current iterate)
     SM_EPS,            // eps_t of the iteration in progress
     SM_S,              // s of X_t (spectrum value off span V)
-    SM_LOGS,           // log s
+    SM_LOGS,           // log s of X_t (set with s: by the exp-map, meg_create, checkpoints)
     SM_SHIFT,          // c: the subspace iteration runs on M_t - c I
     SM_C0,             // identity coefficient of M_t (without the shift)
     SM_ALPHA,          // coefficient of the gradient product Y in M_t W
@@ -68,7 +68,8 @@ enum SmallSlot : int {
     SM_H00 = SM_G01 + 1024, // W0^T (M_t - c I) W0
     SM_KC = SM_H00 + 1024,  // C M, C = G0^{-1} W0^T Z the projection of Z = (M_t - c I) W0 on W0
     SM_QW = SM_KC + 1024,   // [W0 W1] QW = the next block (2k x k)
-    SM_TOTAL = SM_QW + 1024
+    SM_LOGMU = SM_QW + 1024, // [32] log mu of X_t, set with mu (the next iteration needs no logarithm)
+    SM_TOTAL = SM_LOGMU + 32
 };
 
 // Work-partition kinds (one offset table per kind in a group).
@@ -288,6 +289,16 @@ template <> struct Coef<float> {
     __device__ __forceinline__ float mul(float x) const { return fmaf(x, lo, x * hi); }
     __device__ __forceinline__ float fma_(float x, float acc) const { return fmaf(x, hi, fmaf(x, lo, acc)); }
 };
+
+// 1/x for a positive double within the float range, without a float64
+// division (a float64 division costs thousands of cycles on GB300): the float
+// reciprocal refined by two Newton-Raphson steps y <- y (2 - x y), each of
+// which squares the relative error (2^-23 -> 2^-46 -> the float64 rounding).
+__device__ __forceinline__ double rcp_newton(double x) {
+    double y = (double)__frcp_rn((float)x);
+    y = y * fma(-x, y, 2.0);
+    return y * fma(-x, y, 2.0);
+}
 
 // eps_t = a / (t + c + 1)^q  (Section 7 schedule, parameters of the solve)
 __device__ __forceinline__ double eps_of(const SolveDev& s, double t) {
