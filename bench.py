@@ -34,8 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MEG iters/s at n=4096 and solves/s p50/p99 vs plain FP32 GPU form at 1e-6 gap"
 N, R = 4096, 10
-P, Q = 6, 3          # extra subspace vectors, products per iteration: set by meg_autotune in the GPU arm
-AUTOTUNE = dict(q_max=4, p_cand=(4, 6, 8, 12, 16), pilot_iters=20, horizon=500, tol_x=1e-5)
+P, Q, EIG = 6, 3, 0  # extra subspace vectors, products per iteration, eigensolver: set by meg_autotune
+AUTOTUNE = dict(q_max=4, p_cand=(2, 4, 6, 8, 12, 16), pilot_iters=20, horizon=500, tol_x=1e-5, krylov=True)
+EIG_NAME = {0: "subspace iteration", 1: "block Krylov"}
 BATCH = 8
 SEED0 = 1001
 
@@ -129,16 +130,18 @@ def make_batch(batch: int, seed0: int):
 
 
 def autotune_pq(prob, device, stream):
-    """meg_autotune on one instance of the batch: the cheapest (p, q) whose
-    iterate stays within 1e-5 of a more resolved reference over 500 iterations."""
+    """meg_autotune on one instance of the batch: the cheapest (eigensolver, p,
+    q) whose iterate stays within 1e-5 of a more resolved reference over 500
+    iterations."""
     import torch
     from paper_2012_10469_gb300 import binding as B
-    global P, Q
+    global P, Q, EIG
     bits = torch.from_numpy(np.ascontiguousarray(prob.bits().view(np.int16))).to(device)
-    p, q, err, ok, _eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, prob.U, prob.w, dense=bits,
-                                   seed=SEED0, stream=stream, **AUTOTUNE)
-    P, Q = p, q
-    return {"p": p, "q": q, "pilot_distance": err, "met_target": ok, **{k: v for k, v in AUTOTUNE.items()}}
+    p, q, err, ok, eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, prob.U, prob.w, dense=bits,
+                                        seed=SEED0, stream=stream, **AUTOTUNE)
+    P, Q, EIG = p, q, eig
+    return {"p": p, "q": q, "eigensolver": EIG_NAME[eig], "pilot_distance": err, "met_target": ok,
+            **{k: v for k, v in AUTOTUNE.items()}}
 
 
 def gpu_solves(probs, device, stream):
@@ -149,7 +152,7 @@ def gpu_solves(probs, device, stream):
     for i, prob in enumerate(probs):
         bits = torch.from_numpy(np.ascontiguousarray(prob.bits().view(np.int16))).to(device)
         s = B.Solve(N, R, p=P, q=Q, precision=B.MEG_MIXED_BF16, eta=1.0, seed=SEED0 + i, stream=stream,
-                    V0=prob.U, lam0=prob.w)
+                    V0=prob.U, lam0=prob.w, eigensolver=EIG)
         s.meg_set_objective(B.MEG_DENSE_QUAD, dense=bits)
         solves.append(s)
         dense.append(bits)
@@ -160,7 +163,7 @@ def gpu_solves(probs, device, stream):
 # ncu capture of it (dram__bytes_read.sum + dram__bytes_write.sum; the summary
 # is kept with the other ncu summaries).  None whenever the kernel has changed
 # since that capture.
-DENSE_TC_TRAFFIC_BYTES = 273.977600e6 + 3.830528e6
+DENSE_TC_TRAFFIC_BYTES = 273.977600e6 + 3.698944e6
 
 
 def algorithmic_bytes_dense_product():
@@ -171,9 +174,14 @@ def algorithmic_bytes_dense_product():
 
 
 # --------------------------------------------------------------------------- CPU baseline (oracle)
-def oracle_sample(seconds: float):
+ERR_CHECKPOINTS = (1, 10, 100, 200)
+
+
+def oracle_sample(seconds: float, record: dict = None):
     """Time the float64 oracle's low-rank MEG iterations (subspace-iteration
-    eigensolver) on one instance of the workload, for about `seconds`."""
+    eigensolver) on one instance of the workload, for about `seconds` (at most
+    200 iterations).  `record` (a dict) receives the oracle's iterate and
+    Ritz values at the checkpoints reached, for the error report."""
     import synth
     from oracle import meg
     prob = synth.dense_quadratic(N, R, seed=SEED0, sigma=1e-5, storage="bf16")
@@ -186,6 +194,8 @@ def oracle_sample(seconds: float):
         X, info, W = meg.lowrank_step(X, obj, iters + 1, 1.0, meg.eps_schedule(iters + 1), method="subspace",
                                       k=R + P, W0=W)
         iters += 1
+        if record is not None and iters in ERR_CHECKPOINTS:
+            record[iters] = ((X.V.copy(), X.mu.copy(), float(X.s)), info.sig[:R].copy())
         el = time.perf_counter() - t0
         if el >= seconds or iters >= 200:
             break
@@ -195,6 +205,58 @@ def oracle_sample(seconds: float):
     except Exception:
         cores = os.cpu_count() or 1
     return iters / el, cores, iters, el
+
+
+def mode_errors(device, stream, record: dict):
+    """Error of each precision mode against the float64 oracle on the
+    oracle-sample instance (seed 1001): the GPU solve runs the same
+    iterations through the C ABI in MEG_FP64 (subspace iteration, q = 3),
+    MEG_FP32 (float32 data, the benchmark's eigensolver, p and q) and
+    MEG_MIXED_BF16 (the benchmarked mode); relative Frobenius error of X_t,
+    largest relative error of sigma_1..r and relative error of f(X_t) at each
+    checkpoint the oracle sample reached."""
+    import torch
+    import synth
+    from paper_2012_10469_gb300 import binding as B
+    prob = synth.dense_quadratic(N, R, seed=SEED0, sigma=1e-5, storage="bf16")
+
+    def dense(V, mu, sv):                 # X = V diag(mu - s) V^T + s I
+        X = (V * (mu - sv)) @ V.T
+        X[np.diag_indices_from(X)] += sv
+        return X
+
+    def fval(X):
+        D = X - prob.M
+        return 0.5 * float(np.sum(D * D))
+
+    out = {}
+    modes = (("fp64", B.MEG_FP64, 3, 0, np.float64), ("fp32", B.MEG_FP32, Q, EIG, np.float32),
+             ("bf16", B.MEG_MIXED_BF16, Q, EIG, None))
+    for name, prec, q, eig, dt in modes:
+        if dt is None:
+            data = torch.from_numpy(np.ascontiguousarray(prob.bits().view(np.int16))).to(device)
+        else:
+            data = torch.from_numpy(np.ascontiguousarray(prob.M.astype(dt))).to(device)
+        s = B.Solve(N, R, p=P, q=q, precision=prec, eta=1.0, seed=SEED0, stream=stream, V0=prob.U, lam0=prob.w,
+                    eigensolver=eig)
+        s.meg_set_objective(B.MEG_DENSE_QUAD, dense=data)
+        rows, t = {}, 0
+        for cp in sorted(record):
+            s.meg_step(cp - t)
+            t = cp
+            Xg = dense(*s.meg_get_iterate())
+            (Vo, muo, so_), sig_o = record[cp]
+            Xo = dense(Vo, muo, so_)
+            sig, _ = s.meg_get_ritz()
+            fo = fval(Xo)
+            rows[str(cp)] = {"x": float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)),
+                             "sigma": float(np.max(np.abs(sig[:R] - sig_o) / np.abs(sig_o))),
+                             "f": abs(fval(Xg) - fo) / abs(fo)}
+        s.meg_destroy()
+        out[name] = {"eigensolver": EIG_NAME[eig], "q": q, "p": P, "checkpoints": rows}
+    out["what"] = ("relative Frobenius error of X_t, max relative error of sigma_1..r, relative error of f(X_t), "
+                   "against the float64 oracle (subspace eigensolver to a 1e-12 residual), n=4096 seed 1001")
+    return out
 
 
 # --------------------------------------------------------------------------- plain FP32 torch form
@@ -211,7 +273,12 @@ def torch_fp32_form(prob, device, iters: int):
     s = eps0 / N
     W, _ = torch.linalg.qr(torch.cat([V, torch.randn(N, P, generator=g).to(device)], 1))
     torch.linalg.eigh(W.T @ W)          # load cuSOLVER before timing
-    gnorm = 0.05
+    # the library's shift bound: 1.25 sqrt(2 f) with f from the factors
+    frod2 = float((M.double() ** 2).sum())
+    trm = float(torch.trace(M.double()))
+    X0 = (V * (mu - s)) @ V.T
+    f0 = 0.5 * float(((X0 + s * torch.eye(N, device=device) - M) ** 2).sum())
+    gnorm = 1.25 * math.sqrt(2.0 * max(f0, 0.0))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -221,8 +288,32 @@ def torch_fp32_form(prob, device, iters: int):
         d = torch.log(mu) - logs - (mu - s)
         c0 = logs - s
         shift = min(logs, float(torch.log(mu).min())) - gnorm
+        if EIG == 1:
+            # block Krylov: Rayleigh-Ritz on [W, orth(A W - W (W^T A W))], next block = top-k Ritz vectors
+            Y1 = M @ W
+            Z1 = V @ (d[:, None] * (V.T @ W)) + (c0 - shift) * W + Y1
+            Zp = Z1 - W @ (W.T @ Z1)
+            Zp = Zp - W @ (W.T @ Zp)        # second Gram-Schmidt pass: Zp is small, the first leaves u |Z1| along W
+            W1, _ = torch.linalg.qr(Zp)
+            Y2 = M @ W1
+            Z2 = V @ (d[:, None] * (V.T @ W1)) + (c0 - shift) * W1 + Y2
+            Bk = torch.cat([W, W1], 1)
+            H = Bk.T @ torch.cat([Z1, Z2], 1)
+            th, Qm = torch.linalg.eigh(0.5 * (H + H.T))
+            th, Qm = th.flip(0), Qm.flip(1)
+            sig = th + shift
+            mu = (1 - eps) * torch.exp(sig[:R] - torch.logsumexp(sig[:R], 0))
+            s = eps / (N - R)
+            pdg = torch.einsum("ai,ab,bi->i", Qm[:, :R], Bk.T @ torch.cat([Y1, Y2], 1), Qm[:, :R])
+            xd = float(((mu - s) * pdg).sum()) + s * trm
+            x2 = float((mu * mu).sum()) + (N - R) * s * s
+            gnorm = 1.25 * math.sqrt(2.0 * max(0.5 * x2 - xd + 0.5 * frod2, 0.0))
+            V = Bk @ Qm[:, :R]
+            W = Bk @ Qm[:, :k]
+            continue
         for j in range(Q):
-            Z = V @ (d[:, None] * (V.T @ W)) + (c0 - shift) * W + M @ W
+            Y = M @ W
+            Z = V @ (d[:, None] * (V.T @ W)) + (c0 - shift) * W + Y
             if j < Q - 1:
                 W, _ = torch.linalg.qr(Z)
         H = W.T @ Z
@@ -232,6 +323,11 @@ def torch_fp32_form(prob, device, iters: int):
         lse = torch.logsumexp(sig[:R], 0)
         mu = (1 - eps) * torch.exp(sig[:R] - lse)
         s = eps / (N - R)
+        # f(X_{t+1}) from the factors: v_i^T M v_i = (Q^T W^T Y Q)_ii
+        pdg = torch.einsum("ai,ab,bi->i", Qm[:, :R], W.T @ Y, Qm[:, :R])
+        xd = float(((mu - s) * pdg).sum()) + s * trm
+        x2 = float((mu * mu).sum()) + (N - R) * s * s
+        gnorm = 1.25 * math.sqrt(2.0 * max(0.5 * x2 - xd + 0.5 * frod2, 0.0))
         V = W @ Qm[:, :R]
         W, _ = torch.linalg.qr(Z @ Qm)
     e1.record()
@@ -485,6 +581,14 @@ def run_gpu(args):
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # the sampler reads the clocks every 200 ms: the same iterations run for
+        # about 2 s (untimed, the warm state continues) so that it sees this load,
+        # then the timed region follows inside the same sampling window
+        t_soak = time.perf_counter()
+        while time.perf_counter() - t_soak < 2.0:
+            group.meg_group_step(200)
+            stream.synchronize()
+        torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("meg_timed")
         e0.record(stream)
         group.meg_group_step(args.steps)
@@ -494,6 +598,8 @@ def run_gpu(args):
     barrier()
     ms = e0.elapsed_time(e1)
     clocks = clk.summary()
+    clocks["window"] = "2 s of the same grouped iterations directly before the timed region, and the timed region"
+
     ms = max_over_ranks(ms, device)
     value = ws * BATCH * args.steps / (ms / 1e3)
 
@@ -533,7 +639,8 @@ def run_gpu(args):
         try:
             torch_fp32_form(probs[0], device, 2)
             fp32_form = {"value": torch_fp32_form(probs[0], device, 30), "unit": "iters/s",
-                         "what": "same iteration in plain float32 torch ops, one solve, no graphs"}
+                         "what": "same iteration (eigensolver, p, q, shift bound) in plain float32 torch ops, one "
+                                 "solve, no graphs"}
         except Exception as ex:  # reported, never fatal
             fp32_form = {"error": repr(ex)[:200]}
         single = None
@@ -545,7 +652,16 @@ def run_gpu(args):
             others = other_kernel_rooflines(device, stream.cuda_stream, hbm_peak)
         except Exception as ex:  # reported, never fatal
             others = {"error": repr(ex)[:300]}
-        cpu_rate, cores, it, el = oracle_sample(args.cpu_seconds)
+        record = {}
+        cpu_rate, cores, it, el = oracle_sample(args.cpu_seconds, record)
+        try:
+            errors = mode_errors(device, stream.cuda_stream, record)
+        except Exception as ex:  # reported, never fatal
+            errors = {"error": repr(ex)[:300]}
+        try:
+            fp32_arm = fp32_data_arm(device, stream.cuda_stream, hbm_peak, args.steps)
+        except Exception as ex:  # reported, never fatal
+            fp32_arm = {"error": repr(ex)[:300]}
         serving = None
         if args.serve_requests > 0:
             try:
@@ -565,16 +681,20 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": f"dense quadratic n={N} r={R} k={R + P} q={Q}, {BATCH} independent "
-                                   f"instances per step (grouped kernels, CUDA graph), bf16 data, "
-                                   f"float32 subspace (one CholeskyQR pass per product, factor refined in Gram space), "
-                                   f"float32 k x k island with double-word refinement, "
-                                   f"X_0 = planted point",
+            "config": {"workload": f"dense quadratic n={N} r={R} k={R + P} q={Q} ({EIG_NAME[EIG]} eigensolver), "
+                                   f"{BATCH} independent instances per step (grouped kernels, CUDA graph), bf16 data, "
+                                   f"tcgen05 product, float32 subspace blocks (CholeskyQR with a factor refined in Gram "
+                                   f"space), float32 k x k island with double-word refinement, X_0 = planted point",
                        "autotune": tuned,
                        "global_batch": ws * BATCH, "l2": "inputs larger than L2 (268 MB bf16 per rank)",
                        "parallelism": f"replicas x{ws}"},
             "clocks": clocks,
-            "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "what": "per step: the batch's bf16 data copied from pinned host memory into the device tensors "
+                            "the solves borrow (torch copy_ on the solves' stream), one meg_group_step, then "
+                            "meg_certificate and meg_get_ritz of every solve (host read-back)"},
+            "errors": errors,
+            "fp32_data_arm": fp32_arm,
             "gpu_launches": kps * args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": DENSE_TC_TRAFFIC_BYTES,
@@ -651,6 +771,44 @@ def other_kernel_rooflines(device, stream, hbm_peak):
     return out
 
 
+def fp32_data_arm(device, stream, hbm_peak, steps):
+    """The same batch with float32 data (MEG_FP32: the product on CUDA cores,
+    k_dense, 537 MB of data per step) with the benchmark's eigensolver, p and
+    q: iterations/s and the product's fraction of the HBM copy bandwidth."""
+    import torch
+    import synth
+    from paper_2012_10469_gb300 import binding as B
+    probs = [synth.dense_quadratic(N, R, seed=SEED0 + i, sigma=1e-5, storage="bf16") for i in range(BATCH)]
+    solves, keep = [], []
+    for i, prob in enumerate(probs):
+        M32 = torch.from_numpy(np.ascontiguousarray(prob.M.astype(np.float32))).to(device)
+        s = B.Solve(N, R, p=P, q=Q, precision=B.MEG_FP32, eta=1.0, seed=SEED0 + i, stream=stream,
+                    V0=prob.U, lam0=prob.w, eigensolver=EIG)
+        s.meg_set_objective(B.MEG_DENSE_QUAD, dense=M32)
+        solves.append(s)
+        keep.append(M32)
+    g = B.Group(solves, stream=stream)
+    g.meg_group_step(20)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.ExternalStream(stream)
+    e0.record(st)
+    g.meg_group_step(steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prod_ms = g.meg_group_time_product(20)
+    k = R + P
+    alg = BATCH * (N * N * 4 + 2 * N * k * 4)
+    g.meg_group_destroy()
+    for s in solves:
+        s.meg_destroy()
+    return {"value": BATCH / (ms / 1e3), "unit": "iters/s", "ms_per_step": ms, "product_ms": prod_ms,
+            "product_GBs": alg / (prod_ms / 1e3) / 1e9, "product_frac": alg / (prod_ms / 1e3) / 1e9 / hbm_peak,
+            "what": "8 x n=4096 with float32 data (the same bf16-valued matrices), MEG_FP32: float32 CUDA-core "
+                    "product k_dense, same eigensolver and (p, q) as the bf16 arm"}
+
+
 def single_solve_rate(prob, device, iters: int = 200):
     """One instance alone (its 33.5 MB of data stays in L2): iterations/s."""
     import torch
@@ -658,7 +816,7 @@ def single_solve_rate(prob, device, iters: int = 200):
     stream = torch.cuda.Stream(device)
     bits = torch.from_numpy(np.ascontiguousarray(prob.bits().view(np.int16))).to(device)
     s = B.Solve(N, R, p=P, q=Q, precision=B.MEG_MIXED_BF16, eta=1.0, seed=SEED0, stream=stream.cuda_stream,
-                V0=prob.U, lam0=prob.w)
+                V0=prob.U, lam0=prob.w, eigensolver=EIG)
     s.meg_set_objective(B.MEG_DENSE_QUAD, dense=bits)
     s.meg_step(20)
     stream.synchronize()

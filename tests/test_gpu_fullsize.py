@@ -38,8 +38,8 @@ def _row(t, s, X, info, obj, f1):
                 eps=info.eps)
 
 
-# the benchmark's autotuner settings (p, q are chosen by meg_autotune on the first instance)
-AUTOTUNE = dict(q_max=4, p_cand=(4, 6, 8, 12, 16), pilot_iters=20, horizon=500, tol_x=1e-5)
+# the benchmark's autotuner settings (eigensolver, p, q are chosen by meg_autotune on the first instance)
+AUTOTUNE = dict(q_max=4, p_cand=(2, 4, 6, 8, 12, 16), pilot_iters=20, horizon=500, tol_x=1e-5, krylov=True)
 
 
 def test_config1_full_batch_as_benchmarked():
@@ -49,12 +49,12 @@ def test_config1_full_batch_as_benchmarked():
     N, R = 4096, 10
     probs = [synth.dense_quadratic(N, R, seed=1001 + i, sigma=1e-5, storage="bf16") for i in range(8)]
     stream = torch.cuda.current_stream().cuda_stream
-    P, Q, _, ok, _eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, probs[0].U, probs[0].w,
-                                 dense=to_device_dense(probs[0], B.MEG_MIXED_BF16), seed=1001, stream=stream,
-                                 **AUTOTUNE)
+    P, Q, _, ok, eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, probs[0].U, probs[0].w,
+                                      dense=to_device_dense(probs[0], B.MEG_MIXED_BF16), seed=1001, stream=stream,
+                                      **AUTOTUNE)
     assert ok
     solves = [make_gpu_solve("dense_quadratic", p, R, P, Q, B.MEG_MIXED_BF16, 1.0, 1001 + i,
-                             V0=p.U, lam0=p.w) for i, p in enumerate(probs)]
+                             V0=p.U, lam0=p.w, eigensolver=eig) for i, p in enumerate(probs)]
     for s in solves:     # the tensor-core product is the one under test
         assert np.frombuffer(s.meg_get_state()[:64], dtype=np.int64)[7] == 1
     g = B.Group(solves, stream=stream)
@@ -77,8 +77,9 @@ def _config1_batch(B, probs, solves, g, R, P, N):
     for t in range(1, T + 1):
         g.meg_group_step(1)
         for i in sampled:
+            # need_r1: the oracle converges sigma_{r+1} as well, the bound the GPU's Ritz value must respect
             Xo[i], info, Wo[i] = meg.lowrank_step(Xo[i], objs[i], t, 1.0, meg.eps_schedule(t), method="subspace",
-                                                  k=R + P, W0=Wo[i])
+                                                  k=R + P, W0=Wo[i], need_r1=True)
             if t in checkpoints:
                 rows[i].append(_row(t, solves[i], Xo[i], info, objs[i], f1[i]))
     for i in sampled:

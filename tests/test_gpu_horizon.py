@@ -49,22 +49,27 @@ def _report(name, rows):
               f"f/f_t {e['f_rel_ft']:.2e}  f/f_1 {e['f_rel_f1']:.2e}")
 
 
-def test_config1_batch_to_the_horizon():
-    """n = 4096, r = 10, the benchmark's batch and (p, q).  f* > 0 here (the
-    noise puts M outside the spectrahedron), so f is compared relative to
-    f(X_t) itself."""
+@pytest.mark.parametrize("scheme", ["benchmarked", "subspace_q3"])
+def test_config1_batch_to_the_horizon(scheme):
+    """n = 4096, r = 10, the benchmark's batch: with the eigensolver, p and q
+    the benchmark's autotuner chooses, and with subspace iteration at
+    (p, q) = (4, 3).  f* > 0 here (the noise puts M outside the
+    spectrahedron), so f is compared relative to f(X_t) itself."""
     import torch
     from paper_2012_10469_gb300 import binding as B
     from test_gpu_fullsize import AUTOTUNE
     N, R = 4096, 10
     probs = [synth.dense_quadratic(N, R, seed=1001 + i, sigma=1e-5, storage="bf16") for i in range(8)]
     stream = torch.cuda.current_stream().cuda_stream
-    P, Q, _, ok, _eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, probs[0].U, probs[0].w,
-                                 dense=to_device_dense(probs[0], B.MEG_MIXED_BF16), seed=1001, stream=stream,
-                                 **AUTOTUNE)
-    assert ok
+    if scheme == "benchmarked":
+        P, Q, _, ok, eig = B.meg_autotune(N, R, B.MEG_MIXED_BF16, B.MEG_DENSE_QUAD, probs[0].U, probs[0].w,
+                                          dense=to_device_dense(probs[0], B.MEG_MIXED_BF16), seed=1001,
+                                          stream=stream, **AUTOTUNE)
+        assert ok
+    else:
+        P, Q, eig = 4, 3, B.MEG_EIG_SUBSPACE
     solves = [make_gpu_solve("dense_quadratic", p, R, P, Q, B.MEG_MIXED_BF16, 1.0, 1001 + i,
-                             V0=p.U, lam0=p.w) for i, p in enumerate(probs)]
+                             V0=p.U, lam0=p.w, eigensolver=eig) for i, p in enumerate(probs)]
     g = B.Group(solves, stream=stream)
     sampled = (0, 5)
     objs = {i: oracle_objective("dense_quadratic", probs[i]) for i in sampled}
@@ -88,7 +93,7 @@ def test_config1_batch_to_the_horizon():
         for s in solves:
             s.meg_destroy()
     for i in sampled:
-        _report(f"n=4096 seed {1001 + i} (p={P}, q={Q})", rows[i])
+        _report(f"n=4096 seed {1001 + i} (eigensolver {eig}, p={P}, q={Q})", rows[i])
     for i in sampled:
         for e in rows[i]:
             assert e["trace"] <= 1e-12 and e["pos"]
