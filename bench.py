@@ -41,6 +41,17 @@ BATCH = 8
 SEED0 = 1001
 
 
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"])
+    return 1900.0
+
+
+BF16_TFLOPS = None
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -608,6 +619,8 @@ def run_gpu(args):
     # ---- the kernels after an intermediate product, each timed alone (warm)
     chain_us = group.meg_group_time_chain(20)
     hbm_peak, peak_kind = peaks()
+    global BF16_TFLOPS
+    BF16_TFLOPS = bf16_peak()
     alg = algorithmic_bytes_dense_product()
     achieved = alg / (prod_ms / 1e3) / 1e9
 
@@ -763,9 +776,17 @@ def other_kernel_rooflines(device, stream, hbm_peak):
     g = B.Group([s], stream=stream)
     ms = g.meg_group_time_product(50)
     alg = 2 * L * n * 2
-    out["minibatch_product_n2048"] = {"bound": "latency (L2-resident batch)", "ms_per_launch": ms,
+    # tensor-core work of the two passes: bf16 A times the three bf16 pieces of the
+    # float operands, [V | W] (2 k_bucket(k) columns) and S (k padded to 16 columns)
+    kb = 8 if k <= 8 else 16 if k <= 16 else 32
+    tflop = 2 * L * n * 3 * 2 * kb + 2 * n * L * 3 * ((k + 15) // 16 * 16)
+    out["minibatch_product_n2048"] = {"bound": "latency (L2-resident batch)", "engine": "tcgen05 (bf16, float pieces)",
+                                      "ms_per_launch": ms, "kernels": 3,
                                       "bytes_per_launch": alg, "achieved_GBs": alg / (ms / 1e3) / 1e9,
-                                      "flops_implicit": 4 * L * n * k, "flops_explicit_syrk": n * (n + 1) * L}
+                                      "flops_implicit": 4 * L * n * k, "flops_explicit_syrk": n * (n + 1) * L,
+                                      "tensor_flops": tflop,
+                                      "tensor_TFLOPs": tflop / (ms / 1e3) / 1e12,
+                                      "tensor_frac_of_bf16_peak": tflop / (ms / 1e3) / 1e12 / BF16_TFLOPS}
     g.meg_group_destroy()
     s.meg_destroy()
     return out

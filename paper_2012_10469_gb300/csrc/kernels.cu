@@ -670,7 +670,7 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
                 for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
             } else if (s.kind == MEG_MEAS_STOCH) {
                 const T* Ys = (const T*)s.Ys;
-                const int np = meas_chunks(s.nb_meas);                      // chunks in order
+                const int np = meas_slots(s.nb_meas, s.mtc);                // chunks in order
                 for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
             } else {
                 y = ((const T*)s.Y)[(size_t)i * k + j];
@@ -2002,6 +2002,93 @@ __device__ __forceinline__ void meas_batch_tile(const SolveDev& s, int lb, bool 
     for (int o = 4; o > 0; o >>= 1) aa += __shfl_xor_sync(0xffffffffu, aa, o);
 }
 
+// Second half of the minibatch pass, for the MB_ROWS batch rows of block lb
+// whose products Ps[row] = [a_b^T V (B columns) | a_b^T W (B columns) | ||a_b||^2]
+// are in shared memory: residuals r_b = a_b^T X a_b - y_b, ||a_b||^2, T_b =
+// a_b^T W and the indices to the solve's scratch, and the shift bound (the
+// last block of the solve combines the per-block parts in a fixed order).
+__device__ void meas_batch_tail(const SolveDev& s, int lb, bool warm, const int64_t* sidx,
+                                double (*Ps)[2 * MEG_KMAX + 1]) {
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    const int Lb = s.nb_meas, nblk = (Lb + MB_ROWS - 1) / MB_ROWS;
+    const int B = k_bucket(k);
+    double* sc = s.meas;              // [Lb] residual, [Lb] ||a||^2, [Lb x 32] T_b, [nblk] bounds
+    // T_b: one thread per (row, column)
+    for (int e = tid; e < MB_ROWS * k; e += NT) {
+        const int rr = e / k, c = e % k, b = lb * MB_ROWS + rr;
+        if (b < Lb) sc[2 * (size_t)Lb + (size_t)b * MEG_KMAX + c] = Ps[rr][B + c];
+    }
+    __shared__ double bsum;
+    static_assert(MB_ROWS == 32, "one warp per block's rows");
+    if (tid < MB_ROWS) {
+        const int b = lb * MB_ROWS + tid;
+        double contrib = 0.0;
+        if (b < Lb) {
+            const double aav = Ps[tid][2 * MEG_KMAX];
+            const double sv = warm ? 0.0 : s.sm[SM_S];
+            double q = sv * aav;
+            if (!warm)
+                for (int l = 0; l < r; ++l) q += (s.sm[SM_MU + l] - sv) * Ps[tid][l] * Ps[tid][l];
+            const double res = q - s.y[sidx[tid]];
+            sc[b] = res;
+            sc[Lb + b] = aav;
+            if (!warm) s.bidx[b] = (int)sidx[tid];
+            if (s.mtc) {
+                // S_b for the tensor-core apply pass, as floats
+                const float sr = (2.f / (float)Lb) * (float)res;
+                for (int c = 0; c < k; ++c) s.mts[(size_t)b * k + c] = sr * (float)Ps[tid][B + c];
+            }
+            // Minibatch (mode 0): the spectral size of (2/L) sum r_b a_b a_b^T is
+            // estimated as for a weighted Wishart matrix,
+            //   (2/L) rms_b(|r_b| ||a_b||^2) (1 + sqrt(L/n))^2.
+            // It only sets the shift c, whose job is to centre the bulk of M_t near
+            // log s: the top-r eigenvalues sit log(mu_r / s) (about 10) above it, far
+            // beyond the gradient's spread, so a direction the estimate misses (one
+            // large residual) only converges more slowly.  Rayleigh-Ritz is exact.
+            // Warm start (mode 1, r_b = -y_b): lambda_min(-grad f(0)) >= -(2/m) sum_{y<0} |y| ||a||^2.
+            contrib = warm ? (res > 0.0 ? res * aav : 0.0) : (res * aav) * (res * aav);
+        }
+        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+        if (tid == 0) bsum = contrib;
+    }
+    __syncthreads();
+    __shared__ int am_last;
+    if (tid == 0) {
+        const double v = bsum;
+        sc[(size_t)Lb * (2 + MEG_KMAX) + lb] = v;
+        __threadfence();
+        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
+        am_last = (atomicAdd(c, 1u) == (unsigned)(nblk - 1));
+        if (am_last) *c = 0u;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    // last block: combine the per-block bounds (fixed order per thread, then a fixed tree)
+    __shared__ double red[NT];
+    const double* bp = sc + (size_t)Lb * (2 + MEG_KMAX);
+    double v = 0.0;
+    for (int q2 = tid; q2 < nblk; q2 += NT) v += __ldcg(bp + q2);
+    red[tid] = v;
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+        if (tid < h) red[tid] = red[tid] + red[tid + h];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        // an estimate that only centres the shift: float arithmetic (a float64
+        // square root or division costs thousands of cycles on GB300)
+        const float sum = (float)red[0], fL = (float)Lb;
+        float bound;
+        if (warm) {
+            bound = sum * (2.f / fL);
+        } else {
+            const float f = 1.f + sqrtf(fL / (float)n);
+            bound = (2.f / fL) * sqrtf(sum / fL) * f * f;
+        }
+        s.sm[SM_RESID_BOUND] = (double)bound;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) {
     pdl_wait();
@@ -2010,7 +2097,7 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
     const SolveDev& s = sds[si];
     const int lb = blockIdx.x - s.off[PK_MEAS];
     const int Lb = s.nb_meas, nblk = (Lb + MB_ROWS - 1) / MB_ROWS;
-    if (lb < 0 || lb >= nblk) return;
+    if (lb < 0 || lb >= nblk || s.mtc) return;              // tensor-core members: k_meas_tc_batch
     const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
     const bool warm = (s.mode == 1);
     __shared__ int64_t sidx[MB_ROWS];
@@ -2056,73 +2143,59 @@ __global__ void __launch_bounds__(NT) k_meas_batch(const SolveDev* sds, int ns) 
         }
     }
     __syncthreads();
-    const int B = k_bucket(k);
-    double* sc = s.meas;              // [Lb] residual, [Lb] ||a||^2, [Lb x 32] T_b, [nblk] bounds
-    // T_b: one thread per (row, column)
-    for (int e = tid; e < MB_ROWS * k; e += NT) {
-        const int rr = e / k, c = e % k, b = lb * MB_ROWS + rr;
-        if (b < Lb) sc[2 * (size_t)Lb + (size_t)b * MEG_KMAX + c] = Ps[rr][B + c];
-    }
-    __shared__ double bpart[MB_ROWS];
+    meas_batch_tail(s, lb, warm, sidx, Ps);
+}
+
+// Second half of the minibatch pass of the tensor-core members: the parts of
+// the batch pass (k_meas_tc_batch: 2B products and ||a_b||^2 per row and part)
+// are added in part order, then meas_batch_tail as for the CUDA-core pass.
+__global__ void __launch_bounds__(NT) k_meas_finish(const SolveDev* sds, int ns) {
+    pdl_wait();
+    pdl_trigger();
+    const int si = find_solve(sds, ns, PK_MEAS, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_MEAS];
+    const int Lb = s.nb_meas, nblk = (Lb + MB_ROWS - 1) / MB_ROWS;
+    if (lb < 0 || lb >= nblk || !s.mtc || s.kind != MEG_MEAS_STOCH) return;
+    const int tid = threadIdx.x;
+    const bool warm = (s.mode == 1);
+    const int B = k_bucket(s.k), NC = 2 * B, KS = meas_ks(Lb, s.n);
+    __shared__ int64_t sidx[MB_ROWS];
+    __shared__ double Ps[MB_ROWS][2 * MEG_KMAX + 1];
     if (tid < MB_ROWS) {
         const int b = lb * MB_ROWS + tid;
-        double contrib = 0.0;
+        int64_t idx = 0;
+        if (b < Lb)
+            idx = warm ? (int64_t)b
+                       : (int64_t)(splitmix64(s.seed + ((uint64_t)s.sm[SM_T] * (uint64_t)s.L + (uint64_t)b + 1ull) *
+                                                           0x9E3779B97F4A7C15ull) %
+                                   (uint64_t)s.m);
+        sidx[tid] = idx;
+    }
+    // each entry adds its KS parts in part order; the parts of an entry are
+    // contiguous ([row][column][part]): with KS a multiple of 4 they are read
+    // as 16-byte vectors, all in flight together (one L2 round trip)
+    for (int e = tid; e < MB_ROWS * (NC + 1); e += NT) {
+        const int rr = e / (NC + 1), c = e % (NC + 1), b = lb * MB_ROWS + rr;
+        float acc = 0.f;
         if (b < Lb) {
-            const double aav = Ps[tid][2 * MEG_KMAX];
-            const double sv = warm ? 0.0 : s.sm[SM_S];
-            double q = sv * aav;
-            if (!warm)
-                for (int l = 0; l < r; ++l) q += (s.sm[SM_MU + l] - sv) * Ps[tid][l] * Ps[tid][l];
-            const double res = q - s.y[sidx[tid]];
-            sc[b] = res;
-            sc[Lb + b] = aav;
-            if (!warm) s.bidx[b] = (int)sidx[tid];
-            // Minibatch (mode 0): the spectral size of (2/L) sum r_b a_b a_b^T is
-            // estimated as for a weighted Wishart matrix,
-            //   (2/L) rms_b(|r_b| ||a_b||^2) (1 + sqrt(L/n))^2.
-            // It only sets the shift c, whose job is to centre the bulk of M_t near
-            // log s: the top-r eigenvalues sit log(mu_r / s) (about 10) above it, far
-            // beyond the gradient's spread, so a direction the estimate misses (one
-            // large residual) only converges more slowly.  Rayleigh-Ritz is exact.
-            // Warm start (mode 1, r_b = -y_b): lambda_min(-grad f(0)) >= -(2/m) sum_{y<0} |y| ||a||^2.
-            contrib = warm ? (res > 0.0 ? res * aav : 0.0) : (res * aav) * (res * aav);
+            const float* p0 = s.mtp + ((size_t)b * (NC + 1) + c) * KS;
+            if ((KS & 3) == 0) {
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (4 * u < KS) v[u] = __ldcg((const float4*)p0 + u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (4 * u < KS) acc = (((acc + v[u].x) + v[u].y) + v[u].z) + v[u].w;
+            } else {
+                for (int p = 0; p < KS; ++p) acc += __ldcg(p0 + p);
+            }
         }
-        bpart[tid] = contrib;
+        Ps[rr][c == NC ? 2 * MEG_KMAX : c] = (double)acc;
     }
     __syncthreads();
-    __shared__ int am_last;
-    if (tid == 0) {
-        double v = 0.0;
-        for (int w = 0; w < MB_ROWS; ++w) v += bpart[w];
-        sc[(size_t)Lb * (2 + MEG_KMAX) + lb] = v;
-        __threadfence();
-        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
-        am_last = (atomicAdd(c, 1u) == (unsigned)(nblk - 1));
-        if (am_last) *c = 0u;
-    }
-    __syncthreads();
-    if (!am_last) return;
-    // last block: combine the per-block bounds (fixed order per thread, then a fixed tree)
-    __shared__ double red[NT];
-    const double* bp = sc + (size_t)Lb * (2 + MEG_KMAX);
-    double v = 0.0;
-    for (int q2 = tid; q2 < nblk; q2 += NT) v += __ldcg(bp + q2);
-    red[tid] = v;
-    __syncthreads();
-    for (int h = NT / 2; h > 0; h >>= 1) {
-        if (tid < h) red[tid] = red[tid] + red[tid + h];
-        __syncthreads();
-    }
-    if (tid == 0) {
-        double bound = red[0];
-        if (warm) {
-            bound *= 2.0 / (double)Lb;
-        } else {
-            const double f = 1.0 + sqrt((double)Lb / (double)n);
-            bound = 2.0 / (double)Lb * sqrt(bound / (double)Lb) * f * f;
-        }
-        s.sm[SM_RESID_BOUND] = bound;
-    }
+    meas_batch_tail(s, lb, warm, sidx, Ps);
 }
 
 // Y = (2/Lb) sum_b r_b a_b (a_b^T W): block = MA_ROWS rows of Y times one chunk
@@ -2141,7 +2214,7 @@ __global__ void __launch_bounds__(NT) k_meas_apply(const SolveDev* sds, int ns) 
     const int n = s.n, k = s.k, tid = threadIdx.x;
     const int Lb = s.nb_meas, nch = meas_chunks(Lb);
     const int ntile = (n + MA_ROWS - 1) / MA_ROWS;
-    if (lb < 0 || lb >= ntile * nch || s.kind != MEG_MEAS_STOCH) return;
+    if (lb < 0 || lb >= ntile * nch || s.kind != MEG_MEAS_STOCH || s.mtc) return;
     const int tile = lb % ntile, ch = lb / ntile;
     const int b_lo = (int)((int64_t)ch * Lb / nch), b_hi = (int)((int64_t)(ch + 1) * Lb / nch);
     const bool warm = (s.mode == 1);
@@ -2427,6 +2500,7 @@ cudaError_t init_kernel_attributes() {
     if ((e = set_smem(k_orth_kry, orth_kry_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_kry_proj, kry_proj_smem())) != cudaSuccess) return e;
     if ((e = set_smem(k_objective<float>, OBJ_SMEM_MAX)) != cudaSuccess) return e;
+    if ((e = meas_tc_init()) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -2457,14 +2531,23 @@ cudaError_t launch_csr(const GroupLaunch& g) {
 cudaError_t launch_meas_batch(const GroupLaunch& g) {
     const dim3 grid(g.blocks[PK_MEAS]), blk(NT);
     if (g.prec == MEG_FP64) return launch_k(k_meas_batch<double>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
-    return launch_k(k_meas_batch<float>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
+    cudaError_t e = cudaSuccess;
+    if (g.meas_tc) {         // tensor-core members: the batch pass, then its finish
+        if ((e = launch_meas_tc_batch(g)) != cudaSuccess) return e;
+        if ((e = launch_k(k_meas_finish, grid, blk, 0, g.stream, 1, g.d_solves, g.ns)) != cudaSuccess) return e;
+    }
+    if (g.meas_plain) e = launch_k(k_meas_batch<float>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
+    return e;
 }
 
 cudaError_t launch_meas_apply(const GroupLaunch& g) {
     if (g.blocks[PK_MEAS] == 0) return cudaSuccess;
     const dim3 grid(g.blocks[PK_MAP]), blk(NT);
     if (g.prec == MEG_FP64) return launch_k(k_meas_apply<double>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
-    return launch_k(k_meas_apply<float>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
+    cudaError_t e = cudaSuccess;
+    if (g.meas_tc && (e = launch_meas_tc_apply(g)) != cudaSuccess) return e;
+    if (g.meas_plain) e = launch_k(k_meas_apply<float>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
+    return e;
 }
 
 // a row kernel (clusters) followed by its per-solve island kernel

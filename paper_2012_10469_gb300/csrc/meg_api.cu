@@ -114,6 +114,7 @@ struct meg_solve_s {
     double* sm = nullptr;
     double* meas = nullptr;
     int* bidx = nullptr;
+    float* mtp = nullptr;                  // partials of the tensor-core minibatch pass
     double* d_f = nullptr;
     SolveDev desc{};
     SolveDev* d_desc = nullptr;   // solo descriptor (offsets 0)
@@ -171,7 +172,10 @@ int blocks_of(const SolveDev& d, int kind) {
         case PK_DTC: return (dense && d.tc) ? (int)tc_chunks_of(d) : 0;
         case PK_MEAS: return d.kind == MEG_MEAS_STOCH ? (d.nb_meas + MB_ROWS - 1) / MB_ROWS : 0;
         case PK_MAP:
-            return d.kind == MEG_MEAS_STOCH ? (d.n + MA_ROWS - 1) / MA_ROWS * meas_chunks(d.nb_meas) : 0;
+            if (d.kind != MEG_MEAS_STOCH) return 0;
+            return (d.mtc ? (d.n + MT_BM - 1) / MT_BM : (d.n + MA_ROWS - 1) / MA_ROWS) * meas_slots(d.nb_meas, d.mtc);
+        case PK_MTB:
+            return (d.kind == MEG_MEAS_STOCH && d.mtc) ? (d.nb_meas + MT_BM - 1) / MT_BM * meas_ks(d.nb_meas, d.n) : 0;
         default: return 0;
     }
 }
@@ -184,6 +188,8 @@ GroupLaunch solo_launch(meg_solve_s* h) {
     g.prec = h->prec;
     g.stream = h->stream;
     g.meas_vr = h->desc.kind == MEG_MEAS_STOCH ? h->n * (rank_bucket(h->r) + 1) : 0;
+    g.meas_tc = h->desc.kind == MEG_MEAS_STOCH && h->desc.mtc;
+    g.meas_plain = h->desc.kind == MEG_MEAS_STOCH && !h->desc.mtc;
     if (g.blocks[PK_DTC] > 0) {
         g.tc_chunks = 1;
         g.tc_desc[0] = h->d_desc;
@@ -354,7 +360,8 @@ int64_t meg_footprint(int n, int r, int p, int precision, int kind) {
     int64_t b = 0;
     b += ts * (int64_t)n * (2 * r + 4 * k);
     if (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR) b += ts * (int64_t)std::max(dense_splits(n), 16) * n * k;
-    if (kind == MEG_MEAS_STOCH) b += ts * (int64_t)MEAS_CHUNKS * n * k;   // (+ scratch of 8 (34 m + m/8) bytes)
+    if (kind == MEG_MEAS_STOCH) b += ts * (int64_t)MEAS_CHUNKS * n * k;   // (+ scratch of 8 (34 m + m/8) bytes and
+                                                                           //  4 (2 k_bucket(k) + 1) m tensor-core partials)
     if (precision == MEG_MIXED_BF16 && n % 8 == 0) b += 2 * (int64_t)((3 * k + 15) / 16 * 16) * ((n + 63) / 64 * 64);
     b += 4 * (nb_red + groups) * 2 * RED_MAX_ENTRIES;
     b += 4 * (groups + 3) + 8 * SM_TOTAL + 8;
@@ -576,6 +583,23 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     }
     d.meas = h->meas; d.bidx = h->bidx;
     d.nb_meas = o->kind == MEG_MEAS_STOCH ? o->L : 0;
+    // minibatch products on the tensor cores: float storage (bf16 A), rows of A
+    // 16-byte aligned (n % 8 == 0, aligned base); partials for the larger of
+    // the minibatch pass and the warm start's pass over all m measurements
+    d.mtc = 0;
+    d.mtp = nullptr;
+    d.mts = nullptr;
+    if (h->mtp) { cudaFreeAsync(h->mtp, h->stream); h->mtp = nullptr; }
+    if (o->kind == MEG_MEAS_STOCH && h->prec != MEG_FP64 && n % 8 == 0 && ((uintptr_t)o->A % 16) == 0) {
+        const size_t cols = (size_t)2 * k_bucket(k) + 1;
+        const size_t rows = std::max((size_t)meas_ks(o->L, n) * o->L, (size_t)meas_ks((int)o->m, n) * o->m);
+        const size_t srows = (size_t)std::max<int64_t>(o->L, o->m);     // S: one row per batch row
+        if (cudaMallocAsync((void**)&h->mtp, sizeof(float) * (rows * cols + srows * k), h->stream) != cudaSuccess)
+            return fail(MEG_ERR_OOM, "meg_set_objective: tensor-core partials");
+        d.mtc = 1;
+        d.mtp = h->mtp;
+        d.mts = h->mtp + rows * cols;
+    }
     meg_status st = upload_desc(h, d);
     if (st != MEG_OK) return st;
     // statistics of the data used by the objective estimate and the shift: Tr D, ||D||_F^2
@@ -650,6 +674,8 @@ meg_status meg_warm_start(meg_handle h, int products) {
     g.prec = h->prec;
     g.stream = h->stream;
     g.meas_vr = dw.kind == MEG_MEAS_STOCH ? n * (rank_bucket(r) + 1) : 0;
+    g.meas_tc = dw.kind == MEG_MEAS_STOCH && dw.mtc;
+    g.meas_plain = dw.kind == MEG_MEAS_STOCH && !dw.mtc;
     if ((st = enqueue_init_orth(g)) != MEG_OK) return st;
     if (dw.kind == MEG_CSR_QUAD) CU(launch_csr(g));   // bound max_i sum_j |M_ij| for the shift
     const bool dense = dw.kind == MEG_DENSE_QUAD || dw.kind == MEG_LINEAR;
@@ -906,7 +932,7 @@ meg_status meg_destroy(meg_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->solve_gexec) cudaGraphExecDestroy(h->solve_gexec);
     void* bufs[] = {h->V, h->Vn, h->W, h->Wp, h->Z, h->Y, h->Ys, h->Wsp, h->part, h->ctr,
-                    h->sm, h->meas, h->bidx, h->d_f, h->d_desc};
+                    h->sm, h->meas, h->bidx, h->mtp, h->d_f, h->d_desc};
     for (void* b : bufs)
         if (b) cudaFreeAsync(b, h->stream);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -1041,8 +1067,12 @@ meg_status group_create_impl(const meg_handle* solves, int count, void* stream, 
     g->gl.prec = prec;
     g->gl.stream = g->stream;
     g->gl.meas_vr = 0;
+    g->gl.meas_tc = g->gl.meas_plain = 0;
     for (auto* h : g->solves)
-        if (h->desc.kind == MEG_MEAS_STOCH) g->gl.meas_vr = std::max(g->gl.meas_vr, h->n * (rank_bucket(h->r) + 1));
+        if (h->desc.kind == MEG_MEAS_STOCH) {
+            g->gl.meas_vr = std::max(g->gl.meas_vr, h->n * (rank_bucket(h->r) + 1));
+            if (h->desc.mtc) g->gl.meas_tc = 1; else g->gl.meas_plain = 1;
+        }
     if (!tcd.empty()) {
         if (cudaMallocAsync((void**)&g->d_tc_desc, sizeof(SolveDev) * tcd.size(), g->stream) != cudaSuccess ||
             cudaMemcpyAsync(g->d_tc_desc, tcd.data(), sizeof(SolveDev) * tcd.size(), cudaMemcpyHostToDevice,
@@ -1237,7 +1267,9 @@ int meg_group_kernels_per_step(meg_group g) {
     // orth2; float storage: combine, orth); plus the begin kernel once per iteration
     const int dense = g->gl.tc_chunks + (g->gl.blocks[PK_DENSE] > 0 ? 1 : 0);
     const int csr = g->has_csr ? (g->gl.prec == MEG_FP64 ? 1 : 2) : 0;   // float modes: V cast + product
-    const int per = dense + csr + (g->has_meas ? 2 : 0) + (g->gl.prec == MEG_FP64 ? 6 : 4);
+    // minibatch: batch and apply passes (tensor cores: batch pass, its finish, apply pass)
+    const int meas = g->has_meas ? (g->gl.meas_tc ? 3 : 0) + (g->gl.meas_plain ? 2 : 0) : 0;
+    const int per = dense + csr + meas + (g->gl.prec == MEG_FP64 ? 6 : 4);
     // block Krylov: the projection pass and its factor kernel after the first product
     return g->q * per + 1 + (g->krylov ? 2 : 0);
 }

@@ -73,7 +73,8 @@ enum SmallSlot : int {
 };
 
 // Work-partition kinds (one offset table per kind in a group).
-enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_DTC = 4, PK_MAP = 5, PK_COUNT = 6 };
+enum PartKind : int { PK_RED = 0, PK_DENSE = 1, PK_CSR = 2, PK_MEAS = 3, PK_DTC = 4, PK_MAP = 5, PK_MTB = 6,
+                     PK_COUNT = 7 };
 
 // Minibatch kernels (MEAS_STOCH).  k_meas_batch: MB_ROWS batch rows per
 // block as a small tiled product [rows of A] x [V | W], MB_TILE elements of
@@ -94,6 +95,26 @@ __host__ __device__ __forceinline__ int meas_chunks(int Lb) {
     const int c = (Lb + MA_CHUNK - 1) / MA_CHUNK;
     return c < MEAS_CHUNKS ? (c > 0 ? c : 1) : MEAS_CHUNKS;
 }
+// Minibatch products on the tensor cores (meas_tc.cu), float storage: the
+// batch pass tiles the Lb gathered rows of A by 128 and splits the n-long
+// contraction into meas_ks(Lb, n) parts (for a 256-row minibatch one
+// 64-wide K chunk per CTA); its float partials, (2 B + 1) per row and part,
+// go to mtp.  The apply pass splits the batch into meas_slots partial slots
+// (64 batch rows each for a minibatch), which k_combine adds in order.
+#define MT_BM 128
+#define MT_BK 64
+__host__ __device__ __forceinline__ int meas_ks(int Lb, int n) {
+    const int mtiles = (Lb + MT_BM - 1) / MT_BM, nch = (n + MT_BK - 1) / MT_BK;
+    int ks = (64 + mtiles - 1) / mtiles;
+    if (ks > 32) ks = 32;
+    if (ks > nch) ks = nch;
+    return ks < 1 ? 1 : ks;
+}
+__host__ __device__ __forceinline__ int meas_slots(int Lb, int mtc) {
+    if (!mtc) return meas_chunks(Lb);
+    const int c = (Lb + MT_BK - 1) / MT_BK;
+    return c < MEAS_CHUNKS ? (c > 0 ? c : 1) : MEAS_CHUNKS;
+}
 
 #define RED_GROUP 16            // blocks per first-level group of a reduction
 #define ROWS_MAX 64             // rows per block of the row-reduction kernels, at most
@@ -112,6 +133,9 @@ struct SolveDev {
     int nb_csr, nb_meas; // blocks of the CSR / measurement kernels
     int tc;              // 1: dense product on tcgen05 (bf16 data, n % 8 == 0)
     int eig;             // MEG_EIG_SUBSPACE or MEG_EIG_BLOCK_KRYLOV
+    int mtc;             // 1: minibatch products on tcgen05 (bf16 A, n % 8 == 0, float storage)
+    float* mtp;          // partials of the tensor-core batch pass (meas_ks parts x rows x (2 B + 1))
+    float* mts;          // S_b = (2/Lb) r_b a_b^T W as floats (rows x k), the apply pass's operand
     int nb_tm;           // tensor-core path: 128-row tiles
     int tc_npad, tc_kpad;// Wsp: (3k padded to 16) x (n padded to 64) bf16
     int tc_G;            // tensor-core launch holding this solve: CTAs
@@ -317,6 +341,7 @@ struct GroupLaunch {
     // tensor-core dense product: chunks of at most TC_MAXG solves, each with
     // its own descriptor sub-array (PK_DTC offsets relative to the chunk)
     int meas_vr;                // largest n*(rank_bucket(r)+1) of a MEAS_STOCH member (objective staging), 0 if none
+    int meas_tc, meas_plain;    // members whose minibatch products run on the tensor cores / on CUDA cores
     int tc_chunks;
     const SolveDev* tc_desc[TC_MAX_CHUNKS];
     int tc_ns[TC_MAX_CHUNKS];
@@ -341,6 +366,10 @@ cudaError_t launch_dense(const GroupLaunch& g);
 cudaError_t launch_csr(const GroupLaunch& g);
 cudaError_t launch_meas_batch(const GroupLaunch& g);
 cudaError_t launch_meas_apply(const GroupLaunch& g);
+// tensor-core minibatch products (meas_tc.cu)
+cudaError_t launch_meas_tc_batch(const GroupLaunch& g);
+cudaError_t launch_meas_tc_apply(const GroupLaunch& g);
+cudaError_t meas_tc_init();
 cudaError_t launch_combine(const GroupLaunch& g, int phase);
 cudaError_t launch_orthonormalise(const GroupLaunch& g, int phase);
 cudaError_t launch_chain_kernel(const GroupLaunch& g, int which, int phase);

@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "../../include/meg.h"
+#include "meg_dev.cuh"
 
 namespace meg_internal {
 void set_last_error(const std::string& msg);
@@ -437,10 +438,16 @@ meg_status meg_server_submit(meg_server s, const meg_request* rq, uint64_t* id) 
     const int64_t fp = meg_footprint(n, r, rq->opt.p, rq->opt.precision, rq->kind);
     if (fp < 0) return sfail(MEG_ERR_INVALID_ARG, "meg_server_submit: sizes");
     // the objective data copied in, and for measurements the per-measurement scratch
-    // (residual, ||a||^2, a^T W) that meg_footprint cannot size without m
+    // (residual, ||a||^2, a^T W) that meg_footprint cannot size without m, and the
+    // partials of the tensor-core minibatch pass (float storage)
+    const int64_t mtp = rq->kind == MEG_MEAS_STOCH && rq->opt.precision != MEG_FP64
+                            ? 4 * (int64_t)(2 * k_bucket(r + rq->opt.p) + 1) *
+                                      std::max((int64_t)meas_ks(rq->L, n) * rq->L, (int64_t)meas_ks((int)rq->m, n) * rq->m) +
+                                  4 * (int64_t)(r + rq->opt.p) * std::max<int64_t>(rq->L, rq->m)
+                            : 0;
     int64_t data = rq->kind == MEG_MEAS_STOCH
                        ? rq->m * (int64_t)n * (int64_t)elem_bytes(rq->opt.precision) + 8 * rq->m +
-                             8 * (rq->m * 34 + rq->m / 8 + 1) + 4 * (int64_t)rq->L
+                             8 * (rq->m * 34 + rq->m / 8 + 1) + 4 * (int64_t)rq->L + mtp
                        : (int64_t)n * n * (int64_t)elem_bytes(rq->opt.precision);
     Req* q = new Req();
     q->rq = *rq;
