@@ -1765,19 +1765,19 @@ __global__ void __launch_bounds__(NT) k_dense(const SolveDev* sds, int ns) {
 // R_ij = X_ij - M_ij formed on the fly from the factors (never stored).
 // One warp per row.  Also sum of R_ij^2 (for the shift bound of the next
 // iteration), reduced deterministically through per-block partials.
-// Float rows of V and W for the sparse product of the float-storage modes,
-// padded to a multiple of 4 floats (16-byte aligned: one row is a few
-// vector loads), in the solve's scratch after the row-block maxima.
+// Float rows [V_j | W_j] for the sparse product of the float-storage modes,
+// each part padded to a multiple of 4 floats (16-byte slots: a row is
+// pad4(r)/4 + pad4(k)/4 vector loads), in the solve's scratch after the
+// row-block maxima.
 __host__ __device__ __forceinline__ int csr_pad4(int x) { return (x + 3) & ~3; }
-__device__ __forceinline__ float* csr_vf(const SolveDev& s) { return (float*)(s.meas + ((s.nb_csr + 1) & ~1)); }
-__device__ __forceinline__ float* csr_wf(const SolveDev& s) { return csr_vf(s) + (size_t)s.n * csr_pad4(s.r); }
+constexpr int CSR_CAP = 256;        // entries of a row staged at a time (per warp)
+__device__ __forceinline__ float* csr_vw(const SolveDev& s) { return (float*)(s.meas + ((s.nb_csr + 1) & ~1)); }
 
-// One row i of the sparse product, KB = k_bucket(k) >= k > r: each lane takes
-// every 32nd stored entry (i, j) of the row, forms R = X_ij - M_ij from the
-// gathered row j of V and adds R W[j][:] into its own k running sums; the
-// warp then sums the lanes' vectors.  Float storage gathers the padded float
-// rows (vector loads); float64 storage the rows of V and W themselves.
-// Returns sum_j |R_ij| (on every lane).
+// One row i of the sparse product in float64 storage, KB = k_bucket(k) >= k > r:
+// each lane takes every 32nd stored entry (i, j) of the row, forms R = X_ij -
+// M_ij from the gathered row j of V and adds R W[j][:] into its own k running
+// sums; the warp then sums the lanes' vectors.  Returns sum_j |R_ij| (on
+// every lane).
 template <typename T, int KB>
 __device__ __forceinline__ double csr_row(const SolveDev& s, int i, const double* coef, int lane) {
     const int r = s.r, k = s.k;
@@ -1798,26 +1798,7 @@ __device__ __forceinline__ double csr_row(const SolveDev& s, int i, const double
         const int j = s.col[p];
         T x = (j == i) ? sd : (T)0;
         T R;
-        if constexpr (sizeof(T) == 4) {
-            const float4* vj = (const float4*)(csr_vf(s) + (size_t)j * csr_pad4(r));
-#pragma unroll
-            for (int l4 = 0; l4 < KB / 4; ++l4)
-                if (4 * l4 < r) {
-                    const float4 v = vj[l4];
-                    x += vi[4 * l4] * v.x + vi[4 * l4 + 1] * v.y + vi[4 * l4 + 2] * v.z + vi[4 * l4 + 3] * v.w;
-                }
-            R = x - val[p];
-            const float4* wj = (const float4*)(csr_wf(s) + (size_t)j * csr_pad4(k));
-#pragma unroll
-            for (int c4 = 0; c4 < KB / 4; ++c4)
-                if (4 * c4 < k) {
-                    const float4 w = wj[c4];
-                    z[4 * c4] += R * w.x;
-                    z[4 * c4 + 1] += R * w.y;
-                    z[4 * c4 + 2] += R * w.z;
-                    z[4 * c4 + 3] += R * w.w;
-                }
-        } else {
+        {
             const T* vj = (const T*)s.V + (size_t)j * r;
 #pragma unroll
             for (int l = 0; l < KB; ++l)
@@ -1843,6 +1824,100 @@ __device__ __forceinline__ double csr_row(const SolveDev& s, int i, const double
     return rabs;
 }
 
+// One row i of the sparse product in float storage.  The warp's lanes form
+// groups of GS; a group takes one stored entry (i, j) at a time, each of its
+// lanes one 16-byte slot of the padded row [V_j | W_j] (vs slots of V, ws of
+// W), so that each lane holds a few registers and a warp keeps 32/GS entries
+// (two per group, unrolled) of gathers in flight: the product is bound by the
+// latency of these L2 gathers.  The V lanes form partial dots with their
+// slot of V_i (mu - s); the group adds them (shuffles), R = X_ij - M_ij, and
+// the W lanes add R W_j into their slot's running sums.  The groups' sums are
+// added at the end (fixed shuffle order).  Returns sum_j |R_ij| (every lane).
+template <int GS>
+__device__ __forceinline__ double csr_row_coop(const SolveDev& s, int i, const double* coef, int lane, int* scol,
+                                               float* sval) {
+    const int r = s.r, k = s.k, vs = csr_pad4(r) / 4, ws = csr_pad4(k) / 4, rw = vs + ws;
+    constexpr int NG = 32 / GS, U = 4;                       // groups per warp, entries per group and step
+    const int g = lane / GS, l = lane % GS;
+    const float4* F = (const float4*)csr_vw(s);
+    const float* val = (const float*)s.val;
+    float4 vi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (l < vs) {
+        float t[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int idx = 4 * l + c;
+            // V_il (mu_l - s) formed in float64 and rounded once
+            t[c] = idx < r ? (float)(s.V[(size_t)i * r + idx] * coef[idx]) : 0.f;
+        }
+        vi = make_float4(t[0], t[1], t[2], t[3]);
+    }
+    const float sd = (float)coef[MEG_RMAX];
+    const bool vlane = l < vs, wlane = l >= vs && l < rw;
+    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float rabs = 0.f;
+    const int b = s.rowptr[i], e = s.rowptr[i + 1];
+    // the row in pieces of CSR_CAP entries: indices and values staged in the
+    // warp's shared buffer with all loads in flight at once, then the gathers
+    // of [V_j | W_j], U per group and step (independent loads); every loop
+    // bound is warp-uniform, so the shuffles always have the whole warp
+    for (int cb = b; cb < e; cb += CSR_CAP) {
+        const int cn = min(CSR_CAP, e - cb);
+        __syncwarp();
+        for (int q = lane; q < cn; q += 32) {
+            scol[q] = s.col[cb + q];
+            sval[q] = val[cb + q];
+        }
+        __syncwarp();
+        for (int pb = 0; pb < cn; pb += U * NG) {
+            int j[U];
+            float4 f[U];
+            float x[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = pb + u * NG + g;
+                j[u] = q < cn ? scol[q] : -1;
+                f[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (j[u] >= 0 && l < rw) f[u] = F[(size_t)j[u] * rw + l];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                x[u] = vlane ? vi.x * f[u].x + vi.y * f[u].y + vi.z * f[u].z + vi.w * f[u].w : 0.f;
+#pragma unroll
+            for (int o = GS / 2; o > 0; o >>= 1)
+#pragma unroll
+                for (int u = 0; u < U; ++u) x[u] += __shfl_xor_sync(0xffffffffu, x[u], o);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int q = pb + u * NG + g;
+                if (j[u] == i) x[u] += sd;
+                const float R = j[u] >= 0 ? x[u] - sval[q] : 0.f;
+                if (wlane) {
+                    z.x += R * f[u].x; z.y += R * f[u].y; z.z += R * f[u].z; z.w += R * f[u].w;
+                }
+                if (l == 0) rabs += fabsf(R);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = GS; o < 32; o <<= 1) {
+        z.x += __shfl_xor_sync(0xffffffffu, z.x, o);
+        z.y += __shfl_xor_sync(0xffffffffu, z.y, o);
+        z.z += __shfl_xor_sync(0xffffffffu, z.z, o);
+        z.w += __shfl_xor_sync(0xffffffffu, z.w, o);
+    }
+    if (g == 0 && wlane) {
+        float* Y = (float*)s.Y + (size_t)i * k;
+        const int c0 = 4 * (l - vs);
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (c0 + c < k) Y[c0 + c] = zz[c];
+    }
+    for (int o = 16; o > 0; o >>= 1) rabs += __shfl_xor_sync(0xffffffffu, rabs, o);
+    return (double)rabs;
+}
+
 // The padded float rows of V and W for the block's rows (one pass per product).
 __global__ void __launch_bounds__(NT) k_csr_prep(const SolveDev* sds, int ns) {
     pdl_wait();
@@ -1851,18 +1926,16 @@ __global__ void __launch_bounds__(NT) k_csr_prep(const SolveDev* sds, int ns) {
     const SolveDev& s = sds[si];
     const int lb = blockIdx.x - s.off[PK_CSR];
     if (lb < 0 || lb >= s.nb_csr) return;
-    const int r = s.r, k = s.k, rs = csr_pad4(r), ks = csr_pad4(k);
+    const int r = s.r, k = s.k, rs = csr_pad4(r), ks = csr_pad4(k), w = rs + ks;
     const int row0 = lb * (NT / 32), nr = min(NT / 32, s.n - row0);
-    float* Vf = csr_vf(s);
-    float* Wf = csr_wf(s);
+    float* F = csr_vw(s);
     const float* W = (const float*)s.W;
-    for (int e = threadIdx.x; e < nr * rs; e += NT) {
-        const int q = e / rs, l = e % rs;
-        Vf[(size_t)(row0 + q) * rs + l] = l < r ? (float)s.V[(size_t)(row0 + q) * r + l] : 0.f;
-    }
-    for (int e = threadIdx.x; e < nr * ks; e += NT) {
-        const int q = e / ks, c = e % ks;
-        Wf[(size_t)(row0 + q) * ks + c] = c < k ? W[(size_t)(row0 + q) * k + c] : 0.f;
+    for (int e = threadIdx.x; e < nr * w; e += NT) {
+        const int q = e / w, c = e % w, i = row0 + q;
+        float x = 0.f;
+        if (c < rs) { if (c < r) x = (float)s.V[(size_t)i * r + c]; }
+        else if (c - rs < k) x = W[(size_t)i * k + (c - rs)];
+        F[(size_t)i * w + c] = x;
     }
 }
 
@@ -1870,7 +1943,7 @@ __global__ void __launch_bounds__(NT) k_csr_prep(const SolveDev* sds, int ns) {
 // entry is formed on the fly and never stored), one warp per row; also the
 // row abs-sums of the residual, whose maximum bounds ||P_Omega(X - M)||_2.
 template <typename T>
-__global__ void __launch_bounds__(NT, 3) k_csr(const SolveDev* sds, int ns) {
+__global__ void __launch_bounds__(NT) k_csr(const SolveDev* sds, int ns) {
     pdl_wait();
     pdl_trigger();
     const int si = find_solve(sds, ns, PK_CSR, blockIdx.x);
@@ -1888,10 +1961,20 @@ __global__ void __launch_bounds__(NT, 3) k_csr(const SolveDev* sds, int ns) {
     __syncthreads();
     double rabs = 0.0;        // sum_j |R_ij| of this row: ||P_Omega(X - M)||_2 <= max_i of it
     if (i < n) {
-        switch (k_bucket(s.k)) {
-            case 8: rabs = csr_row<T, 8>(s, i, coef, lane); break;
-            case 16: rabs = csr_row<T, 16>(s, i, coef, lane); break;
-            default: rabs = csr_row<T, 32>(s, i, coef, lane); break;
+        if constexpr (sizeof(T) == 4) {
+            __shared__ int scol[NT / 32][CSR_CAP];
+            __shared__ float sval[NT / 32][CSR_CAP];
+            // 16-byte slots of [V_j | W_j]: at most 8 -> groups of 8 lanes, else 16
+            if (csr_pad4(r) / 4 + csr_pad4(s.k) / 4 <= 8)
+                rabs = csr_row_coop<8>(s, i, coef, lane, scol[warp], sval[warp]);
+            else
+                rabs = csr_row_coop<16>(s, i, coef, lane, scol[warp], sval[warp]);
+        } else {
+            switch (k_bucket(s.k)) {
+                case 8: rabs = csr_row<T, 8>(s, i, coef, lane); break;
+                case 16: rabs = csr_row<T, 16>(s, i, coef, lane); break;
+                default: rabs = csr_row<T, 32>(s, i, coef, lane); break;
+            }
         }
     }
     if (lane == 0) wsum[warp] = rabs;
