@@ -366,7 +366,7 @@ class BilinearMeasurements:
             pa, pb = self.A @ X.V, self.B @ X.V
             q = (pa * pb) @ (X.mu - X.s) + X.s * np.einsum("ij,ij->i", self.A, self.B)
         else:
-            q = np.einsum("ij,jk,ik->i", self.A, np.asarray(X), self.B)
+            q = np.einsum("ij,ij->i", self.A @ np.asarray(X), self.B)      # (a_i^T X) . b_i
         return self.tau * q
 
     def residual(self, X) -> np.ndarray:
