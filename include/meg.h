@@ -81,7 +81,11 @@ enum {
                             Omega mirrored, grad f = P_Omega(X - M)           */
     MEG_MEAS_STOCH = 2,  /* f = (1/m) sum_i (a_i^T X a_i - y_i)^2; step t uses
                             the minibatch gradient (2/L) sum_b r_b a_b a_b^T   */
-    MEG_LINEAR = 3       /* f = <C, X>,  grad f = C                          */
+    MEG_LINEAR = 3,      /* f = <C, X>,  grad f = C                          */
+    MEG_BILINEAR = 4     /* Section 7, eq. recoveryProb, in trace-1 variables:
+                            f = 1/2 sum_i (tau a_i^T X b_i - y_i)^2,
+                            grad f = (tau/2) sum_i r_i (a_i b_i^T + b_i a_i^T),
+                            r_i = tau a_i^T X b_i - y_i (full gradient)       */
 };
 
 /*
@@ -126,6 +130,14 @@ typedef struct {
  *          val[nnz] = M_ij as double (MEG_FP64) or float (otherwise).
  *   A, y, m, L (MEAS_STOCH): A m x n row-major, double (MEG_FP64) or
  *          bfloat16 bits (otherwise); y[m] double; minibatch size L.
+ *   A, B, y, m, tau (BILINEAR): A and B m x n row-major bfloat16 bits,
+ *          y[m] double, trace scale tau > 0 (the tau-spectrahedron of the
+ *          problem is mapped to the unit one, X' = X / tau); L is ignored.
+ *          Needs MEG_FP32 or MEG_MIXED_BF16, n % 8 == 0, A and B 16-byte
+ *          aligned and 1 <= m <= 2^30 - 1 (both products run on the tensor
+ *          cores over the 2 m stacked rows [A; B]); MEG_ERR_INVALID_ARG
+ *          otherwise.
+ * Fields a kind does not use are ignored (zero them).
  */
 typedef struct {
     int kind;
@@ -138,6 +150,8 @@ typedef struct {
     const double* y;
     int64_t m;
     int L;
+    const void* B;
+    double tau;
 } meg_objective_desc;
 
 /*
@@ -171,6 +185,18 @@ meg_status meg_warm_start(meg_handle h, int products);
  * with the same results as warming each alone.  f1 (host, count values,
  * may be NULL) receives f(X_1) of each solve.  Synchronises. */
 meg_status meg_warm_start_many(const meg_handle* solves, int count, int products, void* stream, double* f1);
+
+/* meg_refine_subspace -- `products` extra subspace-iteration products of
+ * the next iteration's operator M_t - c I (Algorithm 2's eigensolver),
+ * each followed by the orthonormalisation of the block W; X_t and t are
+ * unchanged, so the next meg_step computes the same iterate from a better
+ * start block.  Meant for t = 1, where W holds V_0 and random columns
+ * (the top-r eigenvectors of M_1 can lie outside span V_0, e.g. after
+ * eq. (exp:init) gave some of its directions zero weight).  Needs the
+ * objective and X_t; a solve in a group answers MEG_ERR_STATE.
+ * products in 0..4096 (MEG_ERR_INVALID_ARG otherwise).  Synchronises the
+ * stream and reports a device error as meg_step's callers see it. */
+meg_status meg_refine_subspace(meg_handle h, int products);
 
 /* meg_step -- run `nsteps` iterations of Algorithm 2 (t -> t + nsteps),
  * enqueued on the stream without a host synchronisation. */

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmeg.so")
 MEG_OK, MEG_ERR_INVALID_ARG, MEG_ERR_OOM, MEG_ERR_CUDA, MEG_ERR_NUMERIC, MEG_ERR_NOT_CONVERGED, \
     MEG_ERR_TIMEOUT, MEG_ERR_STATE = range(8)
 MEG_FP64, MEG_FP32, MEG_MIXED_BF16 = 0, 1, 2
-MEG_DENSE_QUAD, MEG_CSR_QUAD, MEG_MEAS_STOCH, MEG_LINEAR = 0, 1, 2, 3
+MEG_DENSE_QUAD, MEG_CSR_QUAD, MEG_MEAS_STOCH, MEG_LINEAR, MEG_BILINEAR = 0, 1, 2, 3, 4
 MEG_EIG_SUBSPACE, MEG_EIG_BLOCK_KRYLOV = 0, 1
 PRECISION = {"fp64": MEG_FP64, "fp32": MEG_FP32, "bf16": MEG_MIXED_BF16}
 # slots of the small state (csrc/meg_dev.cuh, SmallSlot)
@@ -40,7 +40,8 @@ class meg_options(C.Structure):
 class meg_objective_desc(C.Structure):
     _fields_ = [("kind", C.c_int), ("dense", C.c_void_p), ("rowptr", C.c_void_p),
                 ("col", C.c_void_p), ("val", C.c_void_p), ("nnz", C.c_int64),
-                ("A", C.c_void_p), ("y", C.c_void_p), ("m", C.c_int64), ("L", C.c_int)]
+                ("A", C.c_void_p), ("y", C.c_void_p), ("m", C.c_int64), ("L", C.c_int),
+                ("B", C.c_void_p), ("tau", C.c_double)]
 
 
 class meg_autotune_options(C.Structure):
@@ -102,6 +103,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_create": (C.c_int, [_P(meg_options), _P(C.c_double), _P(C.c_double), _P(H)]),
         "meg_set_objective": (C.c_int, [H, _P(meg_objective_desc)]),
         "meg_warm_start": (C.c_int, [H, C.c_int]),
+        "meg_refine_subspace": (C.c_int, [H, C.c_int]),
         "meg_step": (C.c_int, [H, C.c_int]),
         "meg_solve": (C.c_int, [H, C.c_double, C.c_int, _P(C.c_int)]),
         "meg_set_fstar": (C.c_int, [H, C.c_double]),
@@ -201,16 +203,21 @@ class Solve:
         self.h = h
 
     # -- objective
-    def meg_set_objective(self, kind, dense=None, rowptr=None, col=None, val=None, A=None, y=None, L=0):
+    def meg_set_objective(self, kind, dense=None, rowptr=None, col=None, val=None, A=None, y=None, L=0,
+                          B=None, tau=1.0):
         """Tensors are borrowed (kept alive by this object)."""
-        self._keep = [t for t in (dense, rowptr, col, val, A, y) if t is not None]
+        self._keep = [t for t in (dense, rowptr, col, val, A, y, B) if t is not None]
         d = meg_objective_desc(kind=kind, dense=_dptr(dense), rowptr=_dptr(rowptr), col=_dptr(col),
                                val=_dptr(val), nnz=0 if col is None else int(col.numel()),
-                               A=_dptr(A), y=_dptr(y), m=0 if A is None else int(A.shape[0]), L=L)
+                               A=_dptr(A), y=_dptr(y), m=0 if A is None else int(A.shape[0]), L=L,
+                               B=_dptr(B), tau=float(tau))
         _check(load().meg_set_objective(self.h, C.byref(d)), "meg_set_objective")
 
     def meg_warm_start(self, products: int = 40):
         _check(load().meg_warm_start(self.h, products), "meg_warm_start")
+
+    def meg_refine_subspace(self, products: int):
+        _check(load().meg_refine_subspace(self.h, products), "meg_refine_subspace")
 
     def meg_step(self, nsteps: int = 1):
         _check(load().meg_step(self.h, nsteps), "meg_step")

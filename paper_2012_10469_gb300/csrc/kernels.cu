@@ -213,7 +213,7 @@ __global__ void k_begin(const SolveDev* sds, int ns) {
             sm[SM_C0] = 0.0;
             sm[SM_ALPHA] = (s.kind == MEG_DENSE_QUAD) ? 1.0 : -1.0;
             double g0;
-            if (s.kind == MEG_MEAS_STOCH) g0 = sm[SM_RESID_BOUND];
+            if (s.kind == MEG_MEAS_STOCH || s.kind == MEG_BILINEAR) g0 = sm[SM_RESID_BOUND];
             else if (s.kind == MEG_CSR_QUAD) g0 = sm[SM_RSS];
             else g0 = sqrt(sm[SM_FROD2]);
             sm[SM_SHIFT] = -1.0001 * g0 - 1e-300;
@@ -253,7 +253,24 @@ __global__ void k_begin(const SolveDev* sds, int ns) {
             case MEG_CSR_QUAD: g = sm[SM_RSS]; break;
             default: g = sm[SM_RESID_BOUND]; break;
         }
-        sm[SM_SHIFT] = lmin - eta * g - 1e-12 * fabs(lmin);
+        double c = lmin - eta * g - 1e-12 * fabs(lmin);
+        // Subspace iteration after a Rayleigh-Ritz step.  c above is a lower
+        // bound of the spectrum; the previous step's lowest Ritz value
+        // sigma_k, carried to this iterate's bulk level (sigma_k - log s moves
+        // with log s: e = log s + SM_SKREL), estimates the top of the unwanted
+        // part.  Their midpoint centres the unwanted eigenvalues of M_t - c I
+        // around zero, halving their largest magnitude, while every wanted
+        // eigenvalue (above e) stays the larger: per product the error of
+        // eigenvector i shrinks by (e - c) / (2 lambda_i - c - e) instead of
+        // (lambda_{k+1} - c) / (lambda_i - c).  The shift stays at least
+        // (sigma_1 - e) / 64 below e, so that (M_t - c I) W keeps its rank in
+        // float arithmetic when the unwanted spectrum is one narrow cluster.
+        const double e = logs + sm[SM_SKREL], s1 = sm[SM_SIGMA];
+        if (s.eig == MEG_EIG_SUBSPACE && t > 1.0 && sm[SM_LAST_T] == t - 1.0 && isfinite(e) && isfinite(s1)) {
+            const double cm = fmin(0.5 * (c + e), e - (s1 - e) * (1.0 / 64.0));
+            if (cm > c) c = cm;
+        }
+        sm[SM_SHIFT] = c;
     }
 }
 
@@ -519,6 +536,7 @@ __device__ void rr_fast_f32(const SolveDev& s, double* smw, const double* S1, co
                     }
                 }
                 smw[SM_S] = s_new;
+                smw[SM_SKREL] = sig[s.k - 1] - smw[SM_LOGS];
                 smw[SM_LOGS] = log_eps - s.log_nr;
                 smw[SM_T] = t + 1.0;
             }
@@ -668,7 +686,7 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
                 const T* Ys = (const T*)s.Ys;
                 const int np = s.tc ? tc_tile_slots(s, i / 128) : s.nb_ds;   // slots in order
                 for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
-            } else if (s.kind == MEG_MEAS_STOCH) {
+            } else if (s.kind == MEG_MEAS_STOCH || s.kind == MEG_BILINEAR) {
                 const T* Ys = (const T*)s.Ys;
                 const int np = meas_slots(s.nb_meas, s.mtc);                // chunks in order
                 for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
@@ -908,6 +926,7 @@ __global__ void __launch_bounds__(NT) k_island_c(const SolveDev* sds, int ns, in
                 smw[SM_LOGMU + i] = log_1meps + (sig[i] - lse_r);
             }
             smw[SM_S] = s_new;
+            smw[SM_SKREL] = sig[s.k - 1] - smw[SM_LOGS];
             smw[SM_LOGS] = log(eps) - log((double)(n - r));
             smw[SM_T] = t + 1.0;
         }
@@ -2281,6 +2300,124 @@ __global__ void __launch_bounds__(NT) k_meas_finish(const SolveDev* sds, int ns)
     meas_batch_tail(s, lb, warm, sidx, Ps);
 }
 
+// Bilinear measurements (Section 7, eq. recoveryProb, trace-1 variables):
+// second half of the tensor-core batch pass over the stacked rows [A; B].
+// Block lb takes the MB_ROWS pairs i = MB_ROWS lb + ...; the parts of rows i
+// and m + i are added in part order, giving a_i^T [V | W], ||a_i||^2 and
+// b_i^T [V | W], ||b_i||^2.  Then
+//   r_i = tau (sum_l (mu_l - s)(a_i^T v_l)(b_i^T v_l) + s a_i^T b_i) - y_i
+//   (mode 1, the warm start's -grad f(0): r_i = -y_i),
+//   S_i = (tau/2) r_i b_i^T W,   S_{m+i} = (tau/2) r_i a_i^T W
+// for the apply pass.  a_i^T b_i is precomputed (meas[i], k_bil_prep).
+// Shift estimate: grad f = (tau/2)(A^T D B + B^T D A), D = diag(r), so
+// ||grad f|| <= tau ||A^T D B|| <= tau (||A^T |D| A|| ||B^T |D| B||)^(1/2);
+// each factor is estimated as for a weighted Wishart matrix, which gives
+//   g = (tau / n) (1 + sqrt(n/m))^2 (m sum_i r_i^2 ||a_i||^2 ||b_i||^2)^(1/2).
+// As for the minibatch estimate it only centres the shift; Rayleigh-Ritz is
+// exact.
+__global__ void __launch_bounds__(NT) k_bil_finish(const SolveDev* sds, int ns) {
+    pdl_wait();
+    pdl_trigger();
+    const int si = find_solve(sds, ns, PK_MEAS, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_MEAS];
+    const int64_t m = s.m;
+    const int nblk = (int)((m + MB_ROWS - 1) / MB_ROWS);
+    if (lb < 0 || lb >= nblk || s.kind != MEG_BILINEAR) return;
+    const int tid = threadIdx.x, n = s.n, k = s.k, r = s.r;
+    const bool warm = (s.mode == 1);
+    const int Lb = s.nb_meas, B = k_bucket(k), NC = 2 * B, KS = meas_ks(Lb, n);
+    __shared__ float Pp[2][MB_ROWS][2 * MEG_KMAX + 1];     // [a or b][pair][column], ||.||^2 last
+    __shared__ float rs[MB_ROWS];
+    for (int e = tid; e < 2 * MB_ROWS * (NC + 1); e += NT) {
+        const int side = e / (MB_ROWS * (NC + 1)), rem = e % (MB_ROWS * (NC + 1));
+        const int rr = rem / (NC + 1), c = rem % (NC + 1);
+        const int64_t i = (int64_t)lb * MB_ROWS + rr;
+        float acc = 0.f;
+        if (i < m) {
+            const float* p0 = s.mtp + ((size_t)(side ? m + i : i) * (NC + 1) + c) * KS;
+            for (int p = 0; p < KS; ++p) acc += __ldcg(p0 + p);
+        }
+        Pp[side][rr][c == NC ? 2 * MEG_KMAX : c] = acc;
+    }
+    __syncthreads();
+    double* sc = s.meas;               // [m] a_i^T b_i, then one bound partial per block
+    __shared__ double bsum;
+    if (tid < MB_ROWS) {
+        const int64_t i = (int64_t)lb * MB_ROWS + tid;
+        double contrib = 0.0;
+        float sr = 0.f;
+        if (i < m) {
+            double q = 0.0;
+            if (!warm) {
+                // float terms: each product a_i^T v_l is a float-accurate sum
+                const double sv = s.sm[SM_S];
+                float qf = 0.f;
+                for (int l = 0; l < r; ++l)
+                    qf = fmaf((float)(s.sm[SM_MU + l] - sv), Pp[0][tid][l] * Pp[1][tid][l], qf);
+                q = s.tau * ((double)qf + sv * sc[i]);
+            }
+            const double res = q - s.y[i];
+            sr = (float)(0.5 * s.tau * res);
+            const float na = Pp[0][tid][2 * MEG_KMAX], nb = Pp[1][tid][2 * MEG_KMAX], rf = (float)res;
+            contrib = (double)(rf * rf * na * nb);
+        }
+        rs[tid] = sr;
+        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+        if (tid == 0) bsum = contrib;
+    }
+    __syncthreads();
+    // S rows: pair i's two rows, k values each
+    for (int e = tid; e < 2 * MB_ROWS * k; e += NT) {
+        const int side = e / (MB_ROWS * k), rem = e % (MB_ROWS * k);
+        const int rr = rem / k, c = rem % k;
+        const int64_t i = (int64_t)lb * MB_ROWS + rr;
+        if (i < m)   // row i (a_i) takes b_i^T W, row m + i (b_i) takes a_i^T W
+            s.mts[(size_t)(side ? m + i : i) * k + c] = rs[rr] * Pp[side ? 0 : 1][rr][B + c];
+    }
+    __shared__ int am_last;
+    if (tid == 0) {
+        sc[(size_t)m + lb] = bsum;
+        __threadfence();
+        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
+        am_last = (atomicAdd(c, 1u) == (unsigned)(nblk - 1));
+        if (am_last) *c = 0u;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __shared__ double red[NT];
+    const double* bp = sc + m;
+    double v = 0.0;
+    for (int q2 = tid; q2 < nblk; q2 += NT) v += __ldcg(bp + q2);
+    red[tid] = v;
+    __syncthreads();
+    for (int h = NT / 2; h > 0; h >>= 1) {
+        if (tid < h) red[tid] = red[tid] + red[tid + h];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const float fm = (float)m, fn = (float)n;
+        const float f = 1.f + sqrtf(fn / fm);
+        s.sm[SM_RESID_BOUND] = (double)((float)s.tau / fn * f * f * sqrtf(fm * (float)red[0]));
+    }
+}
+
+// c_i = a_i^T b_i of the bilinear pairs (bf16 products are exact in float;
+// sums in float64), one warp per pair, into meas[i].
+__global__ void __launch_bounds__(NT) k_bil_prep(const SolveDev* sd, int64_t m) {
+    const SolveDev& s = *sd;
+    const int n = s.n, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (NT / 32) + (threadIdx.x >> 5);
+    if (i >= m) return;
+    const unsigned short* a = (const unsigned short*)s.A + (size_t)i * n;
+    const unsigned short* b = (const unsigned short*)s.Bm + (size_t)i * n;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32)
+        acc += (double)(__uint_as_float((unsigned)a[j] << 16) * __uint_as_float((unsigned)b[j] << 16));
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) s.meas[i] = acc;
+}
+
 // Y = (2/Lb) sum_b r_b a_b (a_b^T W): block = MA_ROWS rows of Y times one chunk
 // of the batch.  Thread (row i, column group of 8) accumulates over the
 // chunk's rows; a warp reads 32 consecutive elements of a row of A per step,
@@ -2415,6 +2552,89 @@ __device__ void obj_meas_rows(const SolveDev& s, int lb, float* vsm, const doubl
     }
 }
 
+// Bilinear measurements: f = 1/2 sum_i (tau a_i^T X b_i - y_i)^2 with
+// a_i^T X b_i = sum_l (mu_l - s)(a_i^T v_l)(b_i^T v_l) + s a_i^T b_i, a_i^T b_i
+// from meas[i].  One warp per pair, 8 columns of V at a time; a_i^T v_l is a
+// double-word sum of the bf16 data times the float hi piece of v_l plus a
+// float sum with its lo piece (V staged as hi/lo floats in shared memory when
+// vsm is given, else split from the float64 V as it is read).  Adds r_i^2
+// to acc (the caller halves the total).
+template <typename A>
+__device__ void obj_bil_rows(const SolveDev& s, int lb, float* vsm, const double* coef, A& acc) {
+    const int n = s.n, r = s.r, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int RB = rank_bucket(r), rp = RB + 1;
+    if (vsm) {
+        for (int e = tid; e < n * RB; e += NT) {
+            const int j = e / RB, l = e % RB;
+            const double v = l < r ? s.V[(size_t)j * r + l] : 0.0;
+            const float h = (float)v;
+            vsm[j * rp + l] = h;
+            vsm[(size_t)n * rp + j * rp + l] = (float)(v - (double)h);
+        }
+        __syncthreads();
+    }
+    const unsigned short* Aa = (const unsigned short*)s.A;
+    const unsigned short* Bb = (const unsigned short*)s.Bm;
+    const int64_t per = (s.m + s.nb_red - 1) / s.nb_red;
+    const int64_t i0 = (int64_t)lb * per, i1 = min((int64_t)s.m, i0 + per);
+    for (int64_t i = i0 + warp; i < i1; i += NT / 32) {
+        double q = 0.0;                                     // lane 0
+        for (int l0 = 0; l0 < r; l0 += 8) {
+            dw pa[8], pb[8];
+            float la[8], lbv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { pa[u] = pb[u] = {0.f, 0.f}; la[u] = lbv[u] = 0.f; }
+            for (int j = lane; j < n; j += 32) {
+                const float a = __uint_as_float((unsigned)Aa[(size_t)i * n + j] << 16);
+                const float b = __uint_as_float((unsigned)Bb[(size_t)i * n + j] << 16);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int l = l0 + u;
+                    float vh = 0.f, vl = 0.f;
+                    if (l < r) {
+                        if (vsm) {
+                            vh = vsm[j * rp + l];
+                            vl = vsm[(size_t)n * rp + j * rp + l];
+                        } else {
+                            const double v = s.V[(size_t)j * r + l];
+                            vh = (float)v;
+                            vl = (float)(v - (double)vh);
+                        }
+                    }
+                    dot2_acc(pa[u], a, vh);
+                    la[u] = fmaf(a, vl, la[u]);
+                    dot2_acc(pb[u], b, vh);
+                    lbv[u] = fmaf(b, vl, lbv[u]);
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    dw t = {__shfl_xor_sync(0xffffffffu, pa[u].hi, o), __shfl_xor_sync(0xffffffffu, pa[u].lo, o)};
+                    dw_add(pa[u], t);
+                    t = {__shfl_xor_sync(0xffffffffu, pb[u].hi, o), __shfl_xor_sync(0xffffffffu, pb[u].lo, o)};
+                    dw_add(pb[u], t);
+                    la[u] += __shfl_xor_sync(0xffffffffu, la[u], o);
+                    lbv[u] += __shfl_xor_sync(0xffffffffu, lbv[u], o);
+                }
+            }
+            if (lane == 0)
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (l0 + u < r)
+                        q += coef[l0 + u] * (dw_value(pa[u]) + (double)la[u]) * (dw_value(pb[u]) + (double)lbv[u]);
+        }
+        if (lane == 0) {
+            q += coef[MEG_RMAX] * s.meas[i];
+            const double R = s.tau * q - s.y[i];
+            const double w = R * R;
+            const float wh = (float)w;
+            acc.add_prod(wh, 1.f);
+            acc.add_prod((float)(w - (double)wh), 1.f);
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, double* out, int vcap) {
     pdl_wait();
@@ -2460,6 +2680,12 @@ __global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, d
                     }
                 }
             }
+        }
+    } else if (s.kind == MEG_BILINEAR) {
+        // float storage only (the kind needs bf16 A and B)
+        if constexpr (sizeof(T) == 4) {
+            extern __shared__ __align__(16) unsigned char bsm[];
+            obj_bil_rows(s, lb, vcap >= 2 * n * (rank_bucket(r) + 1) ? (float*)bsm : nullptr, coef, acc);
         }
     } else if (sizeof(T) == 4 && vcap >= 2 * n * (rank_bucket(r) + 1)) {
         // measurements, bf16 A: see obj_meas_rows
@@ -2517,7 +2743,7 @@ __global__ void __launch_bounds__(NT) k_objective(const SolveDev* sds, int ns, d
     if (!red_two_level(s, lb, ent, &fin, 1)) return;
     if (tid == 0) {
         double v = dw_value(fin);
-        if (s.kind == MEG_DENSE_QUAD || s.kind == MEG_CSR_QUAD) v *= 0.5;
+        if (s.kind == MEG_DENSE_QUAD || s.kind == MEG_CSR_QUAD || s.kind == MEG_BILINEAR) v *= 0.5;
         out[si] = v;
     }
 }
@@ -2615,10 +2841,12 @@ cudaError_t launch_meas_batch(const GroupLaunch& g) {
     const dim3 grid(g.blocks[PK_MEAS]), blk(NT);
     if (g.prec == MEG_FP64) return launch_k(k_meas_batch<double>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
     cudaError_t e = cudaSuccess;
-    if (g.meas_tc) {         // tensor-core members: the batch pass, then its finish
-        if ((e = launch_meas_tc_batch(g)) != cudaSuccess) return e;
-        if ((e = launch_k(k_meas_finish, grid, blk, 0, g.stream, 1, g.d_solves, g.ns)) != cudaSuccess) return e;
-    }
+    // tensor-core members: the batch pass, then its finish (minibatch and bilinear kinds)
+    if ((g.meas_tc || g.meas_bil) && (e = launch_meas_tc_batch(g)) != cudaSuccess) return e;
+    if (g.meas_tc && (e = launch_k(k_meas_finish, grid, blk, 0, g.stream, 1, g.d_solves, g.ns)) != cudaSuccess)
+        return e;
+    if (g.meas_bil && (e = launch_k(k_bil_finish, grid, blk, 0, g.stream, 1, g.d_solves, g.ns)) != cudaSuccess)
+        return e;
     if (g.meas_plain) e = launch_k(k_meas_batch<float>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
     return e;
 }
@@ -2628,9 +2856,14 @@ cudaError_t launch_meas_apply(const GroupLaunch& g) {
     const dim3 grid(g.blocks[PK_MAP]), blk(NT);
     if (g.prec == MEG_FP64) return launch_k(k_meas_apply<double>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
     cudaError_t e = cudaSuccess;
-    if (g.meas_tc && (e = launch_meas_tc_apply(g)) != cudaSuccess) return e;
+    if ((g.meas_tc || g.meas_bil) && (e = launch_meas_tc_apply(g)) != cudaSuccess) return e;
     if (g.meas_plain) e = launch_k(k_meas_apply<float>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
     return e;
+}
+
+cudaError_t launch_bil_prep(const SolveDev* d_solve, int64_t m, cudaStream_t st) {
+    const int64_t blocks = (m + NT / 32 - 1) / (NT / 32);
+    return launch_k(k_bil_prep, dim3((unsigned)blocks), dim3(NT), 0, st, 1, d_solve, m);
 }
 
 // a row kernel (clusters) followed by its per-solve island kernel

@@ -163,19 +163,25 @@ void compute_partition(meg_solve_s* h, SolveDev& d) {
     d.nb_meas = 0;
 }
 
+bool meas_kind(int kind) { return kind == MEG_MEAS_STOCH || kind == MEG_BILINEAR; }
+
 int blocks_of(const SolveDev& d, int kind) {
     const bool dense = (d.kind == MEG_DENSE_QUAD || d.kind == MEG_LINEAR);
+    const bool bil = d.kind == MEG_BILINEAR;
     switch (kind) {
         case PK_RED: return (d.nb_red + RED_CLUSTER - 1) / RED_CLUSTER * RED_CLUSTER;
         case PK_DENSE: return (dense && !d.tc) ? d.nb_dm * d.nb_ds : 0;
         case PK_CSR: return d.kind == MEG_CSR_QUAD ? d.nb_csr : 0;
         case PK_DTC: return (dense && d.tc) ? (int)tc_chunks_of(d) : 0;
-        case PK_MEAS: return d.kind == MEG_MEAS_STOCH ? (d.nb_meas + MB_ROWS - 1) / MB_ROWS : 0;
+        // minibatch: batch rows; bilinear: pairs (its batch rows are the 2 m stacked rows)
+        case PK_MEAS:
+            if (bil) return (int)((d.m + MB_ROWS - 1) / MB_ROWS);
+            return d.kind == MEG_MEAS_STOCH ? (d.nb_meas + MB_ROWS - 1) / MB_ROWS : 0;
         case PK_MAP:
-            if (d.kind != MEG_MEAS_STOCH) return 0;
+            if (!meas_kind(d.kind)) return 0;
             return (d.mtc ? (d.n + MT_BM - 1) / MT_BM : (d.n + MA_ROWS - 1) / MA_ROWS) * meas_slots(d.nb_meas, d.mtc);
         case PK_MTB:
-            return (d.kind == MEG_MEAS_STOCH && d.mtc) ? (d.nb_meas + MT_BM - 1) / MT_BM * meas_ks(d.nb_meas, d.n) : 0;
+            return (meas_kind(d.kind) && d.mtc) ? (d.nb_meas + MT_BM - 1) / MT_BM * meas_ks(d.nb_meas, d.n) : 0;
         default: return 0;
     }
 }
@@ -187,9 +193,10 @@ GroupLaunch solo_launch(meg_solve_s* h) {
     for (int p = 0; p < PK_COUNT; ++p) g.blocks[p] = blocks_of(h->desc, p);
     g.prec = h->prec;
     g.stream = h->stream;
-    g.meas_vr = h->desc.kind == MEG_MEAS_STOCH ? h->n * (rank_bucket(h->r) + 1) : 0;
+    g.meas_vr = meas_kind(h->desc.kind) ? h->n * (rank_bucket(h->r) + 1) : 0;
     g.meas_tc = h->desc.kind == MEG_MEAS_STOCH && h->desc.mtc;
     g.meas_plain = h->desc.kind == MEG_MEAS_STOCH && !h->desc.mtc;
+    g.meas_bil = h->desc.kind == MEG_BILINEAR;
     if (g.blocks[PK_DTC] > 0) {
         g.tc_chunks = 1;
         g.tc_desc[0] = h->d_desc;
@@ -360,8 +367,10 @@ int64_t meg_footprint(int n, int r, int p, int precision, int kind) {
     int64_t b = 0;
     b += ts * (int64_t)n * (2 * r + 4 * k);
     if (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR) b += ts * (int64_t)std::max(dense_splits(n), 16) * n * k;
-    if (kind == MEG_MEAS_STOCH) b += ts * (int64_t)MEAS_CHUNKS * n * k;   // (+ scratch of 8 (34 m + m/8) bytes and
-                                                                           //  4 (2 k_bucket(k) + 1) m tensor-core partials)
+    if (kind == MEG_MEAS_STOCH || kind == MEG_BILINEAR)
+        b += ts * (int64_t)MEAS_CHUNKS * n * k;   // (+ scratch of 8 (34 m + m/8) bytes and
+                                                  //  4 (2 k_bucket(k) + 1) m tensor-core partials; bilinear:
+                                                  //  8 (m + m/32) bytes and 8 (2 k_bucket(k) + 1 + k) m)
     if (precision == MEG_MIXED_BF16 && n % 8 == 0) b += 2 * (int64_t)((3 * k + 15) / 16 * 16) * ((n + 63) / 64 * 64);
     b += 4 * (nb_red + groups) * 2 * RED_MAX_ENTRIES;
     b += 4 * (groups + 3) + 8 * SM_TOTAL + 8;
@@ -541,6 +550,16 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
         if (!o->A || !o->y || o->m < 1 || o->L < 1)
             return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: measurement arrays missing");
         if (o->m > 0x7fffffff) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: m too large");
+    } else if (o->kind == MEG_BILINEAR) {
+        if (!o->A || !o->B || !o->y || o->m < 1)
+            return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: bilinear arrays missing");
+        if (o->m > 0x3fffffff) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: m too large (2 m stacked rows)");
+        if (!(o->tau > 0.0) || !std::isfinite(o->tau))
+            return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: tau must be positive and finite");
+        // both products run on the tensor cores over 16-byte rows of bf16 data
+        if (h->prec == MEG_FP64 || n % 8 != 0 || ((uintptr_t)o->A % 16) != 0 || ((uintptr_t)o->B % 16) != 0)
+            return fail(MEG_ERR_INVALID_ARG,
+                        "meg_set_objective: bilinear kind needs float storage, n % 8 == 0 and 16-byte aligned A, B");
     } else {
         return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: unknown kind");
     }
@@ -548,6 +567,8 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     d.kind = o->kind;
     d.D = o->dense; d.rowptr = o->rowptr; d.col = o->col; d.val = o->val; d.nnz = o->nnz;
     d.A = o->A; d.y = o->y; d.m = o->m; d.L = o->L;
+    d.Bm = o->kind == MEG_BILINEAR ? o->B : nullptr;
+    d.tau = o->kind == MEG_BILINEAR ? o->tau : 1.0;
     const size_t ts = tsize(h->prec);
     const bool dense_kind = (o->kind == MEG_DENSE_QUAD || o->kind == MEG_LINEAR);
     d.tc = 0;
@@ -558,7 +579,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     } else {
         compute_partition(h, d);
     }
-    if (dense_kind || o->kind == MEG_MEAS_STOCH) {
+    if (dense_kind || meas_kind(o->kind)) {
         // partial products: K splits of the dense product, or batch chunks of the minibatch product
         const size_t slots = dense_kind ? (size_t)d.nb_ds : (size_t)MEAS_CHUNKS;
         if (h->Ys) { cudaFreeAsync(h->Ys, h->stream); h->Ys = nullptr; }
@@ -566,13 +587,15 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
             return fail(MEG_ERR_OOM, "meg_set_objective: partial products");
     }
     d.Ys = h->Ys;
-    if (o->kind == MEG_MEAS_STOCH || o->kind == MEG_CSR_QUAD) {
-        // minibatch scratch: [Lb] residuals, [Lb] ||a||^2, [Lb x 32] a^T W, one partial bound per block
+    if (meas_kind(o->kind) || o->kind == MEG_CSR_QUAD) {
+        // minibatch scratch: [Lb] residuals, [Lb] ||a||^2, [Lb x 32] a^T W, one partial bound per block;
+        // bilinear: [m] a_i^T b_i, one partial bound per block of MB_ROWS pairs
         const size_t lbm = (size_t)std::max<int64_t>(o->m, o->L);
         // CSR: one maximum per row block (rounded up to 16 bytes), then V and W as
         // float rows padded to a multiple of 4 for the sparse product
         const size_t pad4r = (size_t)((h->r + 3) & ~3), pad4k = (size_t)((k + 3) & ~3);
         size_t cnt = o->kind == MEG_MEAS_STOCH ? lbm * (2 + MEG_KMAX) + lbm / MB_ROWS + 1
+                     : o->kind == MEG_BILINEAR ? (size_t)o->m + (size_t)o->m / MB_ROWS + 1
                                                : (size_t)((d.nb_csr + 1) & ~1) + ((size_t)n * (pad4r + pad4k) + 1) / 2;
         if (h->meas) cudaFreeAsync(h->meas, h->stream);
         if (h->bidx) cudaFreeAsync(h->bidx, h->stream);
@@ -582,7 +605,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
             return fail(MEG_ERR_OOM, "meg_set_objective: scratch");
     }
     d.meas = h->meas; d.bidx = h->bidx;
-    d.nb_meas = o->kind == MEG_MEAS_STOCH ? o->L : 0;
+    d.nb_meas = o->kind == MEG_MEAS_STOCH ? o->L : o->kind == MEG_BILINEAR ? (int)(2 * o->m) : 0;
     // minibatch products on the tensor cores: float storage (bf16 A), rows of A
     // 16-byte aligned (n % 8 == 0, aligned base); partials for the larger of
     // the minibatch pass and the warm start's pass over all m measurements
@@ -590,10 +613,14 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     d.mtp = nullptr;
     d.mts = nullptr;
     if (h->mtp) { cudaFreeAsync(h->mtp, h->stream); h->mtp = nullptr; }
-    if (o->kind == MEG_MEAS_STOCH && h->prec != MEG_FP64 && n % 8 == 0 && ((uintptr_t)o->A % 16) == 0) {
+    if (o->kind == MEG_BILINEAR ||
+        (o->kind == MEG_MEAS_STOCH && h->prec != MEG_FP64 && n % 8 == 0 && ((uintptr_t)o->A % 16) == 0)) {
         const size_t cols = (size_t)2 * k_bucket(k) + 1;
-        const size_t rows = std::max((size_t)meas_ks(o->L, n) * o->L, (size_t)meas_ks((int)o->m, n) * o->m);
-        const size_t srows = (size_t)std::max<int64_t>(o->L, o->m);     // S: one row per batch row
+        const size_t rows = o->kind == MEG_BILINEAR
+                                ? (size_t)meas_ks(d.nb_meas, n) * d.nb_meas
+                                : std::max((size_t)meas_ks(o->L, n) * o->L, (size_t)meas_ks((int)o->m, n) * o->m);
+        // S: one row per batch row (bilinear: per stacked row)
+        const size_t srows = o->kind == MEG_BILINEAR ? (size_t)d.nb_meas : (size_t)std::max<int64_t>(o->L, o->m);
         if (cudaMallocAsync((void**)&h->mtp, sizeof(float) * (rows * cols + srows * k), h->stream) != cudaSuccess)
             return fail(MEG_ERR_OOM, "meg_set_objective: tensor-core partials");
         d.mtc = 1;
@@ -602,6 +629,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     }
     meg_status st = upload_desc(h, d);
     if (st != MEG_OK) return st;
+    if (o->kind == MEG_BILINEAR) CU(launch_bil_prep(h->d_desc, o->m, h->stream));   // a_i^T b_i
     // statistics of the data used by the objective estimate and the shift: Tr D, ||D||_F^2
     // (computed by the objective kernel on X = 0 and X = I/n would need two passes;
     //  the k_objective pass on a zero iterate gives 1/2 ||D||^2 directly)
@@ -673,19 +701,20 @@ meg_status meg_warm_start(meg_handle h, int products) {
     for (int p = 0; p < PK_COUNT; ++p) g.blocks[p] = blocks_of(dw, p);
     g.prec = h->prec;
     g.stream = h->stream;
-    g.meas_vr = dw.kind == MEG_MEAS_STOCH ? n * (rank_bucket(r) + 1) : 0;
+    g.meas_vr = meas_kind(dw.kind) ? n * (rank_bucket(r) + 1) : 0;
     g.meas_tc = dw.kind == MEG_MEAS_STOCH && dw.mtc;
     g.meas_plain = dw.kind == MEG_MEAS_STOCH && !dw.mtc;
+    g.meas_bil = dw.kind == MEG_BILINEAR;
     if ((st = enqueue_init_orth(g)) != MEG_OK) return st;
     if (dw.kind == MEG_CSR_QUAD) CU(launch_csr(g));   // bound max_i sum_j |M_ij| for the shift
     const bool dense = dw.kind == MEG_DENSE_QUAD || dw.kind == MEG_LINEAR;
     for (int j = 0; j < products; ++j) {
         const int phase = (j == products - 1) ? PH_FINAL : PH_ADVANCE;
-        if (dw.kind == MEG_MEAS_STOCH) CU(launch_meas_batch(g));
+        if (meas_kind(dw.kind)) CU(launch_meas_batch(g));
         if (j == 0) CU(launch_begin(g));
         if (dense) CU(launch_dense(g));
         if (dw.kind == MEG_CSR_QUAD) CU(launch_csr(g));
-        if (dw.kind == MEG_MEAS_STOCH) CU(launch_meas_apply(g));
+        if (meas_kind(dw.kind)) CU(launch_meas_apply(g));
         CU(launch_combine(g, phase));
         CU(launch_orthonormalise(g, phase));
     }
@@ -704,6 +733,27 @@ static meg_status ready(meg_handle h, const char* who) {
     return MEG_OK;
 }
 
+meg_status meg_refine_subspace(meg_handle h, int products) {
+    meg_status st = ready(h, "meg_refine_subspace");
+    if (st != MEG_OK) return st;
+    if (h->in_group) return fail(MEG_ERR_STATE, "meg_refine_subspace: solve belongs to a group");
+    if (products < 0 || products > 4096) return fail(MEG_ERR_INVALID_ARG, "meg_refine_subspace: products in 0..4096");
+    const GroupLaunch g = solo_launch(h);
+    const int kind = h->desc.kind;
+    const bool dense = kind == MEG_DENSE_QUAD || kind == MEG_LINEAR;
+    for (int j = 0; j < products; ++j) {
+        if (meas_kind(kind)) CU(launch_meas_batch(g));
+        if (j == 0) CU(launch_begin(g));
+        if (dense) CU(launch_dense(g));
+        if (kind == MEG_CSR_QUAD) CU(launch_csr(g));
+        if (meas_kind(kind)) CU(launch_meas_apply(g));
+        CU(launch_combine(g, PH_ADVANCE));
+        CU(launch_orthonormalise(g, PH_ADVANCE));
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    return check_device_status(h);
+}
+
 meg_status meg_step(meg_handle h, int nsteps) {
     meg_status st = ready(h, "meg_step");
     if (st != MEG_OK) return st;
@@ -714,7 +764,7 @@ meg_status meg_step(meg_handle h, int nsteps) {
         CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         const int kind = h->desc.kind;
         st = enqueue_iteration(solo_launch(h), kind == MEG_DENSE_QUAD || kind == MEG_LINEAR,
-                               kind == MEG_CSR_QUAD, kind == MEG_MEAS_STOCH, h->q,
+                               kind == MEG_CSR_QUAD, meas_kind(kind), h->q,
                                h->desc.eig == MEG_EIG_BLOCK_KRYLOV);
         cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
         if (st != MEG_OK) return st;
@@ -769,7 +819,7 @@ meg_status build_solve_graph(meg_solve_s* h) {
             const GroupLaunch g = solo_launch(h);
             for (int i = 0; i < SOLVE_CHUNK && st == MEG_OK; ++i)
                 st = enqueue_iteration(g, kind == MEG_DENSE_QUAD || kind == MEG_LINEAR, kind == MEG_CSR_QUAD,
-                                       kind == MEG_MEAS_STOCH, h->q, h->desc.eig == MEG_EIG_BLOCK_KRYLOV);
+                                       meas_kind(kind), h->q, h->desc.eig == MEG_EIG_BLOCK_KRYLOV);
             cudaError_t le = cudaSuccess;
             if (st == MEG_OK) le = launch_objective(g, h->d_f);
             if (st == MEG_OK && le == cudaSuccess) le = launch_solve_check(h->sm, h->d_f, cond, h->stream);
@@ -994,7 +1044,7 @@ meg_status group_create_impl(const meg_handle* solves, int count, void* stream, 
         const int kind = h->desc.kind;
         g->has_dense |= (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR);
         g->has_csr |= kind == MEG_CSR_QUAD;
-        g->has_meas |= kind == MEG_MEAS_STOCH;
+        g->has_meas |= meas_kind(kind);
     }
     // tensor-core solves: chunks of at most TC_MAXG solves, one stream-K launch
     // each; offsets, chunk totals and grids go into both descriptor copies
@@ -1067,11 +1117,13 @@ meg_status group_create_impl(const meg_handle* solves, int count, void* stream, 
     g->gl.prec = prec;
     g->gl.stream = g->stream;
     g->gl.meas_vr = 0;
-    g->gl.meas_tc = g->gl.meas_plain = 0;
+    g->gl.meas_tc = g->gl.meas_plain = g->gl.meas_bil = 0;
     for (auto* h : g->solves)
-        if (h->desc.kind == MEG_MEAS_STOCH) {
+        if (meas_kind(h->desc.kind)) {
             g->gl.meas_vr = std::max(g->gl.meas_vr, h->n * (rank_bucket(h->r) + 1));
-            if (h->desc.mtc) g->gl.meas_tc = 1; else g->gl.meas_plain = 1;
+            if (h->desc.kind == MEG_BILINEAR) g->gl.meas_bil = 1;
+            else if (h->desc.mtc) g->gl.meas_tc = 1;
+            else g->gl.meas_plain = 1;
         }
     if (!tcd.empty()) {
         if (cudaMallocAsync((void**)&g->d_tc_desc, sizeof(SolveDev) * tcd.size(), g->stream) != cudaSuccess ||
@@ -1267,8 +1319,12 @@ int meg_group_kernels_per_step(meg_group g) {
     // orth2; float storage: combine, orth); plus the begin kernel once per iteration
     const int dense = g->gl.tc_chunks + (g->gl.blocks[PK_DENSE] > 0 ? 1 : 0);
     const int csr = g->has_csr ? (g->gl.prec == MEG_FP64 ? 1 : 2) : 0;   // float modes: V cast + product
-    // minibatch: batch and apply passes (tensor cores: batch pass, its finish, apply pass)
-    const int meas = g->has_meas ? (g->gl.meas_tc ? 3 : 0) + (g->gl.meas_plain ? 2 : 0) : 0;
+    // minibatch: batch and apply passes (tensor cores: batch pass, its finish, apply pass;
+    // the bilinear kind shares the two tensor-core passes and has its own finish)
+    const bool tcp = g->gl.meas_tc || g->gl.meas_bil;
+    const int meas = g->has_meas ? (tcp ? 2 : 0) + (g->gl.meas_tc ? 1 : 0) + (g->gl.meas_bil ? 1 : 0) +
+                                       (g->gl.meas_plain ? 2 : 0)
+                                 : 0;
     const int per = dense + csr + meas + (g->gl.prec == MEG_FP64 ? 6 : 4);
     // block Krylov: the projection pass and its factor kernel after the first product
     return g->q * per + 1 + (g->krylov ? 2 : 0);

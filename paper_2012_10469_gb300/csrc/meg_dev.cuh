@@ -50,6 +50,8 @@ enum SmallSlot : int {
     SM_SOLVE_CHUNKS,   //   chunks run so far
     SM_SOLVE_DONE,     //   1 once the gap test held
     SM_SOLVE_F,        //   f(X_t) at the last check
+    SM_SKREL,          // sigma_k - log s of the last Rayleigh-Ritz step (the block's lowest Ritz value
+                       //   relative to the bulk level log s of the iterate it was computed at)
     SM_MU = 32,        // [32] mu of X_t
     SM_DCOEF = 64,     // [32] coefficients of V diag(.) V^T in M_t
     SM_SIGMA = 96,     // [32] Ritz values of the last Rayleigh-Ritz, unshifted
@@ -164,6 +166,8 @@ struct SolveDev {
     const double* y;
     int64_t m;
     int L;
+    const void* Bm;      // BILINEAR: the b_i (m x n bf16); A holds the a_i
+    double tau;          // BILINEAR: trace scale of the tau-spectrahedron
     // schedule
     double eta, eps_a, eps_c, eps_pow;
     double log_nr;       // log(n - r), used by the certificate
@@ -342,6 +346,7 @@ struct GroupLaunch {
     // its own descriptor sub-array (PK_DTC offsets relative to the chunk)
     int meas_vr;                // largest n*(rank_bucket(r)+1) of a MEAS_STOCH member (objective staging), 0 if none
     int meas_tc, meas_plain;    // members whose minibatch products run on the tensor cores / on CUDA cores
+    int meas_bil;               // members of the bilinear kind (tensor-core passes over [A; B])
     int tc_chunks;
     const SolveDev* tc_desc[TC_MAX_CHUNKS];
     int tc_ns[TC_MAX_CHUNKS];
@@ -370,6 +375,8 @@ cudaError_t launch_meas_apply(const GroupLaunch& g);
 cudaError_t launch_meas_tc_batch(const GroupLaunch& g);
 cudaError_t launch_meas_tc_apply(const GroupLaunch& g);
 cudaError_t meas_tc_init();
+// bilinear measurements: c_i = a_i^T b_i of the m pairs of one solve into meas[0, m)
+cudaError_t launch_bil_prep(const SolveDev* d_solve, int64_t m, cudaStream_t st);
 cudaError_t launch_combine(const GroupLaunch& g, int phase);
 cudaError_t launch_orthonormalise(const GroupLaunch& g, int phase);
 cudaError_t launch_chain_kernel(const GroupLaunch& g, int which, int phase);
