@@ -789,7 +789,53 @@ def other_kernel_rooflines(device, stream, hbm_peak):
                                       "tensor_frac_of_bf16_peak": tflop / (ms / 1e3) / 1e12 / BF16_TFLOPS}
     g.meg_group_destroy()
     s.meg_destroy()
+    out["bilinear_n600_r20"] = bilinear_timing(device, stream, hbm_peak)
     return out
+
+
+def bilinear_timing(device, stream, hbm_peak):
+    """Section 7's experiment at its largest size: n = 600, rank 20, m = 20 n r
+    = 240000 pairs of unit bf16 measurement vectors (2 x 288 MB), full
+    gradient every iteration, p = 8 and q = 6 (the products the parity test
+    at this size uses).  Per product the two tensor-core passes read the
+    stacked rows [A; B] twice: 4 m n bf16 values.  Iterations/s of meg_step
+    (a captured graph) and the product's fraction of the HBM copy bandwidth."""
+    import torch
+    import synth
+    from paper_2012_10469_gb300 import binding as B
+    n, rank, p_, q_ = 600, 20, 8, 6
+    prob = synth.bilinear_recovery(n, rank, seed=7)
+    A = torch.from_numpy(np.ascontiguousarray(synth.bf16_bits(prob.A).view(np.int16))).to(device)
+    Bm = torch.from_numpy(np.ascontiguousarray(synth.bf16_bits(prob.B).view(np.int16))).to(device)
+    y = torch.from_numpy(prob.y).to(device)
+    m = prob.A.shape[0]
+    del prob.A, prob.B
+    U = np.linalg.qr(prob.U)[0]
+    eta = 1.0 / (prob.tau * 0.4 * np.sqrt(rank * n))
+    s = B.Solve(n, rank, p=p_, q=q_, precision=B.MEG_FP32, eta=eta, seed=7, stream=stream, V0=U,
+                lam0=np.full(rank, 1.0 / rank))
+    s.meg_set_objective(B.MEG_BILINEAR, A=A, B=Bm, y=y, tau=prob.tau)
+    s.meg_refine_subspace(8)
+    st = torch.cuda.ExternalStream(stream)
+    s.meg_step(3)
+    torch.cuda.synchronize()
+    iters = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.meg_step(iters)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_iter = e0.elapsed_time(e1) / iters
+    g = B.Group([s], stream=stream)
+    ms = g.meg_group_time_product(20)
+    alg = 4 * m * n * 2
+    g.meg_group_destroy()
+    s.meg_destroy()
+    return {"bound": "hbm", "engine": "tcgen05 (bf16 data, float pieces)", "n": n, "rank": rank, "m": m,
+            "p": p_, "q": q_, "ms_per_iteration": ms_iter, "iterations_per_s": 1e3 / ms_iter,
+            "ms_per_product": ms, "kernels_per_product": 3, "bytes_per_product": alg,
+            "achieved_GBs": alg / (ms / 1e3) / 1e9, "frac": alg / (ms / 1e3) / 1e9 / hbm_peak,
+            "product_share_of_iteration": q_ * ms / ms_iter}
 
 
 def fp32_data_arm(device, stream, hbm_peak, steps):

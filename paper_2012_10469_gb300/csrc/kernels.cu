@@ -688,7 +688,7 @@ __global__ void __launch_bounds__(NT) k_combine(const SolveDev* sds, int ns, int
                 for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
             } else if (s.kind == MEG_MEAS_STOCH || s.kind == MEG_BILINEAR) {
                 const T* Ys = (const T*)s.Ys;
-                const int np = meas_slots(s.nb_meas, s.mtc);                // chunks in order
+                const int np = apply_slots(s.kind, s.nb_meas, n, s.mtc);    // chunks in order
                 for (int p = 0; p < np; ++p) y += Ys[((size_t)p * n + i) * k + j];
             } else {
                 y = ((const T*)s.Y)[(size_t)i * k + j];
@@ -2138,7 +2138,7 @@ __device__ void meas_batch_tail(const SolveDev& s, int lb, bool warm, const int6
             if (s.mtc) {
                 // S_b for the tensor-core apply pass, as floats
                 const float sr = (2.f / (float)Lb) * (float)res;
-                for (int c = 0; c < k; ++c) s.mts[(size_t)b * k + c] = sr * (float)Ps[tid][B + c];
+                for (int c = 0; c < k; ++c) mts_put(s.mts, k, b, c, sr * (float)Ps[tid][B + c]);
             }
             // Minibatch (mode 0): the spectral size of (2/L) sum r_b a_b a_b^T is
             // estimated as for a weighted Wishart matrix,
@@ -2373,7 +2373,7 @@ __global__ void __launch_bounds__(NT) k_bil_finish(const SolveDev* sds, int ns) 
         const int rr = rem / k, c = rem % k;
         const int64_t i = (int64_t)lb * MB_ROWS + rr;
         if (i < m)   // row i (a_i) takes b_i^T W, row m + i (b_i) takes a_i^T W
-            s.mts[(size_t)(side ? m + i : i) * k + c] = rs[rr] * Pp[side ? 0 : 1][rr][B + c];
+            mts_put(s.mts, k, side ? m + i : i, c, rs[rr] * Pp[side ? 0 : 1][rr][B + c]);
     }
     __shared__ int am_last;
     if (tid == 0) {

@@ -13,18 +13,22 @@
 // The operands of the tensor cores are bf16: A is bf16 already; the float
 // operands ([V | W] and S) are split exactly into three bf16 pieces
 // (x = hi + mid + lo, 24 mantissa bits), so each product equals the float
-// product up to the float32 accumulation.  Each accumulation covers one
-// 16-wide K slice (one MMA) and the slices are added in registers as
-// compensated float32 sums (an accumulation's error grows with its length on
-// the tensor cores, a plain float sum's with the number of terms).
+// product up to the float32 accumulation.  Each accumulation covers 32 of a
+// chunk's 64 K (two MMAs; two accumulators per chunk, one commit) and the
+// accumulations are added in registers as compensated float32 sums (an
+// accumulation's error grows with its length on the tensor cores, where
+// partial sums are rounded toward zero; a plain float sum's with the number
+// of terms).
 //
-// Tiles are staged by the CTA's threads with ordinary loads (the rows of A
-// are gathered by the minibatch indices; the apply pass transposes them)
-// into the canonical K-major layout with the 128-byte swizzle: row q of a
+// Tiles are staged by the CTA's threads (asynchronous 16-byte copies of the
+// gathered rows of A and of the operand images that k_meas_tc_split and the
+// finish kernels write; the apply pass transposes A through registers) into
+// the canonical K-major layout with the 128-byte swizzle: row q of a
 // tile is 128 bytes (64 bf16 of K), its 16-byte piece c sits at position
-// c xor (q mod 8), rows grouped by 8 into 1024-byte atoms.  One thread issues
-// each MMA of a chunk (M = 128, N = 3 x columns, K = 16) into tensor memory
-// and commits it to an mbarrier; the block waits (bounded: about 1 s,
+// c xor (q mod 8), rows grouped by 8 into 1024-byte atoms.  Both passes keep
+// two tile stages: the next chunk's copies are in flight while one thread
+// issues the current chunk's four MMAs (M = 128, N = 3 x columns, K = 16) into
+// tensor memory and commits them to an mbarrier; the block waits (bounded: about 1 s,
 // then MEG_ERR_TIMEOUT is recorded, the CTA waits for its own MMAs, frees its
 // tensor memory and returns) and drains the accumulator with tcgen05.ld.
 //
@@ -43,6 +47,7 @@ namespace {
 
 constexpr int MT_THREADS = 256;
 constexpr int MT_TMEM_COLS = 256;
+constexpr int MT_BATCH_COLS = 512;                            // two accumulators of N <= 192 columns
 constexpr int MT_A_BYTES = MT_BM * MT_BK * 2;                 // 16 KB
 constexpr int MT_B_MAX = 192 * MT_BK * 2;                     // N <= 192 (B = 32: 3 x 64 columns)
 
@@ -86,6 +91,16 @@ __device__ __forceinline__ void csum_add(float& hi, float& lo, float x) {
     lo = __fadd_rn(lo, err);
 }
 
+// 16-byte asynchronous global -> shared copy (zero fill when !pred; nothing is
+// read then, src only has to be a valid address) and its group operations
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(pred ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // exact three-piece bf16 split of a float: piece 0, 1 or 2
 __device__ __forceinline__ unsigned short bf16_piece(float x, int p) {
     const __nv_bfloat16 hi = __float2bfloat16_rn(x);
@@ -106,18 +121,20 @@ struct MtSmem {
     int* err;
 };
 
-__device__ __forceinline__ MtSmem mt_carve(unsigned char* raw) {
+// stages: tile buffers one after the other (stage st: a + st MT_STAGE, b + st MT_STAGE)
+constexpr int MT_STAGE = MT_A_BYTES + MT_B_MAX;
+__device__ __forceinline__ MtSmem mt_carve(unsigned char* raw, int stages = 1) {
     MtSmem m;
     unsigned char* base = (unsigned char*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
     m.a = base;
     m.b = base + MT_A_BYTES;
-    m.bar = (uint64_t*)(m.b + MT_B_MAX);
+    m.bar = (uint64_t*)(base + stages * MT_STAGE);
     m.tslot = (uint32_t*)(m.bar + 2);
     m.err = (int*)(m.tslot + 1);
     return m;
 }
 
-__device__ __forceinline__ uint32_t mt_setup(const MtSmem& m) {
+__device__ __forceinline__ uint32_t mt_setup(const MtSmem& m, uint32_t cols = MT_TMEM_COLS) {
     if (threadIdx.x == 0) {
         mbar_init(m.bar, 1);
         mbar_init(m.bar + 1, 1);
@@ -126,7 +143,7 @@ __device__ __forceinline__ uint32_t mt_setup(const MtSmem& m) {
     }
     if (threadIdx.x < 32) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(m.tslot)),
-                     "r"(MT_TMEM_COLS)
+                     "r"(cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -136,34 +153,10 @@ __device__ __forceinline__ uint32_t mt_setup(const MtSmem& m) {
     return *m.tslot;
 }
 
-// One 16-wide K slice of the staged chunk as a fresh accumulation.  The
-// tensor cores round each partial sum of an accumulation toward zero, so its
-// error grows with the accumulation's length (about 4e-8 K relative for sums
-// that cancel, as dot products of random-sign data do); every MMA therefore
-// starts afresh and the slices are added in registers as compensated sums.
-// Slice 0 makes the staged tiles (generic-proxy stores) visible
-// to the tensor cores; a later slice first orders the previous slice's drain
-// before the accumulator is overwritten.  One thread issues and commits; the
-// block waits for the commit (bounded).  Returns false on timeout.
-__device__ __forceinline__ bool mt_mma_slice(const MtSmem& m, uint32_t tmem, uint32_t idesc, uint32_t parity,
-                                             int kk) {
-    if (kk == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    else tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tc_fence_after();
-        umma_bf16(tmem, sdesc_sw128(smem_u32(m.a) + kk * 32), sdesc_sw128(smem_u32(m.b) + kk * 32), idesc, 0u);
-        umma_commit(m.bar);
-    }
-    const bool ok = mbar_wait(m.bar, parity);
-    const bool bad = __syncthreads_or(ok ? 0 : 1) != 0;      // the same verdict in every thread
-    tc_fence_after();
-    return !bad;
-}
-
 // End of a CTA: on error, wait (bounded) for every MMA this CTA issued and
 // flag the solve; free the tensor memory.
-__device__ __forceinline__ void mt_teardown(const MtSmem& m, uint32_t tmem, const SolveDev& s, bool bad) {
+__device__ __forceinline__ void mt_teardown(const MtSmem& m, uint32_t tmem, const SolveDev& s, bool bad,
+                                            uint32_t cols = MT_TMEM_COLS) {
     tc_fence_before();
     __syncthreads();
     if (bad) {
@@ -177,79 +170,36 @@ __device__ __forceinline__ void mt_teardown(const MtSmem& m, uint32_t tmem, cons
     if (threadIdx.x == 0 && *m.err) s.sm[SM_STATUS] = MEG_ERR_TIMEOUT;
     if (threadIdx.x < 32) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MT_TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols)
                      : "memory");
     }
 }
 
 // ==========================================================================
-// Batch pass.  CTA (tile, part): 128 batch rows b times the columns [V | W]
-// (B each, zero beyond r and k), the part's K chunks of the n-long
-// contraction.  The B operand holds the three pieces of the float values,
-// N = 3 x 2B rows: piece p of column c is row p 2B + c.  Warps w and w + 4
-// share the tensor-memory lanes of rows 32 (w mod 4) ...; each takes every
-// other 16-column group.  Output: per row and part, the 2B products and the
-// part's ||a_b||^2, as floats in mtp, parts innermost ([row][column][part]) so
-// that the finish kernel reads an entry's parts as contiguous vectors.
-__global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev* sds, int ns) {
+// Split image of the batch pass's B operand, once per product: for each
+// 64-wide K chunk c, the N = 3 x 2B rows of [V | W] (B columns each, zero
+// beyond r and k; piece p of column col at row p 2B + col) as the chunk's 64
+// bf16 values, laid out byte for byte as the swizzled shared-memory tile
+// (N x 128 bytes per chunk), so that every CTA of the batch pass copies it
+// with 16-byte loads instead of splitting the same values again.  The blocks
+// of the batch-pass grid take the chunks in turn.
+__global__ void __launch_bounds__(MT_THREADS) k_meas_tc_split(const SolveDev* sds, int ns) {
     pdl_wait();
     pdl_trigger();
     const int si = find_solve(sds, ns, PK_MTB, blockIdx.x);
     const SolveDev& s = sds[si];
     const int lb = blockIdx.x - s.off[PK_MTB];
     const int Lb = s.nb_meas, n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
-    const int mtiles = (Lb + MT_BM - 1) / MT_BM, KS = meas_ks(Lb, n);
-    if (!s.mtc || (s.kind != MEG_MEAS_STOCH && s.kind != MEG_BILINEAR) || lb < 0 || lb >= mtiles * KS) return;
-    const int mt = lb % mtiles, part = lb / mtiles;
+    const int G = (Lb + MT_BM - 1) / MT_BM * meas_ks(Lb, n);
+    if (!s.mtc || (s.kind != MEG_MEAS_STOCH && s.kind != MEG_BILINEAR) || lb < 0 || lb >= G) return;
     const int nch = (n + MT_BK - 1) / MT_BK;
-    const int c_lo = (int)((int64_t)part * nch / KS), c_hi = (int)((int64_t)(part + 1) * nch / KS);
     const bool warm = (s.mode == 1);
     const int B = k_bucket(k), NC = 2 * B, N = 3 * NC;
-    extern __shared__ __align__(1024) unsigned char smraw[];
-    const MtSmem m = mt_carve(smraw);
-    __shared__ int64_t rowidx[MT_BM];
-    if (tid < MT_BM) {
-        const int b = mt * MT_BM + tid;
-        rowidx[tid] = b < Lb ? batch_row(s, warm, b) : -1;
-    }
-    const uint32_t tmem = mt_setup(m);                      // (synchronises the block)
-    const uint32_t idesc = idesc_bf16(MT_BM, N);
     const float* W = (const float*)s.W;
     const double* V = s.V;
-    // A tile: thread = (row, half of the 64 columns), four 16-byte vectors
-    const int arow = tid >> 1, ahalf = tid & 1;
-    const int64_t ar = rowidx[arow];
-    const unsigned short* arp = ar >= 0 ? stacked_row(s, ar) : nullptr;
-    float aa = 0.f;                                         // this thread's part of ||a||^2
-    // accumulator drain: rows (lanes) and 16-column groups of this warp
-    const int warp = tid >> 5, quarter = warp & 3, lane = tid & 31;
-    const int grow = quarter * 32 + lane;                   // tile row of this thread's results
-    const int ngroups = NC / 16;                            // 1, 2 or 4
-    float run[2][16], rlo[2][16];
-#pragma unroll
-    for (int g = 0; g < 2; ++g)
-#pragma unroll
-        for (int j = 0; j < 16; ++j) run[g][j] = rlo[g][j] = 0.f;
-    bool ok = true;
-    uint32_t parity = 0;
-    for (int c = c_lo; c < c_hi && ok; ++c) {
+    for (int c = lb; c < nch; c += G) {
+        unsigned char* img = (unsigned char*)(s.mtb + (size_t)c * N * 64);
         const int k0 = c * MT_BK;
-        // ---- A tile (gathered rows)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const int kc = ahalf * 4 + v;                   // 16-byte piece of the row
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (ar >= 0 && k0 + kc * 8 < n) val = *(const uint4*)(arp + k0 + kc * 8);
-            *(uint4*)(m.a + arow * 128 + ((kc ^ (arow & 7)) << 4)) = val;
-            const unsigned wds[4] = {val.x, val.y, val.z, val.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const float lo = __uint_as_float(wds[h] << 16), hi = __uint_as_float(wds[h] & 0xffff0000u);
-                aa = fmaf(lo, lo, aa);
-                aa = fmaf(hi, hi, aa);
-            }
-        }
-        // ---- B tile: N rows (piece, column) x 64 K, one 16-byte vector per item
         for (int it = tid; it < N * 8; it += MT_THREADS) {
             const int q = it >> 3, kc = it & 7;
             const int p = q / NC, col = q % NC;
@@ -269,35 +219,137 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev*
             val.y = (unsigned)e[2] | ((unsigned)e[3] << 16);
             val.z = (unsigned)e[4] | ((unsigned)e[5] << 16);
             val.w = (unsigned)e[6] | ((unsigned)e[7] << 16);
-            *(uint4*)(m.b + q * 128 + ((kc ^ (q & 7)) << 4)) = val;
+            *(uint4*)(img + q * 128 + ((kc ^ (q & 7)) << 4)) = val;
         }
-        // K slices beyond n multiply zero columns: skipped
-        const int nsl = min(MT_BK / 16, (n - k0 + 15) / 16);
-        for (int kk = 0; kk < nsl; ++kk) {
-            ok = mt_mma_slice(m, tmem, idesc, parity, kk);
-            parity ^= 1u;
-            if (!ok) break;
-            // ---- drain: hi + mid + lo of each output column, added to the running sums
-            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
+    }
+}
+
+// ==========================================================================
+// Batch pass.  CTA (tile, part): 128 batch rows b times the columns [V | W]
+// (B each, zero beyond r and k), the part's K chunks of the n-long
+// contraction.  The B operand holds the three pieces of the float values,
+// N = 3 x 2B rows: piece p of column c is row p 2B + c.  Warps w and w + 4
+// share the tensor-memory lanes of rows 32 (w mod 4) ...; each takes every
+// other 16-column group.  Output: per row and part, the 2B products and the
+// part's ||a_b||^2, as floats in mtp, parts innermost ([row][column][part]) so
+// that the finish kernel reads an entry's parts as contiguous vectors.
+__global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev* sds, int ns) {
+    pdl_wait();
+    pdl_trigger();
+    const int si = find_solve(sds, ns, PK_MTB, blockIdx.x);
+    const SolveDev& s = sds[si];
+    const int lb = blockIdx.x - s.off[PK_MTB];
+    const int Lb = s.nb_meas, n = s.n, k = s.k, tid = threadIdx.x;
+    const int mtiles = (Lb + MT_BM - 1) / MT_BM, KS = meas_ks(Lb, n);
+    if (!s.mtc || (s.kind != MEG_MEAS_STOCH && s.kind != MEG_BILINEAR) || lb < 0 || lb >= mtiles * KS) return;
+    const int mt = lb % mtiles, part = lb / mtiles;
+    const int nch = (n + MT_BK - 1) / MT_BK;
+    const int c_lo = (int)((int64_t)part * nch / KS), c_hi = (int)((int64_t)(part + 1) * nch / KS);
+    const bool warm = (s.mode == 1);
+    const int B = k_bucket(k), NC = 2 * B, N = 3 * NC;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    const MtSmem m = mt_carve(smraw, 2);
+    __shared__ int64_t rowidx[MT_BM];
+    if (tid < MT_BM) {
+        const int b = mt * MT_BM + tid;
+        rowidx[tid] = b < Lb ? batch_row(s, warm, b) : -1;
+    }
+    const uint32_t tmem = mt_setup(m, MT_BATCH_COLS);       // (synchronises the block)
+    const uint32_t idesc = idesc_bf16(MT_BM, N);
+    // A tile: thread = (row, half of the 64 columns), four 16-byte vectors
+    const int arow = tid >> 1, ahalf = tid & 1;
+    const int64_t ar = rowidx[arow];
+    const unsigned short* arp = ar >= 0 ? stacked_row(s, ar) : (const unsigned short*)s.A;
+    float aa = 0.f;                                         // this thread's part of ||a||^2
+    // accumulator drain: rows (lanes) and 16-column groups of this warp
+    const int warp = tid >> 5, quarter = warp & 3, lane = tid & 31;
+    const int grow = quarter * 32 + lane;                   // tile row of this thread's results
+    const int ngroups = NC / 16;                            // 1, 2 or 4
+    float run[2][16], rlo[2][16];
+#pragma unroll
+    for (int g = 0; g < 2; ++g)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) run[g][j] = rlo[g][j] = 0.f;
+    // chunk c into stage st: the gathered rows of A (zero beyond n) and the chunk's
+    // image of the split [V | W] (k_meas_tc_split), asynchronous 16-byte copies
+    auto stage = [&](int c, int st) {
+        unsigned char* As = m.a + st * MT_STAGE;
+        unsigned char* Bs = m.b + st * MT_STAGE;
+        const int k0 = c * MT_BK;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int kc = ahalf * 4 + v;                   // 16-byte piece of the row
+            const bool pred = ar >= 0 && k0 + kc * 8 < n;
+            cp_async16(As + arow * 128 + ((kc ^ (arow & 7)) << 4), pred ? arp + k0 + kc * 8 : arp, pred);
+        }
+        const unsigned short* src = s.mtb + (size_t)c * N * 64;
+        for (int it = tid; it < N * 8; it += MT_THREADS) cp_async16(Bs + it * 16, src + it * 8, true);
+        cp_async_commit();
+    };
+    bool ok = true;
+    uint32_t parity = 0;
+    if (c_lo < c_hi) stage(c_lo, 0);
+    for (int c = c_lo; c < c_hi && ok; ++c) {
+        const int st = (c - c_lo) & 1;
+        // the next chunk's copies run while this chunk is multiplied
+        if (c + 1 < c_hi) stage(c + 1, st ^ 1);
+        else cp_async_commit();                             // an empty group: wait_group 1 still means chunk c
+        cp_async_wait1();
+        __syncthreads();
+        const unsigned char* As = m.a + st * MT_STAGE;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int kc = ahalf * 4 + v;
+            const uint4 val = *(const uint4*)(As + arow * 128 + ((kc ^ (arow & 7)) << 4));
+            const unsigned wds[4] = {val.x, val.y, val.z, val.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const float lo = __uint_as_float(wds[h] << 16), hi = __uint_as_float(wds[h] & 0xffff0000u);
+                aa = fmaf(lo, lo, aa);
+                aa = fmaf(hi, hi, aa);
+            }
+        }
+        // slices 0 and 1 accumulate in columns 0.., slices 2 and 3 in columns 256..
+        // (32-wide accumulations); one commit for the chunk
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(m.a + st * MT_STAGE), b0 = smem_u32(m.b + st * MT_STAGE);
+#pragma unroll
+            for (int kk = 0; kk < MT_BK / 16; ++kk)
+                umma_bf16(tmem + (uint32_t)((kk >> 1) * 256), sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32),
+                          idesc, (uint32_t)(kk & 1));
+            umma_commit(m.bar);
+        }
+        const bool done = mbar_wait(m.bar, parity);
+        parity ^= 1u;
+        ok = __syncthreads_or(done ? 0 : 1) == 0;
+        tc_fence_after();
+        if (!ok) break;
+        // ---- drain: hi + mid + lo of each output column of both accumulators
+        const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+        for (int acc = 0; acc < 2; ++acc)
 #pragma unroll
             for (int gi = 0; gi < 2; ++gi) {
                 const int g = (warp >> 2) + 2 * gi;         // this warp's 16-column groups
                 if (g < ngroups) {
                     uint32_t vh[16], vm[16], vl[16];
-                    tmem_ld16(tb + (uint32_t)(16 * g), vh);
-                    tmem_ld16(tb + (uint32_t)(NC + 16 * g), vm);
-                    tmem_ld16(tb + (uint32_t)(2 * NC + 16 * g), vl);
+                    const uint32_t t0 = tb + (uint32_t)(acc * 256 + 16 * g);
+                    tmem_ld16(t0, vh);
+                    tmem_ld16(t0 + (uint32_t)NC, vm);
+                    tmem_ld16(t0 + (uint32_t)(2 * NC), vl);
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
                         csum_add(run[gi][j], rlo[gi][j],
                                  (__uint_as_float(vh[j]) + __uint_as_float(vm[j])) + __uint_as_float(vl[j]));
                 }
             }
-        }
-        if (!ok) break;
         tc_fence_before();
-        __syncthreads();                                    // tiles and accumulator are reused
+        __syncthreads();                                    // the stage and the accumulators are reused
     }
+    cp_async_wait0();                                       // no copy in flight when the CTA ends
     // ---- partials of this part: columns, then ||a||^2 (the two threads of a row add theirs)
     aa += __shfl_xor_sync(0xffffffffu, aa, 1);
     const int b = mt * MT_BM + grow;
@@ -313,34 +365,36 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev*
     }
     if (ok && ahalf == 0 && mt * MT_BM + arow < Lb)
         s.mtp[((size_t)(mt * MT_BM + arow) * (NC + 1) + NC) * KS + part] = aa;
-    mt_teardown(m, tmem, s, !ok);
+    mt_teardown(m, tmem, s, !ok, MT_BATCH_COLS);
 }
 
 // ==========================================================================
-// Apply pass.  CTA (tile, chunk of the batch): 128 rows i of Y = A_B^T S over
-// the chunk's batch rows, 64 at a time.  The A operand is A_B^T: element
-// (i, b) = A[idx_b, i], loaded 8 consecutive i at a time (16 bytes of one
-// row of A) and scattered into the K-major tile (2-byte stores).  The B
-// operand holds the pieces of S_bj = (2/Lb) r_b T_bj, N = 3 P rows (P = k
-// padded to 16): piece p of column j is row p P + j.  Output: the chunk's
-// partial of Y in slot `chunk` of Ys (k_combine adds the slots in order).
-__global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_apply(const SolveDev* sds, int ns) {
+// Apply pass.  CTA (tile, slot of the batch): 128 rows i of Y = A_B^T S over
+// the slot's batch rows, 64-row chunks (slots start on chunk boundaries).  The
+// A operand is A_B^T: element (i, b) = A[idx_b, i], loaded 8 consecutive i
+// at a time (16 bytes of one row of A) into registers one chunk ahead and
+// scattered into the K-major tile (2-byte stores).  The B operand is the
+// chunk's image of S (mts_put: the three pieces of S_bj, N = 3 P rows, P = k
+// padded to 16), copied asynchronously one chunk ahead.  Slices 0-1 and 2-3
+// of a chunk accumulate in two accumulators, one commit per chunk.  Output:
+// the slot's partial of Y in slot `chunk` of Ys (k_combine adds the slots in
+// order).
+__global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_apply(const SolveDev* sds, int ns) {
     pdl_wait();
     pdl_trigger();
     const int si = find_solve(sds, ns, PK_MAP, blockIdx.x);
     const SolveDev& s = sds[si];
     const int lb = blockIdx.x - s.off[PK_MAP];
     const int Lb = s.nb_meas, n = s.n, k = s.k, tid = threadIdx.x;
-    const int ntile = (n + MT_BM - 1) / MT_BM, nchk = meas_slots(Lb, 1);
+    const int ntile = (n + MT_BM - 1) / MT_BM, nchk = apply_slots(s.kind, Lb, n, 1);
     if (!s.mtc || (s.kind != MEG_MEAS_STOCH && s.kind != MEG_BILINEAR) || lb < 0 || lb >= ntile * nchk) return;
     const int tile = lb % ntile, chunk = lb / ntile;
-    const int b_lo = (int)((int64_t)chunk * Lb / nchk), b_hi = (int)((int64_t)(chunk + 1) * Lb / nchk);
+    const int nc64 = (Lb + MT_BK - 1) / MT_BK;
+    const int c_lo = (int)((int64_t)chunk * nc64 / nchk), c_hi = (int)((int64_t)(chunk + 1) * nc64 / nchk);
     const bool full = (s.mode == 1) || s.kind == MEG_BILINEAR;    // batch row b is stacked row b
     const int P = (k + 15) / 16 * 16, N = 3 * P;
-    const float* S = s.mts;                                 // S_b = (2/Lb) r_b T_b (bilinear: see above), rows x k
     extern __shared__ __align__(1024) unsigned char smraw[];
-    const MtSmem m = mt_carve(smraw);
-    __shared__ int64_t bidx[MT_BK];
+    const MtSmem m = mt_carve(smraw, 2);
     const uint32_t tmem = mt_setup(m);
     const uint32_t idesc = idesc_bf16(MT_BM, N);
     const int i0 = tile * MT_BM;
@@ -351,64 +405,92 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_apply(const SolveDev*
     float run[16], rlo[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) run[j] = rlo[j] = 0.f;
-    bool ok = true;
-    uint32_t parity = 0;
-    for (int b0 = b_lo; b0 < b_hi && ok; b0 += MT_BK) {
-        const int bn = min(MT_BK, b_hi - b0);
-        if (tid < MT_BK) bidx[tid] = tid < bn ? (full ? (int64_t)(b0 + tid) : (int64_t)s.bidx[b0 + tid]) : -1;
-        __syncthreads();
-        // ---- A^T tile: 64 batch rows x 16 vectors of 8 consecutive i
-        for (int it = tid; it < MT_BK * (MT_BM / 8); it += MT_THREADS) {
-            const int kk = it / (MT_BM / 8), iv = it % (MT_BM / 8);
-            const int64_t row = bidx[kk];
-            const int ii = iv * 8;
-            uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if (row >= 0 && i0 + ii < n) val = *(const uint4*)(stacked_row(s, row) + i0 + ii);
-            const unsigned wds[4] = {val.x, val.y, val.z, val.w};
+    // A^T items of this thread: (batch row kk, 8 consecutive i); consecutive lanes
+    // take consecutive kk, so their 2-byte stores to one tile row i fall in
+    // different banks
+    constexpr int NIT = MT_BK * (MT_BM / 8) / MT_THREADS;   // 4
+    uint4 pv[NIT];
+    auto fetch = [&](int c) {
+#pragma unroll
+        for (int j = 0; j < NIT; ++j) {
+            const int it = tid + j * MT_THREADS, kk = it % MT_BK, ii = (it / MT_BK) * 8;
+            const int b = c * MT_BK + kk;
+            pv[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (b < Lb && i0 + ii < n) {
+                const int64_t row = full ? (int64_t)b : (int64_t)s.bidx[b];
+                pv[j] = *(const uint4*)(stacked_row(s, row) + i0 + ii);
+            }
+        }
+    };
+    auto put = [&](int st) {
+        unsigned char* As = m.a + st * MT_STAGE;
+#pragma unroll
+        for (int j = 0; j < NIT; ++j) {
+            const int it = tid + j * MT_THREADS, kk = it % MT_BK, ii = (it / MT_BK) * 8;
+            const unsigned wds[4] = {pv[j].x, pv[j].y, pv[j].z, pv[j].w};
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                *(unsigned short*)(m.a + sw_off(ii + 2 * h, kk)) = (unsigned short)(wds[h] & 0xffffu);
-                *(unsigned short*)(m.a + sw_off(ii + 2 * h + 1, kk)) = (unsigned short)(wds[h] >> 16);
+                *(unsigned short*)(As + sw_off(ii + 2 * h, kk)) = (unsigned short)(wds[h] & 0xffffu);
+                *(unsigned short*)(As + sw_off(ii + 2 * h + 1, kk)) = (unsigned short)(wds[h] >> 16);
             }
         }
-        // ---- S tile: N rows (piece, column j) x 64 batch rows, 16-byte vectors
-        for (int it = tid; it < N * 8; it += MT_THREADS) {
-            const int q = it >> 3, kc = it & 7;
-            const int p = q / P, j = q % P;
-            unsigned short e[8];
+    };
+    auto stage_s = [&](int c, int st) {
+        unsigned char* Bs = m.b + st * MT_STAGE;
+        const unsigned short* src = s.mts + (size_t)c * N * 64;
+        for (int it = tid; it < N * 8; it += MT_THREADS) cp_async16(Bs + it * 16, src + it * 8, true);
+        cp_async_commit();
+    };
+    bool ok = true;
+    uint32_t parity = 0;
+    if (c_lo < c_hi) {
+        fetch(c_lo);
+        stage_s(c_lo, 0);
+    }
+    for (int c = c_lo; c < c_hi && ok; ++c) {
+        const int st = (c - c_lo) & 1;
+        put(st);                                            // chunk c's A^T, from the registers
+        if (c + 1 < c_hi) {                                 // chunk c + 1 is read while c is multiplied
+            fetch(c + 1);
+            stage_s(c + 1, st ^ 1);
+        } else {
+            cp_async_commit();                              // an empty group: wait_group 1 still means chunk c
+        }
+        cp_async_wait1();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(m.a + st * MT_STAGE), b0 = smem_u32(m.b + st * MT_STAGE);
 #pragma unroll
-            for (int h = 0; h < 8; ++h) {
-                const int bb = kc * 8 + h;
-                const float x = (bb < bn && j < k) ? S[(size_t)(b0 + bb) * k + j] : 0.f;
-                e[h] = bf16_piece(x, p);
-            }
-            uint4 val;
-            val.x = (unsigned)e[0] | ((unsigned)e[1] << 16);
-            val.y = (unsigned)e[2] | ((unsigned)e[3] << 16);
-            val.z = (unsigned)e[4] | ((unsigned)e[5] << 16);
-            val.w = (unsigned)e[6] | ((unsigned)e[7] << 16);
-            *(uint4*)(m.b + q * 128 + ((kc ^ (q & 7)) << 4)) = val;
+            for (int kk = 0; kk < MT_BK / 16; ++kk)
+                umma_bf16(tmem + (uint32_t)((kk >> 1) * 128), sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32),
+                          idesc, (uint32_t)(kk & 1));
+            umma_commit(m.bar);
         }
-        // K slices beyond the chunk's rows multiply zero rows: skipped
-        for (int kk = 0; kk < (bn + 15) / 16; ++kk) {
-            ok = mt_mma_slice(m, tmem, idesc, parity, kk);
-            parity ^= 1u;
-            if (!ok) break;
-            if (g < ngroups) {
-                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
+        const bool done = mbar_wait(m.bar, parity);
+        parity ^= 1u;
+        ok = __syncthreads_or(done ? 0 : 1) == 0;
+        tc_fence_after();
+        if (!ok) break;
+        if (g < ngroups) {
+            const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll
+            for (int acc = 0; acc < 2; ++acc) {
                 uint32_t vh[16], vm[16], vl[16];
-                tmem_ld16(tb + (uint32_t)(16 * g), vh);
-                tmem_ld16(tb + (uint32_t)(P + 16 * g), vm);
-                tmem_ld16(tb + (uint32_t)(2 * P + 16 * g), vl);
+                const uint32_t t0 = tb + (uint32_t)(acc * 128 + 16 * g);
+                tmem_ld16(t0, vh);
+                tmem_ld16(t0 + (uint32_t)P, vm);
+                tmem_ld16(t0 + (uint32_t)(2 * P), vl);
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
                     csum_add(run[j], rlo[j], (__uint_as_float(vh[j]) + __uint_as_float(vm[j])) + __uint_as_float(vl[j]));
             }
         }
-        if (!ok) break;
         tc_fence_before();
-        __syncthreads();
+        __syncthreads();                                    // the stage and the accumulators are reused
     }
+    cp_async_wait0();                                       // no copy in flight when the CTA ends
     const int i = i0 + grow;
     if (ok && g < ngroups && i < n) {
         float* Ys = (float*)s.Ys + ((size_t)chunk * n + i) * k;
@@ -419,18 +501,22 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_apply(const SolveDev*
     mt_teardown(m, tmem, s, !ok);
 }
 
-constexpr size_t MT_SMEM = 1024 + MT_A_BYTES + MT_B_MAX + 64;
+constexpr size_t MT_SMEM = 1024 + 2 * (size_t)MT_STAGE + 64;   // two stages (both passes)
 
 }  // namespace
 
 cudaError_t meas_tc_init() {
-    cudaError_t e = cudaFuncSetAttribute(k_meas_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_meas_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_meas_tc_apply, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)MT_SMEM);
 }
 
 cudaError_t launch_meas_tc_batch(const GroupLaunch& g) {
     if (g.blocks[PK_MTB] == 0) return cudaSuccess;
+    cudaError_t e = launch_k(k_meas_tc_split, dim3(g.blocks[PK_MTB]), dim3(MT_THREADS), 0, g.stream, 1, g.d_solves,
+                             g.ns);
+    if (e != cudaSuccess) return e;
     return launch_k(k_meas_tc_batch, dim3(g.blocks[PK_MTB]), dim3(MT_THREADS), MT_SMEM, g.stream, 1, g.d_solves,
                     g.ns);
 }

@@ -179,7 +179,8 @@ int blocks_of(const SolveDev& d, int kind) {
             return d.kind == MEG_MEAS_STOCH ? (d.nb_meas + MB_ROWS - 1) / MB_ROWS : 0;
         case PK_MAP:
             if (!meas_kind(d.kind)) return 0;
-            return (d.mtc ? (d.n + MT_BM - 1) / MT_BM : (d.n + MA_ROWS - 1) / MA_ROWS) * meas_slots(d.nb_meas, d.mtc);
+            return (d.mtc ? (d.n + MT_BM - 1) / MT_BM : (d.n + MA_ROWS - 1) / MA_ROWS) *
+                   apply_slots(d.kind, d.nb_meas, d.n, d.mtc);
         case PK_MTB:
             return (meas_kind(d.kind) && d.mtc) ? (d.nb_meas + MT_BM - 1) / MT_BM * meas_ks(d.nb_meas, d.n) : 0;
         default: return 0;
@@ -367,10 +368,12 @@ int64_t meg_footprint(int n, int r, int p, int precision, int kind) {
     int64_t b = 0;
     b += ts * (int64_t)n * (2 * r + 4 * k);
     if (kind == MEG_DENSE_QUAD || kind == MEG_LINEAR) b += ts * (int64_t)std::max(dense_splits(n), 16) * n * k;
-    if (kind == MEG_MEAS_STOCH || kind == MEG_BILINEAR)
+    if (kind == MEG_MEAS_STOCH)
         b += ts * (int64_t)MEAS_CHUNKS * n * k;   // (+ scratch of 8 (34 m + m/8) bytes and
-                                                  //  4 (2 k_bucket(k) + 1) m tensor-core partials; bilinear:
-                                                  //  8 (m + m/32) bytes and 8 (2 k_bucket(k) + 1 + k) m)
+                                                  //  4 (2 k_bucket(k) + 1) m tensor-core partials)
+    if (kind == MEG_BILINEAR)                     // apply-pass slots for large m (+ 8 (m + m/32) bytes and
+        b += ts * (int64_t)std::min(BIL_SLOTS_MAX, (4 * 152 + (n + MT_BM - 1) / MT_BM - 1) / ((n + MT_BM - 1) / MT_BM)) *
+             n * k;                               //  8 (2 k_bucket(k) + 1 + k) m of partials and S)
     if (precision == MEG_MIXED_BF16 && n % 8 == 0) b += 2 * (int64_t)((3 * k + 15) / 16 * 16) * ((n + 63) / 64 * 64);
     b += 4 * (nb_red + groups) * 2 * RED_MAX_ENTRIES;
     b += 4 * (groups + 3) + 8 * SM_TOTAL + 8;
@@ -581,7 +584,9 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     }
     if (dense_kind || meas_kind(o->kind)) {
         // partial products: K splits of the dense product, or batch chunks of the minibatch product
-        const size_t slots = dense_kind ? (size_t)d.nb_ds : (size_t)MEAS_CHUNKS;
+        const size_t slots = dense_kind                    ? (size_t)d.nb_ds
+                             : o->kind == MEG_BILINEAR ? (size_t)bil_slots((int)(2 * o->m), n)
+                                                       : (size_t)MEAS_CHUNKS;
         if (h->Ys) { cudaFreeAsync(h->Ys, h->stream); h->Ys = nullptr; }
         if (cudaMallocAsync(&h->Ys, ts * slots * n * k, h->stream) != cudaSuccess)
             return fail(MEG_ERR_OOM, "meg_set_objective: partial products");
@@ -612,6 +617,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     d.mtc = 0;
     d.mtp = nullptr;
     d.mts = nullptr;
+    d.mtb = nullptr;
     if (h->mtp) { cudaFreeAsync(h->mtp, h->stream); h->mtp = nullptr; }
     if (o->kind == MEG_BILINEAR ||
         (o->kind == MEG_MEAS_STOCH && h->prec != MEG_FP64 && n % 8 == 0 && ((uintptr_t)o->A % 16) == 0)) {
@@ -621,11 +627,18 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
                                 : std::max((size_t)meas_ks(o->L, n) * o->L, (size_t)meas_ks((int)o->m, n) * o->m);
         // S: one row per batch row (bilinear: per stacked row)
         const size_t srows = o->kind == MEG_BILINEAR ? (size_t)d.nb_meas : (size_t)std::max<int64_t>(o->L, o->m);
-        if (cudaMallocAsync((void**)&h->mtp, sizeof(float) * (rows * cols + srows * k), h->stream) != cudaSuccess)
+        // + the split images of the apply pass's S (zeroed: columns k..P-1 are never written)
+        // and of the batch pass's [V | W] (ceil(n/64) chunks of 3 x (cols - 1) rows x 64 bf16)
+        const size_t sfl = (rows * cols + 3) & ~(size_t)3;               // 16-byte aligned images
+        const size_t sim = mts_image_bytes((int64_t)srows, k) / 4;
+        const size_t img = (size_t)((n + MT_BK - 1) / MT_BK) * 3 * (cols - 1) * MT_BK / 2;
+        if (cudaMallocAsync((void**)&h->mtp, sizeof(float) * (sfl + sim + img), h->stream) != cudaSuccess)
             return fail(MEG_ERR_OOM, "meg_set_objective: tensor-core partials");
+        CU(cudaMemsetAsync(h->mtp + sfl, 0, sizeof(float) * sim, h->stream));
         d.mtc = 1;
         d.mtp = h->mtp;
-        d.mts = h->mtp + rows * cols;
+        d.mts = (unsigned short*)(h->mtp + sfl);
+        d.mtb = (unsigned short*)(h->mtp + sfl + sim);
     }
     meg_status st = upload_desc(h, d);
     if (st != MEG_OK) return st;
@@ -1319,10 +1332,10 @@ int meg_group_kernels_per_step(meg_group g) {
     // orth2; float storage: combine, orth); plus the begin kernel once per iteration
     const int dense = g->gl.tc_chunks + (g->gl.blocks[PK_DENSE] > 0 ? 1 : 0);
     const int csr = g->has_csr ? (g->gl.prec == MEG_FP64 ? 1 : 2) : 0;   // float modes: V cast + product
-    // minibatch: batch and apply passes (tensor cores: batch pass, its finish, apply pass;
-    // the bilinear kind shares the two tensor-core passes and has its own finish)
+    // minibatch: batch and apply passes (tensor cores: the operand split, batch pass, its
+    // finish, apply pass; the bilinear kind shares the tensor-core passes and has its own finish)
     const bool tcp = g->gl.meas_tc || g->gl.meas_bil;
-    const int meas = g->has_meas ? (tcp ? 2 : 0) + (g->gl.meas_tc ? 1 : 0) + (g->gl.meas_bil ? 1 : 0) +
+    const int meas = g->has_meas ? (tcp ? 3 : 0) + (g->gl.meas_tc ? 1 : 0) + (g->gl.meas_bil ? 1 : 0) +
                                        (g->gl.meas_plain ? 2 : 0)
                                  : 0;
     const int per = dense + csr + meas + (g->gl.prec == MEG_FP64 ? 6 : 4);

@@ -12,6 +12,8 @@
 #include <stdint.h>
 
 #include "../../include/meg.h"
+#include <cuda_bf16.h>
+
 #include "dense_tc.cuh"
 
 #define MEG_KMAX 32
@@ -117,6 +119,47 @@ __host__ __device__ __forceinline__ int meas_slots(int Lb, int mtc) {
     const int c = (Lb + MT_BK - 1) / MT_BK;
     return c < MEAS_CHUNKS ? (c > 0 ? c : 1) : MEAS_CHUNKS;
 }
+// The bilinear kind's apply pass runs over all 2 m stacked rows every
+// product: it is split into enough slots that the grid (row tiles of Y times
+// slots) holds about four CTAs per SM, at most BIL_SLOTS_MAX.
+#define BIL_SLOTS_MAX 256
+__host__ __device__ __forceinline__ int bil_slots(int Lb, int n) {
+    const int ntile = (n + MT_BM - 1) / MT_BM, c = (Lb + MT_BK - 1) / MT_BK;
+    int sl = (4 * 152 + ntile - 1) / ntile;
+    if (sl > BIL_SLOTS_MAX) sl = BIL_SLOTS_MAX;
+    if (sl > c) sl = c;
+    return sl > 0 ? sl : 1;
+}
+// Image of the tensor-core apply pass's S operand: per 64-row chunk of the
+// batch rows, 3 P rows (P = k padded to 16; the exact three-piece bf16 split,
+// piece p of column j at row p P + j) of 64 bf16 values, laid out byte for
+// byte as the 128-byte-swizzled K-major shared-memory tile (3 P x 128 bytes
+// per chunk), so that the apply pass copies it with 16-byte loads.
+__host__ __device__ __forceinline__ size_t mts_image_bytes(int64_t rows, int k) {
+    return (size_t)((rows + 63) / 64) * 3 * ((k + 15) / 16 * 16) * 128;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ void mts_put(unsigned short* img, int k, int64_t b, int j, float x) {
+    const int P = (k + 15) / 16 * 16, kk = (int)(b & 63);
+    unsigned char* base = (unsigned char*)img + (size_t)(b >> 6) * 3 * P * 128;
+    unsigned short pc[3];
+    const float h = __bfloat162float(__float2bfloat16_rn(x));
+    const float r1 = x - h, md = __bfloat162float(__float2bfloat16_rn(r1));
+    pc[0] = __bfloat16_as_ushort(__float2bfloat16_rn(x));
+    pc[1] = __bfloat16_as_ushort(__float2bfloat16_rn(r1));
+    pc[2] = __bfloat16_as_ushort(__float2bfloat16_rn(r1 - md));
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const int q = p * P + j;
+        *(unsigned short*)(base + q * 128 + ((((kk >> 3) ^ (q & 7))) << 4) + (kk & 7) * 2) = pc[p];
+    }
+}
+#endif
+
+// partial-product slots of a member's apply pass (k_combine adds them in order)
+__host__ __device__ __forceinline__ int apply_slots(int kind, int Lb, int n, int mtc) {
+    return kind == MEG_BILINEAR ? bil_slots(Lb, n) : meas_slots(Lb, mtc);
+}
 
 #define RED_GROUP 16            // blocks per first-level group of a reduction
 #define ROWS_MAX 64             // rows per block of the row-reduction kernels, at most
@@ -137,7 +180,8 @@ struct SolveDev {
     int eig;             // MEG_EIG_SUBSPACE or MEG_EIG_BLOCK_KRYLOV
     int mtc;             // 1: minibatch products on tcgen05 (bf16 A, n % 8 == 0, float storage)
     float* mtp;          // partials of the tensor-core batch pass (meas_ks parts x rows x (2 B + 1))
-    float* mts;          // S_b = (2/Lb) r_b a_b^T W as floats (rows x k), the apply pass's operand
+    unsigned short* mts; // the apply pass's operand S (S_b = (2/Lb) r_b a_b^T W) as its split image (mts_put)
+    unsigned short* mtb; // split [V | W] image of the batch pass's B operand (ceil(n/64) x 3 2B x 64 bf16)
     int nb_tm;           // tensor-core path: 128-row tiles
     int tc_npad, tc_kpad;// Wsp: (3k padded to 16) x (n padded to 64) bf16
     int tc_G;            // tensor-core launch holding this solve: CTAs

@@ -439,11 +439,12 @@ meg_status meg_server_submit(meg_server s, const meg_request* rq, uint64_t* id) 
     if (fp < 0) return sfail(MEG_ERR_INVALID_ARG, "meg_server_submit: sizes");
     // the objective data copied in, and for measurements the per-measurement scratch
     // (residual, ||a||^2, a^T W) that meg_footprint cannot size without m, and the
-    // partials of the tensor-core minibatch pass (float storage)
+    // partials of the tensor-core minibatch pass and its split operand image (float storage)
     const int64_t mtp = rq->kind == MEG_MEAS_STOCH && rq->opt.precision != MEG_FP64
                             ? 4 * (int64_t)(2 * k_bucket(r + rq->opt.p) + 1) *
                                       std::max((int64_t)meas_ks(rq->L, n) * rq->L, (int64_t)meas_ks((int)rq->m, n) * rq->m) +
-                                  4 * (int64_t)(r + rq->opt.p) * std::max<int64_t>(rq->L, rq->m)
+                                  (int64_t)mts_image_bytes(std::max<int64_t>(rq->L, rq->m), r + rq->opt.p) + 16 +
+                                  (int64_t)((n + MT_BK - 1) / MT_BK) * 3 * 2 * k_bucket(r + rq->opt.p) * MT_BK * 2
                             : 0;
     int64_t data = rq->kind == MEG_MEAS_STOCH
                        ? rq->m * (int64_t)n * (int64_t)elem_bytes(rq->opt.precision) + 8 * rq->m +

@@ -37,8 +37,9 @@ def _solve(prob, r, p, q, precision, eta, seed, V0, lam0, aligned):
 
 
 def _meas_kernels(s):
-    """Minibatch kernels per iteration of a one-member group: 3 on the tensor
-    cores (batch pass, its finish, apply pass) x q, 2 on the CUDA cores."""
+    """Minibatch kernels per iteration of a one-member group: 4 on the tensor
+    cores (operand split, batch pass, its finish, apply pass) x q, 2 on the
+    CUDA cores."""
     import torch
     from paper_2012_10469_gb300 import binding as B
     g = B.Group([s], stream=torch.cuda.current_stream().cuda_stream)
@@ -61,7 +62,7 @@ def test_tensor_core_minibatch_matches_oracle_and_cuda_cores(prec):
     V0, lam0 = prob.U, prob.w
     tc = _solve(prob, r, p, q, B.PRECISION[prec], eta, 7, V0, lam0, aligned=True)
     cc = _solve(prob, r, p, q, B.PRECISION[prec], eta, 7, V0, lam0, aligned=False)
-    assert _meas_kernels(tc) - _meas_kernels(cc) == q            # one more kernel per product
+    assert _meas_kernels(tc) - _meas_kernels(cc) == 2 * q        # two more kernels per product
     X = meg.init_X1(V0, lam0, meg.eps_schedule(0))
     f1 = obj.value(X)
     rows = []
