@@ -2121,10 +2121,12 @@ __device__ void meas_batch_tail(const SolveDev& s, int lb, bool warm, const int6
         if (b < Lb) sc[2 * (size_t)Lb + (size_t)b * MEG_KMAX + c] = Ps[rr][B + c];
     }
     __shared__ double bsum;
+    __shared__ float srs[MB_ROWS];
     static_assert(MB_ROWS == 32, "one warp per block's rows");
     if (tid < MB_ROWS) {
         const int b = lb * MB_ROWS + tid;
         double contrib = 0.0;
+        srs[tid] = 0.f;
         if (b < Lb) {
             const double aav = Ps[tid][2 * MEG_KMAX];
             const double sv = warm ? 0.0 : s.sm[SM_S];
@@ -2135,11 +2137,7 @@ __device__ void meas_batch_tail(const SolveDev& s, int lb, bool warm, const int6
             sc[b] = res;
             sc[Lb + b] = aav;
             if (!warm) s.bidx[b] = (int)sidx[tid];
-            if (s.mtc) {
-                // S_b for the tensor-core apply pass, as floats
-                const float sr = (2.f / (float)Lb) * (float)res;
-                for (int c = 0; c < k; ++c) mts_put(s.mts, k, b, c, sr * (float)Ps[tid][B + c]);
-            }
+            srs[tid] = (2.f / (float)Lb) * (float)res;   // S_b = srs T_b for the tensor-core apply pass
             // Minibatch (mode 0): the spectral size of (2/L) sum r_b a_b a_b^T is
             // estimated as for a weighted Wishart matrix,
             //   (2/L) rms_b(|r_b| ||a_b||^2) (1 + sqrt(L/n))^2.
@@ -2154,6 +2152,16 @@ __device__ void meas_batch_tail(const SolveDev& s, int lb, bool warm, const int6
         if (tid == 0) bsum = contrib;
     }
     __syncthreads();
+    if (s.mtc) {
+        // the block's 32 rows of S (0 past the batch) as 16-byte pieces of the image
+        __shared__ float Sx[MB_ROWS][MEG_KMAX + 1];
+        for (int e = tid; e < MB_ROWS * k; e += NT) {
+            const int rr = e / k, c = e % k;
+            Sx[rr][c] = srs[rr] * (float)Ps[rr][B + c];
+        }
+        __syncthreads();
+        mts_put32(s.mts, k, (int64_t)lb * MB_ROWS, &Sx[0][0], MEG_KMAX + 1);
+    }
     __shared__ int am_last;
     if (tid == 0) {
         const double v = bsum;
@@ -2367,13 +2375,22 @@ __global__ void __launch_bounds__(NT) k_bil_finish(const SolveDev* sds, int ns) 
         if (tid == 0) bsum = contrib;
     }
     __syncthreads();
-    // S rows: pair i's two rows, k values each
+    // S rows: pair i's two rows, k values each; row i (a_i) takes b_i^T W, row
+    // m + i (b_i) takes a_i^T W.  With m a multiple of MB_ROWS both sides' rows
+    // are whole 32-row halves of image chunks: written as 16-byte pieces.
+    __shared__ float Sx[2][MB_ROWS][MEG_KMAX + 1];
     for (int e = tid; e < 2 * MB_ROWS * k; e += NT) {
         const int side = e / (MB_ROWS * k), rem = e % (MB_ROWS * k);
         const int rr = rem / k, c = rem % k;
         const int64_t i = (int64_t)lb * MB_ROWS + rr;
-        if (i < m)   // row i (a_i) takes b_i^T W, row m + i (b_i) takes a_i^T W
-            mts_put(s.mts, k, side ? m + i : i, c, rs[rr] * Pp[side ? 0 : 1][rr][B + c]);
+        const float v = i < m ? rs[rr] * Pp[side ? 0 : 1][rr][B + c] : 0.f;
+        Sx[side][rr][c] = v;
+        if (m % MB_ROWS != 0 && i < m) mts_put(s.mts, k, side ? m + i : i, c, v);
+    }
+    if (m % MB_ROWS == 0) {
+        __syncthreads();
+        mts_put32(s.mts, k, (int64_t)lb * MB_ROWS, &Sx[0][0][0], MEG_KMAX + 1);
+        mts_put32(s.mts, k, m + (int64_t)lb * MB_ROWS, &Sx[1][0][0], MEG_KMAX + 1);
     }
     __shared__ int am_last;
     if (tid == 0) {

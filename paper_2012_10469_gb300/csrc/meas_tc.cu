@@ -46,8 +46,8 @@
 namespace {
 
 constexpr int MT_THREADS = 256;
-constexpr int MT_TMEM_COLS = 256;
-constexpr int MT_BATCH_COLS = 512;                            // two accumulators of N <= 192 columns
+constexpr int MT_TMEM_COLS = 64;                              // apply pass: two accumulators of P <= 32
+constexpr int MT_BATCH_COLS = 128;                            // two accumulators of NC <= 64 columns
 constexpr int MT_A_BYTES = MT_BM * MT_BK * 2;                 // 16 KB
 constexpr int MT_B_MAX = 192 * MT_BK * 2;                     // N <= 192 (B = 32: 3 x 64 columns)
 
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_meas_tc_split(const SolveDev* sd
 // other 16-column group.  Output: per row and part, the 2B products and the
 // part's ||a_b||^2, as floats in mtp, parts innermost ([row][column][part]) so
 // that the finish kernel reads an entry's parts as contiguous vectors.
-__global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev* sds, int ns) {
+__global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_batch(const SolveDev* sds, int ns) {
     pdl_wait();
     pdl_trigger();
     const int si = find_solve(sds, ns, PK_MTB, blockIdx.x);
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev*
         rowidx[tid] = b < Lb ? batch_row(s, warm, b) : -1;
     }
     const uint32_t tmem = mt_setup(m, MT_BATCH_COLS);       // (synchronises the block)
-    const uint32_t idesc = idesc_bf16(MT_BM, N);
+    const uint32_t idesc = idesc_bf16(MT_BM, NC);
     // A tile: thread = (row, half of the 64 columns), four 16-byte vectors
     const int arow = tid >> 1, ahalf = tid & 1;
     const int64_t ar = rowidx[arow];
@@ -309,8 +309,10 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev*
                 aa = fmaf(hi, hi, aa);
             }
         }
-        // slices 0 and 1 accumulate in columns 0.., slices 2 and 3 in columns 256..
-        // (32-wide accumulations); one commit for the chunk
+        // slices 0 and 1 accumulate in columns 0.., slices 2 and 3 in columns 64..
+        // (32-wide accumulations); each slice adds the lo, mid and hi pieces of
+        // [V | W] (sub-tiles 2 NC, NC, 0 rows into the image), small first; one
+        // commit for the chunk
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
@@ -318,8 +320,11 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev*
             const uint32_t a0 = smem_u32(m.a + st * MT_STAGE), b0 = smem_u32(m.b + st * MT_STAGE);
 #pragma unroll
             for (int kk = 0; kk < MT_BK / 16; ++kk)
-                umma_bf16(tmem + (uint32_t)((kk >> 1) * 256), sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32),
-                          idesc, (uint32_t)(kk & 1));
+#pragma unroll
+                for (int p = 2; p >= 0; --p)
+                    umma_bf16(tmem + (uint32_t)((kk >> 1) * 64), sdesc_sw128(a0 + kk * 32),
+                              sdesc_sw128(b0 + (uint32_t)(p * NC * 128 + kk * 32)), idesc,
+                              (uint32_t)((kk & 1) || p != 2));
             umma_commit(m.bar);
         }
         const bool done = mbar_wait(m.bar, parity);
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev*
         ok = __syncthreads_or(done ? 0 : 1) == 0;
         tc_fence_after();
         if (!ok) break;
-        // ---- drain: hi + mid + lo of each output column of both accumulators
+        // ---- drain: each output column of both accumulators
         const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
         for (int acc = 0; acc < 2; ++acc)
@@ -335,15 +340,10 @@ __global__ void __launch_bounds__(MT_THREADS, 1) k_meas_tc_batch(const SolveDev*
             for (int gi = 0; gi < 2; ++gi) {
                 const int g = (warp >> 2) + 2 * gi;         // this warp's 16-column groups
                 if (g < ngroups) {
-                    uint32_t vh[16], vm[16], vl[16];
-                    const uint32_t t0 = tb + (uint32_t)(acc * 256 + 16 * g);
-                    tmem_ld16(t0, vh);
-                    tmem_ld16(t0 + (uint32_t)NC, vm);
-                    tmem_ld16(t0 + (uint32_t)(2 * NC), vl);
+                    uint32_t v[16];
+                    tmem_ld16(tb + (uint32_t)(acc * 64 + 16 * g), v);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        csum_add(run[gi][j], rlo[gi][j],
-                                 (__uint_as_float(vh[j]) + __uint_as_float(vm[j])) + __uint_as_float(vl[j]));
+                    for (int j = 0; j < 16; ++j) csum_add(run[gi][j], rlo[gi][j], __uint_as_float(v[j]));
                 }
             }
         tc_fence_before();
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_apply(const SolveDev*
     extern __shared__ __align__(1024) unsigned char smraw[];
     const MtSmem m = mt_carve(smraw, 2);
     const uint32_t tmem = mt_setup(m);
-    const uint32_t idesc = idesc_bf16(MT_BM, N);
+    const uint32_t idesc = idesc_bf16(MT_BM, P);
     const int i0 = tile * MT_BM;
     const int warp = tid >> 5, quarter = warp & 3, lane = tid & 31;
     const int grow = quarter * 32 + lane;
@@ -459,13 +459,16 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_apply(const SolveDev*
         cp_async_wait1();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0) {                                     // pieces of S: lo, mid, hi (sub-tiles 2P, P, 0)
             tc_fence_after();
             const uint32_t a0 = smem_u32(m.a + st * MT_STAGE), b0 = smem_u32(m.b + st * MT_STAGE);
 #pragma unroll
             for (int kk = 0; kk < MT_BK / 16; ++kk)
-                umma_bf16(tmem + (uint32_t)((kk >> 1) * 128), sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32),
-                          idesc, (uint32_t)(kk & 1));
+#pragma unroll
+                for (int p = 2; p >= 0; --p)
+                    umma_bf16(tmem + (uint32_t)((kk >> 1) * 32), sdesc_sw128(a0 + kk * 32),
+                              sdesc_sw128(b0 + (uint32_t)(p * P * 128 + kk * 32)), idesc,
+                              (uint32_t)((kk & 1) || p != 2));
             umma_commit(m.bar);
         }
         const bool done = mbar_wait(m.bar, parity);
@@ -477,14 +480,10 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_apply(const SolveDev*
             const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
             for (int acc = 0; acc < 2; ++acc) {
-                uint32_t vh[16], vm[16], vl[16];
-                const uint32_t t0 = tb + (uint32_t)(acc * 128 + 16 * g);
-                tmem_ld16(t0, vh);
-                tmem_ld16(t0 + (uint32_t)P, vm);
-                tmem_ld16(t0 + (uint32_t)(2 * P), vl);
+                uint32_t v[16];
+                tmem_ld16(tb + (uint32_t)(acc * 32 + 16 * g), v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    csum_add(run[j], rlo[j], (__uint_as_float(vh[j]) + __uint_as_float(vm[j])) + __uint_as_float(vl[j]));
+                for (int j = 0; j < 16; ++j) csum_add(run[j], rlo[j], __uint_as_float(v[j]));
             }
         }
         tc_fence_before();

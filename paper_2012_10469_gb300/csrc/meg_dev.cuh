@@ -139,6 +139,36 @@ __host__ __device__ __forceinline__ size_t mts_image_bytes(int64_t rows, int k) 
     return (size_t)((rows + 63) / 64) * 3 * ((k + 15) / 16 * 16) * 128;
 }
 #ifdef __CUDACC__
+// piece p (0: hi, 1: mid, 2: lo) of the exact three-piece bf16 split of x
+__device__ __forceinline__ unsigned short split_piece(float x, int p) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    if (p == 0) return __bfloat16_as_ushort(h);
+    const float r1 = x - __bfloat162float(h);
+    const __nv_bfloat16 md = __float2bfloat16_rn(r1);
+    if (p == 1) return __bfloat16_as_ushort(md);
+    return __bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(md)));
+}
+// Rows b0 .. b0 + 31 of S (b0 a multiple of 32) from shared memory, sx[rr * ld + j]
+// for row b0 + rr and column j < k (rows past the batch hold 0), written as
+// 16-byte pieces: half of one chunk's 64 K positions in all 3 P image rows.
+// Every thread of the block takes part.
+__device__ __forceinline__ void mts_put32(unsigned short* img, int k, int64_t b0, const float* sx, int ld) {
+    const int P = (k + 15) / 16 * 16, kc0 = (int)(b0 & 63) >> 3;
+    unsigned char* base = (unsigned char*)img + (size_t)(b0 >> 6) * 3 * P * 128;
+    for (int e = threadIdx.x; e < 3 * P * 4; e += blockDim.x) {
+        const int q = e >> 2, v = e & 3, p = q / P, j = q % P;
+        unsigned short h[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) h[t] = split_piece(j < k ? sx[(v * 8 + t) * ld + j] : 0.f, p);
+        uint4 val;
+        val.x = (unsigned)h[0] | ((unsigned)h[1] << 16);
+        val.y = (unsigned)h[2] | ((unsigned)h[3] << 16);
+        val.z = (unsigned)h[4] | ((unsigned)h[5] << 16);
+        val.w = (unsigned)h[6] | ((unsigned)h[7] << 16);
+        *(uint4*)(base + q * 128 + (((kc0 + v) ^ (q & 7)) << 4)) = val;
+    }
+}
+// one element of S (any row)
 __device__ __forceinline__ void mts_put(unsigned short* img, int k, int64_t b, int j, float x) {
     const int P = (k + 15) / 16 * 16, kk = (int)(b & 63);
     unsigned char* base = (unsigned char*)img + (size_t)(b >> 6) * 3 * P * 128;
