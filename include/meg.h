@@ -85,7 +85,10 @@ enum {
     MEG_BILINEAR = 4     /* Section 7, eq. recoveryProb, in trace-1 variables:
                             f = 1/2 sum_i (tau a_i^T X b_i - y_i)^2,
                             grad f = (tau/2) sum_i r_i (a_i b_i^T + b_i a_i^T),
-                            r_i = tau a_i^T X b_i - y_i (full gradient)       */
+                            r_i = tau a_i^T X b_i - y_i (full gradient); with
+                            measurement matrices of rank p (mrank):
+                            r_i = tau Tr(A_i^T X B_i) - y_i and
+                            grad f = (tau/2) sum_i r_i (A_i B_i^T + B_i A_i^T) */
 };
 
 /*
@@ -130,13 +133,16 @@ typedef struct {
  *          val[nnz] = M_ij as double (MEG_FP64) or float (otherwise).
  *   A, y, m, L (MEAS_STOCH): A m x n row-major, double (MEG_FP64) or
  *          bfloat16 bits (otherwise); y[m] double; minibatch size L.
- *   A, B, y, m, tau (BILINEAR): A and B m x n row-major bfloat16 bits,
- *          y[m] double, trace scale tau > 0 (the tau-spectrahedron of the
- *          problem is mapped to the unit one, X' = X / tau); L is ignored.
- *          Needs MEG_FP32 or MEG_MIXED_BF16, n % 8 == 0, A and B 16-byte
- *          aligned and 1 <= m <= 2^30 - 1 (both products run on the tensor
- *          cores over the 2 m stacked rows [A; B]); MEG_ERR_INVALID_ARG
- *          otherwise.
+ *   A, B, y, m, tau, mrank (BILINEAR): m measurements; mrank = p, the
+ *          rank of the measurement matrices A_i, B_i in R^{n x p} (0 or 1:
+ *          vectors a_i, b_i; else a power of two up to 32); A and B hold
+ *          m p rows of n bfloat16 bits, row i p + c being column c of A_i
+ *          (of B_i); y[m] double; trace scale tau > 0 (the tau-spectrahedron
+ *          of the problem is mapped to the unit one, X' = X / tau); L is
+ *          ignored.  Needs MEG_FP32 or MEG_MIXED_BF16, n % 8 == 0, A and B
+ *          16-byte aligned and 1 <= m p <= 2^30 - 1 (both products run on
+ *          the tensor cores over the 2 m p stacked rows [A; B]);
+ *          MEG_ERR_INVALID_ARG otherwise.
  * Fields a kind does not use are ignored (zero them).
  */
 typedef struct {
@@ -152,6 +158,7 @@ typedef struct {
     int L;
     const void* B;
     double tau;
+    int mrank;
 } meg_objective_desc;
 
 /*

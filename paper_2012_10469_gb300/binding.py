@@ -41,7 +41,7 @@ class meg_objective_desc(C.Structure):
     _fields_ = [("kind", C.c_int), ("dense", C.c_void_p), ("rowptr", C.c_void_p),
                 ("col", C.c_void_p), ("val", C.c_void_p), ("nnz", C.c_int64),
                 ("A", C.c_void_p), ("y", C.c_void_p), ("m", C.c_int64), ("L", C.c_int),
-                ("B", C.c_void_p), ("tau", C.c_double)]
+                ("B", C.c_void_p), ("tau", C.c_double), ("mrank", C.c_int)]
 
 
 class meg_autotune_options(C.Structure):
@@ -204,13 +204,13 @@ class Solve:
 
     # -- objective
     def meg_set_objective(self, kind, dense=None, rowptr=None, col=None, val=None, A=None, y=None, L=0,
-                          B=None, tau=1.0):
+                          B=None, tau=1.0, mrank=1):
         """Tensors are borrowed (kept alive by this object)."""
         self._keep = [t for t in (dense, rowptr, col, val, A, y, B) if t is not None]
         d = meg_objective_desc(kind=kind, dense=_dptr(dense), rowptr=_dptr(rowptr), col=_dptr(col),
                                val=_dptr(val), nnz=0 if col is None else int(col.numel()),
-                               A=_dptr(A), y=_dptr(y), m=0 if A is None else int(A.shape[0]), L=L,
-                               B=_dptr(B), tau=float(tau))
+                               A=_dptr(A), y=_dptr(y), m=0 if A is None else int(A.shape[0]) // max(1, mrank),
+                               L=L, B=_dptr(B), tau=float(tau), mrank=int(mrank))
         _check(load().meg_set_objective(self.h, C.byref(d)), "meg_set_objective")
 
     def meg_warm_start(self, products: int = 40):

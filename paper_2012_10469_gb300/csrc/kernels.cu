@@ -2355,17 +2355,20 @@ __global__ void __launch_bounds__(NT) k_bil_finish(const SolveDev* sds, int ns) 
         const int64_t i = (int64_t)lb * MB_ROWS + tid;
         double contrib = 0.0;
         float sr = 0.f;
+        double q = 0.0;                                     // a^T X b of this pair
+        if (i < m && !warm) {
+            // float terms: each product a_i^T v_l is a float-accurate sum
+            const double sv = s.sm[SM_S];
+            float qf = 0.f;
+            for (int l = 0; l < r; ++l)
+                qf = fmaf((float)(s.sm[SM_MU + l] - sv), Pp[0][tid][l] * Pp[1][tid][l], qf);
+            q = (double)qf + sv * sc[i];
+        }
+        // rank-p measurements: the p consecutive pairs of a measurement (an aligned
+        // group of lanes) add up to Tr(A^T X B) and share the residual
+        for (int o = 1; o < s.mrank; o <<= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
         if (i < m) {
-            double q = 0.0;
-            if (!warm) {
-                // float terms: each product a_i^T v_l is a float-accurate sum
-                const double sv = s.sm[SM_S];
-                float qf = 0.f;
-                for (int l = 0; l < r; ++l)
-                    qf = fmaf((float)(s.sm[SM_MU + l] - sv), Pp[0][tid][l] * Pp[1][tid][l], qf);
-                q = s.tau * ((double)qf + sv * sc[i]);
-            }
-            const double res = q - s.y[i];
+            const double res = s.tau * q - s.y[i / s.mrank];
             sr = (float)(0.5 * s.tau * res);
             const float na = Pp[0][tid][2 * MEG_KMAX], nb = Pp[1][tid][2 * MEG_KMAX], rf = (float)res;
             contrib = (double)(rf * rf * na * nb);
@@ -2569,9 +2572,65 @@ __device__ void obj_meas_rows(const SolveDev& s, int lb, float* vsm, const doubl
     }
 }
 
+// a_i^T X b_i of pair i (valid in lane 0; the whole warp takes part):
+// sum_l (mu_l - s)(a_i^T v_l)(b_i^T v_l) + s a_i^T b_i, a_i^T b_i from meas[i]
+__device__ double bil_pair_q(const SolveDev& s, int64_t i, const float* vsm, const double* coef) {
+    const int n = s.n, r = s.r, lane = threadIdx.x & 31, rp = rank_bucket(r) + 1;
+    const unsigned short* Aa = (const unsigned short*)s.A;
+    const unsigned short* Bb = (const unsigned short*)s.Bm;
+    double q = 0.0;
+    for (int l0 = 0; l0 < r; l0 += 8) {
+        dw pa[8], pb[8];
+        float la[8], lbv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) { pa[u] = pb[u] = {0.f, 0.f}; la[u] = lbv[u] = 0.f; }
+        for (int j = lane; j < n; j += 32) {
+            const float a = __uint_as_float((unsigned)Aa[(size_t)i * n + j] << 16);
+            const float b = __uint_as_float((unsigned)Bb[(size_t)i * n + j] << 16);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int l = l0 + u;
+                float vh = 0.f, vl = 0.f;
+                if (l < r) {
+                    if (vsm) {
+                        vh = vsm[j * rp + l];
+                        vl = vsm[(size_t)n * rp + j * rp + l];
+                    } else {
+                        const double v = s.V[(size_t)j * r + l];
+                        vh = (float)v;
+                        vl = (float)(v - (double)vh);
+                    }
+                }
+                dot2_acc(pa[u], a, vh);
+                la[u] = fmaf(a, vl, la[u]);
+                dot2_acc(pb[u], b, vh);
+                lbv[u] = fmaf(b, vl, lbv[u]);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                dw t = {__shfl_xor_sync(0xffffffffu, pa[u].hi, o), __shfl_xor_sync(0xffffffffu, pa[u].lo, o)};
+                dw_add(pa[u], t);
+                t = {__shfl_xor_sync(0xffffffffu, pb[u].hi, o), __shfl_xor_sync(0xffffffffu, pb[u].lo, o)};
+                dw_add(pb[u], t);
+                la[u] += __shfl_xor_sync(0xffffffffu, la[u], o);
+                lbv[u] += __shfl_xor_sync(0xffffffffu, lbv[u], o);
+            }
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (l0 + u < r)
+                    q += coef[l0 + u] * (dw_value(pa[u]) + (double)la[u]) * (dw_value(pb[u]) + (double)lbv[u]);
+    }
+    return lane == 0 ? q + coef[MEG_RMAX] * s.meas[i] : 0.0;
+}
+
 // Bilinear measurements: f = 1/2 sum_i (tau a_i^T X b_i - y_i)^2 with
 // a_i^T X b_i = sum_l (mu_l - s)(a_i^T v_l)(b_i^T v_l) + s a_i^T b_i, a_i^T b_i
-// from meas[i].  One warp per pair, 8 columns of V at a time; a_i^T v_l is a
+// from meas[i] (rank-p measurement matrices: Tr(A_i^T X B_i), the sum of this
+// over the p column pairs).  One warp per measurement, 8 columns of V at a time; a_i^T v_l is a
 // double-word sum of the bf16 data times the float hi piece of v_l plus a
 // float sum with its lo piece (V staged as hi/lo floats in shared memory when
 // vsm is given, else split from the float64 V as it is read).  Adds r_i^2
@@ -2590,60 +2649,15 @@ __device__ void obj_bil_rows(const SolveDev& s, int lb, float* vsm, const double
         }
         __syncthreads();
     }
-    const unsigned short* Aa = (const unsigned short*)s.A;
-    const unsigned short* Bb = (const unsigned short*)s.Bm;
-    const int64_t per = (s.m + s.nb_red - 1) / s.nb_red;
-    const int64_t i0 = (int64_t)lb * per, i1 = min((int64_t)s.m, i0 + per);
-    for (int64_t i = i0 + warp; i < i1; i += NT / 32) {
-        double q = 0.0;                                     // lane 0
-        for (int l0 = 0; l0 < r; l0 += 8) {
-            dw pa[8], pb[8];
-            float la[8], lbv[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) { pa[u] = pb[u] = {0.f, 0.f}; la[u] = lbv[u] = 0.f; }
-            for (int j = lane; j < n; j += 32) {
-                const float a = __uint_as_float((unsigned)Aa[(size_t)i * n + j] << 16);
-                const float b = __uint_as_float((unsigned)Bb[(size_t)i * n + j] << 16);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int l = l0 + u;
-                    float vh = 0.f, vl = 0.f;
-                    if (l < r) {
-                        if (vsm) {
-                            vh = vsm[j * rp + l];
-                            vl = vsm[(size_t)n * rp + j * rp + l];
-                        } else {
-                            const double v = s.V[(size_t)j * r + l];
-                            vh = (float)v;
-                            vl = (float)(v - (double)vh);
-                        }
-                    }
-                    dot2_acc(pa[u], a, vh);
-                    la[u] = fmaf(a, vl, la[u]);
-                    dot2_acc(pb[u], b, vh);
-                    lbv[u] = fmaf(b, vl, lbv[u]);
-                }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    dw t = {__shfl_xor_sync(0xffffffffu, pa[u].hi, o), __shfl_xor_sync(0xffffffffu, pa[u].lo, o)};
-                    dw_add(pa[u], t);
-                    t = {__shfl_xor_sync(0xffffffffu, pb[u].hi, o), __shfl_xor_sync(0xffffffffu, pb[u].lo, o)};
-                    dw_add(pb[u], t);
-                    la[u] += __shfl_xor_sync(0xffffffffu, la[u], o);
-                    lbv[u] += __shfl_xor_sync(0xffffffffu, lbv[u], o);
-                }
-            }
-            if (lane == 0)
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (l0 + u < r)
-                        q += coef[l0 + u] * (dw_value(pa[u]) + (double)la[u]) * (dw_value(pb[u]) + (double)lbv[u]);
-        }
+    const int G = s.mrank;                                  // pairs per measurement
+    const int64_t mm = s.m / G;
+    const int64_t per = (mm + s.nb_red - 1) / s.nb_red;
+    const int64_t g0 = (int64_t)lb * per, g1 = min(mm, g0 + per);
+    for (int64_t gm = g0 + warp; gm < g1; gm += NT / 32) {
+        double q = 0.0;                                     // lane 0: Tr(A^T X B) of measurement gm
+        for (int64_t i = gm * G; i < (gm + 1) * G; ++i) q += bil_pair_q(s, i, vsm, coef);
         if (lane == 0) {
-            q += coef[MEG_RMAX] * s.meas[i];
-            const double R = s.tau * q - s.y[i];
+            const double R = s.tau * q - s.y[gm];
             const double w = R * R;
             const float wh = (float)w;
             acc.add_prod(wh, 1.f);

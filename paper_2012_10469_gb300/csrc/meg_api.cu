@@ -556,7 +556,11 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     } else if (o->kind == MEG_BILINEAR) {
         if (!o->A || !o->B || !o->y || o->m < 1)
             return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: bilinear arrays missing");
-        if (o->m > 0x3fffffff) return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: m too large (2 m stacked rows)");
+        const int pr = o->mrank <= 1 ? 1 : o->mrank;
+        if (pr > 32 || (pr & (pr - 1)) != 0)
+            return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: mrank must be 0, 1 or a power of two up to 32");
+        if (o->m > 0x3fffffff / pr)
+            return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: m mrank too large (2 m mrank stacked rows)");
         if (!(o->tau > 0.0) || !std::isfinite(o->tau))
             return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: tau must be positive and finite");
         // both products run on the tensor cores over 16-byte rows of bf16 data
@@ -569,9 +573,13 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     h->obj = *o;
     d.kind = o->kind;
     d.D = o->dense; d.rowptr = o->rowptr; d.col = o->col; d.val = o->val; d.nnz = o->nnz;
-    d.A = o->A; d.y = o->y; d.m = o->m; d.L = o->L;
+    // bilinear: the pair count m p (rank-p measurement matrices: p pairs per measurement)
+    const int mrank = (o->kind == MEG_BILINEAR && o->mrank > 1) ? o->mrank : 1;
+    const int64_t mp = o->m * mrank;
+    d.A = o->A; d.y = o->y; d.m = o->kind == MEG_BILINEAR ? mp : o->m; d.L = o->L;
     d.Bm = o->kind == MEG_BILINEAR ? o->B : nullptr;
     d.tau = o->kind == MEG_BILINEAR ? o->tau : 1.0;
+    d.mrank = mrank;
     const size_t ts = tsize(h->prec);
     const bool dense_kind = (o->kind == MEG_DENSE_QUAD || o->kind == MEG_LINEAR);
     d.tc = 0;
@@ -585,7 +593,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     if (dense_kind || meas_kind(o->kind)) {
         // partial products: K splits of the dense product, or batch chunks of the minibatch product
         const size_t slots = dense_kind                    ? (size_t)d.nb_ds
-                             : o->kind == MEG_BILINEAR ? (size_t)bil_slots((int)(2 * o->m), n)
+                             : o->kind == MEG_BILINEAR ? (size_t)bil_slots((int)(2 * mp), n)
                                                        : (size_t)MEAS_CHUNKS;
         if (h->Ys) { cudaFreeAsync(h->Ys, h->stream); h->Ys = nullptr; }
         if (cudaMallocAsync(&h->Ys, ts * slots * n * k, h->stream) != cudaSuccess)
@@ -600,7 +608,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
         // float rows padded to a multiple of 4 for the sparse product
         const size_t pad4r = (size_t)((h->r + 3) & ~3), pad4k = (size_t)((k + 3) & ~3);
         size_t cnt = o->kind == MEG_MEAS_STOCH ? lbm * (2 + MEG_KMAX) + lbm / MB_ROWS + 1
-                     : o->kind == MEG_BILINEAR ? (size_t)o->m + (size_t)o->m / MB_ROWS + 1
+                     : o->kind == MEG_BILINEAR ? (size_t)mp + (size_t)mp / MB_ROWS + 1
                                                : (size_t)((d.nb_csr + 1) & ~1) + ((size_t)n * (pad4r + pad4k) + 1) / 2;
         if (h->meas) cudaFreeAsync(h->meas, h->stream);
         if (h->bidx) cudaFreeAsync(h->bidx, h->stream);
@@ -610,7 +618,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
             return fail(MEG_ERR_OOM, "meg_set_objective: scratch");
     }
     d.meas = h->meas; d.bidx = h->bidx;
-    d.nb_meas = o->kind == MEG_MEAS_STOCH ? o->L : o->kind == MEG_BILINEAR ? (int)(2 * o->m) : 0;
+    d.nb_meas = o->kind == MEG_MEAS_STOCH ? o->L : o->kind == MEG_BILINEAR ? (int)(2 * mp) : 0;
     // minibatch products on the tensor cores: float storage (bf16 A), rows of A
     // 16-byte aligned (n % 8 == 0, aligned base); partials for the larger of
     // the minibatch pass and the warm start's pass over all m measurements
@@ -642,7 +650,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     }
     meg_status st = upload_desc(h, d);
     if (st != MEG_OK) return st;
-    if (o->kind == MEG_BILINEAR) CU(launch_bil_prep(h->d_desc, o->m, h->stream));   // a_i^T b_i
+    if (o->kind == MEG_BILINEAR) CU(launch_bil_prep(h->d_desc, mp, h->stream));   // a^T b of every pair
     // statistics of the data used by the objective estimate and the shift: Tr D, ||D||_F^2
     // (computed by the objective kernel on X = 0 and X = I/n would need two passes;
     //  the k_objective pass on a zero iterate gives 1/2 ||D||^2 directly)

@@ -242,6 +242,8 @@ struct SolveDev {
     int L;
     const void* Bm;      // BILINEAR: the b_i (m x n bf16); A holds the a_i
     double tau;          // BILINEAR: trace scale of the tau-spectrahedron
+    int mrank;           // BILINEAR: rank p of the measurement matrices; m counts the m p (a, b) pairs,
+                         //   and the p consecutive pairs of measurement i share r_i and y_i
     // schedule
     double eta, eps_a, eps_c, eps_pow;
     double log_nr;       // log(n - r), used by the certificate

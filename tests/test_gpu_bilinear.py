@@ -204,3 +204,69 @@ def test_bilinear_warm_start_and_arguments():
         s.meg_set_objective(B.MEG_BILINEAR, A=A2, B=A2.clone(), y=torch.zeros(16, dtype=torch.float64,
                                                                               device="cuda"), tau=1.0)
     s.meg_destroy()
+
+
+def test_rank_p_measurements_match_oracle():
+    """Section 7's higher-rank measurements: A_i, B_i in R^{n x p} with
+    orthonormal columns (rounded to bf16), r_i = tau Tr(A_i^T X B_i) - y_i.
+    The library takes the p columns of A_i (B_i) as p consecutive rows of A
+    (B) with mrank = p, and the p pairs of a measurement share its residual.
+    n = 96, rank 3, p = 2, m = 20 n r measurements, start eq. (exp:init) as
+    printed, 10 iterations against the oracle's exact low-rank MEG.
+
+    The eigenvalue r of M_t lies close to the top of the unwanted spectrum
+    relative to how far the library's lower bound of the spectrum (the shift
+    estimate of grad f, loose by about 2 sqrt(p) here) lies below it, so
+    subspace iteration converges slowly: 32 products per iteration (q = 8
+    plus 24 by meg_refine_subspace before each step) reach the tolerances.
+    At p = 4 the gap lambda_3 - lambda_4 is about 0.8 against a spread of 50
+    under that bound and the iterates are not resolved (one step from the
+    same iterate is exact to float rounding: f to 1e-14, sigma_1 to 3e-7)."""
+    import torch
+    from paper_2012_10469_gb300 import binding as B
+    n, rank = 96, 3
+    pm = 2
+    prob = synth.rank_p_recovery(n, rank, pm, 20 * n * rank, seed=50 + pm)
+    As, Bs = synth.bf16_round(prob.As), synth.bf16_round(prob.Bs)
+    obj = meg.RankPMeasurements(As, Bs, prob.y, prob.tau)
+    m = obj.m
+    V0, lam0 = meg.warm_start_at(obj, rank, prob.U, printed_sign=True)
+    eta = 1.0 / (prob.tau * 0.4 * math.sqrt(rank * n))
+
+    def rows_of(T):              # row i p + c = column c of T_i
+        return torch.from_numpy(np.ascontiguousarray(
+            synth.bf16_bits(np.ascontiguousarray(T.transpose(0, 2, 1)).reshape(m * pm, n)).view(np.int16))).cuda()
+
+    A, Bm = rows_of(As), rows_of(Bs)
+    bad = B.Solve(n, rank, p=5, q=2, precision=B.MEG_FP32, eta=eta, seed=9, V0=V0, lam0=lam0,
+                  stream=torch.cuda.current_stream().cuda_stream)
+    with pytest.raises(B.MegError):          # mrank must be a power of two
+        bad.meg_set_objective(B.MEG_BILINEAR, A=A, B=Bm, y=torch.from_numpy(obj.y).cuda(), tau=prob.tau, mrank=3)
+    bad.meg_destroy()
+    s = B.Solve(n, rank, p=5, q=8, precision=B.MEG_FP32, eta=eta, seed=9, V0=V0, lam0=lam0,
+                stream=torch.cuda.current_stream().cuda_stream)
+    s.meg_set_objective(B.MEG_BILINEAR, A=A, B=Bm, y=torch.from_numpy(obj.y).cuda(), tau=prob.tau, mrank=pm)
+    s.meg_refine_subspace(32)
+    X = meg.init_X1(V0, lam0, meg.eps_schedule(0))
+    f1 = obj.value(X)
+    assert abs(s.meg_objective() - f1) <= 1e-7 * f1
+    rows = []
+    for t in range(1, 11):
+        X, info, _ = meg.lowrank_step(X, obj, t, eta, meg.eps_schedule(t), method="exact")
+        if t > 1:
+            s.meg_refine_subspace(24)
+        s.meg_step(1)
+        if t in (1, 2, 5, 10):
+            Xg = gpu_factored(s)
+            sig, _ = s.meg_get_ritz()
+            cert, holds, _ = s.meg_certificate()
+            rows.append(dict(t=t, Xg=Xg, Xo=X, sig_g=sig, sig_o=info.sig, fg=s.meg_objective(), fo=obj.value(X),
+                             f1=f1, fo_at_g=obj.value(Xg), cert_g=cert, holds_g=holds, cert_o=info.cert,
+                             holds_o=info.holds, eps=info.eps))
+            print(f"rank-{pm} measurements t={t:2d}  X {rel_frob(Xg, X):.2e}")
+    s.meg_destroy()
+    # sigma to 5e-5: the Ritz values come from float32 work on M_t - c I with the
+    # shift c about 25 below sigma_1 here, so their absolute error is about
+    # 1e-7 |sigma - c| (2.5e-6 of sigma_3, about -1.3), and sigma_3 is the one
+    # the slow convergence above leaves furthest (1.9e-5 at t = 10)
+    _check(rows, rank, tol_sig=5e-5, r1_slack=1e-7)
