@@ -367,6 +367,7 @@ def run_serving(trace, budget_bytes: int, max_active: int = 1024):
     from paper_2012_10469_gb300 import binding as B
     srv = B.Server(budget_bytes, max_active=max_active, check_every=10, meas_check_every=250)
     results, errors = [], []
+    kind_of = {}                       # request id -> 0 (dense quadratic) or 1 (measurements)
 
     def submitter():
         try:
@@ -375,7 +376,7 @@ def run_serving(trace, budget_bytes: int, max_active: int = 1024):
                 delay = base + q.t - srv.meg_server_now()
                 if delay > 0:
                     time.sleep(delay)
-                srv.meg_server_submit(**serve_request_args(B, q))
+                kind_of[srv.meg_server_submit(**serve_request_args(B, q))] = q.kind
         except Exception as ex:  # surfaced below
             errors.append(ex)
 
@@ -404,7 +405,28 @@ def run_serving(trace, budget_bytes: int, max_active: int = 1024):
         "hit_max_iters": int(sum(1 for x in st if x == 5)),
         "failed": int(sum(1 for x in st if x not in (0, 5))),
         "makespan_s": t_last - t_first,
+        "per_class": {name: serving_class_stats([r for r in results if kind_of.get(r["id"]) == kind])
+                      for kind, name in ((0, "dense_quadratic"), (1, "measurements"))},
     }
+
+
+def serving_class_stats(results):
+    """Service time (admission to result) and queueing (submission to admission)
+    percentiles, iterations and outcome counts of one request class."""
+    if not results:
+        return {"requests": 0}
+    svc = np.array([r["t_done"] - r["t_admit"] for r in results])
+    que = np.array([r["t_admit"] - r["t_submit"] for r in results])
+    its = np.array([r["iters"] for r in results])
+    st = [r["status"] for r in results]
+    pct = lambda a, q: float(np.percentile(a, q))
+    return {"requests": len(results),
+            "service_p50_ms": 1e3 * pct(svc, 50), "service_p99_ms": 1e3 * pct(svc, 99),
+            "queue_p50_ms": 1e3 * pct(que, 50), "queue_p99_ms": 1e3 * pct(que, 99),
+            "iters_p50": pct(its, 50), "iters_p99": pct(its, 99),
+            "converged": int(sum(1 for x in st if x == 0)),
+            "hit_max_iters": int(sum(1 for x in st if x == 5)),
+            "failed": int(sum(1 for x in st if x not in (0, 5)))}
 
 
 def torch_fp32_solve(q, device, max_iters=SERVE_MAX_ITERS, tol=SERVE_TOL):

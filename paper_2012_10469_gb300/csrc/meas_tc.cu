@@ -310,21 +310,26 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_batch(const SolveDev*
             }
         }
         // slices 0 and 1 accumulate in columns 0.., slices 2 and 3 in columns 64..
-        // (32-wide accumulations); each slice adds the lo, mid and hi pieces of
-        // [V | W] (sub-tiles 2 NC, NC, 0 rows into the image), small first; one
-        // commit for the chunk
+        // (32-wide accumulations).  Within an accumulation the lo pieces of [V | W]
+        // (sub-tile 2 NC rows into the image) go first, then mid (NC), then hi (0):
+        // the small terms are added while the accumulator is small, so only the
+        // hi MMAs round at its full magnitude.  One commit for the chunk.
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             tc_fence_after();
             const uint32_t a0 = smem_u32(m.a + st * MT_STAGE), b0 = smem_u32(m.b + st * MT_STAGE);
 #pragma unroll
-            for (int kk = 0; kk < MT_BK / 16; ++kk)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int p = 2; p >= 0; --p)
-                    umma_bf16(tmem + (uint32_t)((kk >> 1) * 64), sdesc_sw128(a0 + kk * 32),
-                              sdesc_sw128(b0 + (uint32_t)(p * NC * 128 + kk * 32)), idesc,
-                              (uint32_t)((kk & 1) || p != 2));
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int kk = 2 * h + j;
+                        umma_bf16(tmem + (uint32_t)(h * 64), sdesc_sw128(a0 + kk * 32),
+                                  sdesc_sw128(b0 + (uint32_t)(p * NC * 128 + kk * 32)), idesc,
+                                  (uint32_t)(p != 2 || j != 0));
+                    }
             umma_commit(m.bar);
         }
         const bool done = mbar_wait(m.bar, parity);
@@ -459,16 +464,20 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_apply(const SolveDev*
         cp_async_wait1();
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {                                     // pieces of S: lo, mid, hi (sub-tiles 2P, P, 0)
+        if (tid == 0) {   // pieces of S per accumulation: lo, mid, hi (sub-tiles 2P, P, 0), small first
             tc_fence_after();
             const uint32_t a0 = smem_u32(m.a + st * MT_STAGE), b0 = smem_u32(m.b + st * MT_STAGE);
 #pragma unroll
-            for (int kk = 0; kk < MT_BK / 16; ++kk)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll
                 for (int p = 2; p >= 0; --p)
-                    umma_bf16(tmem + (uint32_t)((kk >> 1) * 32), sdesc_sw128(a0 + kk * 32),
-                              sdesc_sw128(b0 + (uint32_t)(p * P * 128 + kk * 32)), idesc,
-                              (uint32_t)((kk & 1) || p != 2));
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int kk = 2 * h + j;
+                        umma_bf16(tmem + (uint32_t)(h * 32), sdesc_sw128(a0 + kk * 32),
+                                  sdesc_sw128(b0 + (uint32_t)(p * P * 128 + kk * 32)), idesc,
+                                  (uint32_t)(p != 2 || j != 0));
+                    }
             umma_commit(m.bar);
         }
         const bool done = mbar_wait(m.bar, parity);
