@@ -367,16 +367,17 @@ def run_serving(trace, budget_bytes: int, max_active: int = 1024):
     from paper_2012_10469_gb300 import binding as B
     srv = B.Server(budget_bytes, max_active=max_active, check_every=10, meas_check_every=250)
     results, errors = [], []
-    kind_of = {}                       # request id -> 0 (dense quadratic) or 1 (measurements)
+    kind_of, index_of = {}, {}         # request id -> 0 (dense quadratic) or 1 (measurements); trace index
 
     def submitter():
         try:
             base = srv.meg_server_now()
-            for q in trace:
+            for j, q in enumerate(trace):
                 delay = base + q.t - srv.meg_server_now()
                 if delay > 0:
                     time.sleep(delay)
-                kind_of[srv.meg_server_submit(**serve_request_args(B, q))] = q.kind
+                rid = srv.meg_server_submit(**serve_request_args(B, q))
+                kind_of[rid], index_of[rid] = q.kind, j
         except Exception as ex:  # surfaced below
             errors.append(ex)
 
@@ -387,6 +388,7 @@ def run_serving(trace, budget_bytes: int, max_active: int = 1024):
         for rec, _V, _mu, _s in srv.meg_server_poll(max_out=512, timeout_ms=20):
             results.append(rec)
     th.join()
+    ticks, graph_ticks = srv.meg_server_tick_counts()
     srv.meg_server_destroy()
     if errors:
         raise errors[0]
@@ -405,6 +407,8 @@ def run_serving(trace, budget_bytes: int, max_active: int = 1024):
         "hit_max_iters": int(sum(1 for x in st if x == 5)),
         "failed": int(sum(1 for x in st if x not in (0, 5))),
         "makespan_s": t_last - t_first,
+        "ticks": ticks, "graph_ticks": graph_ticks,
+        "service_by_index": {index_of[r["id"]]: r["t_done"] - r["t_admit"] for r in results},
         "per_class": {name: serving_class_stats([r for r in results if kind_of.get(r["id"]) == kind])
                       for kind, name in ((0, "dense_quadratic"), (1, "measurements"))},
     }
@@ -512,34 +516,45 @@ def torch_fp32_solve(q, device, max_iters=SERVE_MAX_ITERS, tol=SERVE_TOL):
     return it, False
 
 
-def torch_fp32_serve_sample(trace, device, seconds: float):
-    """The plain float32 form on the trace's first requests, one at a time, for
-    about `seconds`; latency from a FIFO replay of the arrivals with the measured
-    service times."""
+def torch_fp32_serve_sample(trace, device, seconds: float, count: int = 50, gpu_service=None):
+    """The plain float32 form on `count` requests spread evenly over the trace
+    (every len/count-th arrival, both classes in their trace proportions), one
+    at a time, for at most about `seconds`; latency from a FIFO replay of
+    those arrivals with the measured service times; beside it the serving
+    loop's own service times of the same requests."""
     import torch
     torch_fp32_solve(trace[0], device, max_iters=20)        # load cuBLAS/cuSOLVER
     torch.cuda.synchronize()
-    serv, its, t_all = [], [], time.perf_counter()
-    for q in trace:
+    pick = list(range(0, len(trace), max(1, len(trace) // count)))[:count]
+    serv, its, kinds, t_all = [], [], [], time.perf_counter()
+    for j in pick:
         t0 = time.perf_counter()
-        it, _ok = torch_fp32_solve(q, device)
+        it, _ok = torch_fp32_solve(trace[j], device)
         torch.cuda.synchronize()
         serv.append(time.perf_counter() - t0)
         its.append(it)
+        kinds.append(trace[j].kind)
         if time.perf_counter() - t_all > seconds:
             break
     done, lat = 0.0, []
-    for q, sv in zip(trace, serv):
-        done = max(done, q.t) + sv
-        lat.append(done - q.t)
-    return {"requests": len(serv), "solves_per_s": len(serv) / sum(serv),
-            "service_p50_ms": 1e3 * float(np.percentile(serv, 50)),
-            "service_p99_ms": 1e3 * float(np.percentile(serv, 99)),
-            "latency_p50_ms": 1e3 * float(np.percentile(lat, 50)),
-            "latency_p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "iters_p50": float(np.percentile(its, 50)),
-            "what": "same algorithm and stopping rule in plain float32 torch ops, one request at a time "
-                    "(FIFO replay of the same arrivals for latency), on the trace's first requests"}
+    for j, sv in zip(pick, serv):
+        done = max(done, trace[j].t) + sv
+        lat.append(done - trace[j].t)
+    out = {"requests": len(serv), "requests_dense": kinds.count(0), "requests_measurements": kinds.count(1),
+           "solves_per_s": len(serv) / sum(serv),
+           "service_p50_ms": 1e3 * float(np.percentile(serv, 50)),
+           "service_p99_ms": 1e3 * float(np.percentile(serv, 99)),
+           "latency_p50_ms": 1e3 * float(np.percentile(lat, 50)),
+           "latency_p99_ms": 1e3 * float(np.percentile(lat, 99)),
+           "iters_p50": float(np.percentile(its, 50)),
+           "what": "same algorithm and stopping rule in plain float32 torch ops, one request at a time "
+                   "(FIFO replay of the same arrivals for latency), on requests spread over the trace"}
+    if gpu_service:
+        same = [gpu_service[j] for j in pick[:len(serv)] if j in gpu_service]
+        if same:
+            out["serving_loop_service_p50_ms_same_requests"] = 1e3 * float(np.percentile(same, 50))
+            out["service_ratio_p50"] = float(np.percentile(serv, 50)) / float(np.percentile(same, 50))
+    return out
 
 
 # --------------------------------------------------------------------------- main
@@ -709,7 +724,8 @@ def run_gpu(args):
                                        "dense quadratic (float32 data, noise 1e-4, plateau rule) / measurements "
                                        "(bf16 A, m=50000, L=256, f*=0), tol 1e-6, max_iters 5000, p=4, q=2, objective checked every "
                                        "10 (dense) / 250 (measurements) iterations")
-                serving["plain_fp32_form"] = torch_fp32_serve_sample(trace, device, args.serve_fp32_seconds)
+                serving["plain_fp32_form"] = torch_fp32_serve_sample(
+                    trace, device, args.serve_fp32_seconds, gpu_service=serving.pop("service_by_index", None))
             except Exception as ex:  # reported, never fatal
                 serving = {"error": repr(ex)[:300]}
         line = {
@@ -928,8 +944,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serve-requests", type=int, default=2000, help="serving trace length (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=500.0, help="mean arrivals per second")
-    ap.add_argument("--serve-fp32-seconds", type=float, default=30.0,
-                    help="time spent on the plain float32 form's sample of the trace")
+    ap.add_argument("--serve-fp32-seconds", type=float, default=180.0,
+                    help="time cap on the plain float32 form's 50 requests spread over the trace")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

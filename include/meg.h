@@ -396,6 +396,10 @@ meg_status meg_server_submit(meg_server s, const meg_request* rq, uint64_t* id);
 meg_status meg_server_poll(meg_server s, meg_result* out, int max_out, int* n_out, int timeout_ms);
 /* Requests submitted and finished so far. */
 meg_status meg_server_counts(meg_server s, int64_t* submitted, int64_t* finished);
+/* Ticks launched so far, and how many of them ran as a captured CUDA graph
+ * (a class's tick is captured once its group has held for a tick and is
+ * relaunched while the membership and the tick length stay the same). */
+meg_status meg_server_tick_counts(meg_server s, int64_t* ticks, int64_t* graph_ticks);
 /* The server clock (seconds since meg_server_create). */
 double meg_server_now(meg_server s);
 /* Stop the worker and free everything; unfinished requests are dropped. */

@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_server_submit": (C.c_int, [H, _P(meg_request), _P(C.c_uint64)]),
         "meg_server_poll": (C.c_int, [H, _P(meg_result), C.c_int, _P(C.c_int), C.c_int]),
         "meg_server_counts": (C.c_int, [H, _P(C.c_int64), _P(C.c_int64)]),
+        "meg_server_tick_counts": (C.c_int, [H, _P(C.c_int64), _P(C.c_int64)]),
         "meg_server_now": (C.c_double, [H]),
         "meg_server_destroy": (C.c_int, [H]),
         "meg_state_size": (C.c_int64, [H]),
@@ -439,6 +440,11 @@ class Server:
     def meg_server_counts(self):
         a, b = C.c_int64(), C.c_int64()
         _check(load().meg_server_counts(self.h, C.byref(a), C.byref(b)), "meg_server_counts")
+        return a.value, b.value
+
+    def meg_server_tick_counts(self):
+        a, b = C.c_int64(), C.c_int64()
+        _check(load().meg_server_tick_counts(self.h, C.byref(a), C.byref(b)), "meg_server_tick_counts")
         return a.value, b.value
 
     def meg_server_now(self) -> float:

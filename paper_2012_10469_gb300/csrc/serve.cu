@@ -15,7 +15,9 @@
 //                 on the device;
 //   ticks      -- a class runs `check` iterations of all members, then the
 //                 grouped objective pass; the host polls an event and never
-//                 blocks on a running tick;
+//                 blocks on a running tick.  From the second tick of an
+//                 unchanged group the tick is a captured CUDA graph, relaunched
+//                 until the membership or the tick length changes;
 //   retirement -- a member stops when (f - f*) <= tol (f(X_1) - f*) for a
 //                 known f*, or, when f* is unknown, when the decrease over
 //                 the last check interval is <= tol (f(X_1) - f(X_t)); also at
@@ -87,6 +89,14 @@ struct Class {
     int tick_len = 0;
     double* f_host = nullptr;          // pinned, one per member of the running tick
     int f_cap = 0;
+    // CUDA graph of a tick (its iterations and the objective pass with the copy of f):
+    // captured on the second tick of an unchanged group and relaunched while the
+    // group and the tick length stay the same
+    unsigned gen = 0;                  // bumped whenever the group is rebuilt
+    int ticks_same = 0;                // ticks launched since then
+    cudaGraphExec_t gexec = nullptr;
+    unsigned gexec_gen = 0;
+    int gexec_len = 0;
 };
 
 }  // namespace
@@ -102,6 +112,7 @@ struct meg_server_s {
     std::atomic<bool> stop{false};
     uint64_t next_id = 1;
     int64_t submitted = 0, finished = 0;
+    std::atomic<int64_t> ticks{0}, graph_ticks{0};   // ticks launched; of them from a captured graph
     // worker-owned
     std::vector<Class> classes;
     int active = 0;
@@ -118,6 +129,7 @@ struct meg_server_s {
     void admit_batch(std::vector<Req*>& ready);
     int class_of(const meg_request& rq);
     void launch_tick(Class& c);
+    meg_status capture_tick(Class& c, int len);
     void finish_tick(Class& c);
     void retire(Req* q);
 };
@@ -224,6 +236,9 @@ void meg_server_s::launch_tick(Class& c) {
     }
     if (c.dirty || !c.g) {
         if (c.g) { meg_group_destroy(c.g); c.g = nullptr; }
+        if (c.gexec) { cudaGraphExecDestroy(c.gexec); c.gexec = nullptr; }
+        ++c.gen;
+        c.ticks_same = 0;
         c.dirty = false;
         if (c.members.empty()) return;
         std::vector<meg_handle> hs;
@@ -242,14 +257,50 @@ void meg_server_s::launch_tick(Class& c) {
     int len = c.check;
     for (Req* q : c.members) len = std::min(len, std::max(1, q->rq.max_iters - q->iters));
     c.tick_len = len;
-    meg_status st = meg_group_launch(c.g, len);
-    if (st == MEG_OK) st = meg_internal::group_objective_enqueue(c.g, c.f_host);
+    meg_status st = MEG_OK;
+    if (c.gexec && c.gexec_gen == c.gen && c.gexec_len == len) {
+        st = cudaGraphLaunch(c.gexec, c.stream) == cudaSuccess ? MEG_OK : MEG_ERR_CUDA;
+        if (st == MEG_OK) ++graph_ticks;
+    } else if (c.ticks_same >= 1) {                     // the group held for a tick: capture this one
+        if (c.gexec) { cudaGraphExecDestroy(c.gexec); c.gexec = nullptr; }
+        st = capture_tick(c, len);
+        if (st == MEG_OK) ++graph_ticks;
+    } else {
+        st = meg_group_launch(c.g, len);
+        if (st == MEG_OK) st = meg_internal::group_objective_enqueue(c.g, c.f_host);
+    }
+    ++c.ticks_same;
+    ++ticks;
     if (st != MEG_OK) {
         for (Req* q : c.members) { q->status = st; q->finished = true; }
         return;
     }
     cudaEventRecord(c.ev, c.stream);
     c.inflight = true;
+}
+
+// Capture the tick's grouped iterations and objective pass (kernels and the
+// copy of f to pinned host memory, no allocation) on the class's stream, then
+// launch the graph.
+meg_status meg_server_s::capture_tick(Class& c, int len) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MEG_ERR_CUDA;
+    meg_status st = meg_group_launch(c.g, len);
+    if (st == MEG_OK) st = meg_internal::group_objective_enqueue(c.g, c.f_host);
+    const cudaError_t ce = cudaStreamEndCapture(c.stream, &graph);
+    if (st != MEG_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return st != MEG_OK ? st : MEG_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&c.gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        c.gexec = nullptr;
+        return MEG_ERR_CUDA;
+    }
+    c.gexec_gen = c.gen;
+    c.gexec_len = len;
+    return cudaGraphLaunch(c.gexec, c.stream) == cudaSuccess ? MEG_OK : MEG_ERR_CUDA;
 }
 
 void meg_server_s::finish_tick(Class& c) {
@@ -392,6 +443,7 @@ void meg_server_s::run() {
             delete q;
         }
         if (c.f_host) cudaFreeHost(c.f_host);
+        if (c.gexec) cudaGraphExecDestroy(c.gexec);
         if (c.ev) cudaEventDestroy(c.ev);
         if (c.stream) cudaStreamDestroy(c.stream);
     }
@@ -486,6 +538,14 @@ meg_status meg_server_counts(meg_server s, int64_t* submitted, int64_t* finished
     std::lock_guard<std::mutex> lk(s->mu);
     if (submitted) *submitted = s->submitted;
     if (finished) *finished = s->finished;
+    return MEG_OK;
+}
+
+meg_status meg_server_tick_counts(meg_server s, int64_t* ticks, int64_t* graph_ticks) {
+    if (!s) return sfail(MEG_ERR_INVALID_ARG, "meg_server_tick_counts: null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (ticks) *ticks = s->ticks.load();
+    if (graph_ticks) *graph_ticks = s->graph_ticks.load();
     return MEG_OK;
 }
 

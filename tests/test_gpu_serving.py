@@ -3,7 +3,7 @@
 * every request's result is the same alone and in a mix of requests of
   different n, r, objective and precision that share the GPU;
 * a served request matches the float64 oracle run for the same number of
-  iterations;
+  iterations, with its later ticks run as a captured CUDA graph;
 * admission respects the memory budget, and with room for several
   requests their work overlaps.
 """
@@ -42,7 +42,7 @@ def _requests(B):
     return reqs
 
 
-def _serve(B, reqs, budget=8 << 30, max_active=64, one_at_a_time=False, timeout=120.0):
+def _serve(B, reqs, budget=8 << 30, max_active=64, one_at_a_time=False, timeout=120.0, ticks=None):
     srv = B.Server(budget, max_active=max_active)
     out = {}
     try:
@@ -58,6 +58,8 @@ def _serve(B, reqs, budget=8 << 30, max_active=64, one_at_a_time=False, timeout=
             assert time.time() - t0 < timeout, "serving loop did not finish"
             for rec, V, mu, s in srv.meg_server_poll(timeout_ms=50):
                 out[rec["id"]] = (rec, V, mu, s)
+        if ticks is not None:
+            ticks.extend(srv.meg_server_tick_counts())
     finally:
         srv.meg_server_destroy()
     return [out[i] for i in ids]
@@ -92,7 +94,11 @@ def test_served_request_matches_oracle():
     V0, lam0 = meg.warm_start(obj, r)
     rq = dict(kind=B.MEG_DENSE_QUAD, n=n, r=r, data=p.M, precision=B.MEG_FP64, p=4, q=3, eta=1.0, seed=5,
               warm_start_products=0, V0=V0, lam0=lam0, tol=1e-6, max_iters=60)
-    (rec, V, mu, s), = _serve(B, [rq])
+    ticks = []
+    (rec, V, mu, s), = _serve(B, [rq], ticks=ticks)
+    # one member for 6 ticks of 10 iterations: the first launched plainly, the
+    # second captured as a graph, the rest relaunching it
+    assert ticks[0] == rec["iters"] // 10 and ticks[1] == ticks[0] - 1, (ticks, rec["iters"])
     assert rec["status"] in (B.MEG_OK, B.MEG_ERR_NOT_CONVERGED)
     Xo, _ = meg.lowrank_meg(obj, V0, lam0, rec["iters"], 1.0, method="exact")
     assert rel_frob(_X(V, mu, s), Xo) <= 1e-5
