@@ -205,6 +205,21 @@ meg_status meg_warm_start_many(const meg_handle* solves, int count, int products
  * stream and reports a device error as meg_step's callers see it. */
 meg_status meg_refine_subspace(meg_handle h, int products);
 
+/* meg_trace_exp_estimate -- an estimate of b = Tr exp(M_t), the scalar of the
+ * exact certificate (eq. convergenceGuaranteeExperiment), by sampling as the
+ * note after Lemma 2 suggests: Hutchinson's estimator over the k = r + p
+ * probe vectors u_j, the columns of U (host, n x k row-major float64, e.g.
+ * Gaussian or +-1 entries; the caller draws them), each u^T exp(M_t) u by
+ * `steps` Lanczos steps (Gauss quadrature, full reorthogonalisation) on
+ * the operator of the solve's next iteration, M_t = log X_t - eta grad f(X_t)
+ * (the minibatch gradient of step t for MEAS_STOCH).  *estimate receives
+ * (1/k) sum_j ||u_j||^2 e_1^T exp(T_j) e_1.  The iterate, its subspace block
+ * and t are unchanged.  Needs the objective and X_t, float storage
+ * (MEG_FP32 or MEG_MIXED_BF16) and 1 <= steps <= min(32, n); a solve in a
+ * group answers MEG_ERR_STATE.  Allocates (stream-ordered) and frees its
+ * scratch; synchronises the stream. */
+meg_status meg_trace_exp_estimate(meg_handle h, const double* U, int steps, double* estimate);
+
 /* meg_step -- run `nsteps` iterations of Algorithm 2 (t -> t + nsteps),
  * enqueued on the stream without a host synchronisation. */
 meg_status meg_step(meg_handle h, int nsteps);

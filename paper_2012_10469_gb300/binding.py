@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
         "meg_set_objective": (C.c_int, [H, _P(meg_objective_desc)]),
         "meg_warm_start": (C.c_int, [H, C.c_int]),
         "meg_refine_subspace": (C.c_int, [H, C.c_int]),
+        "meg_trace_exp_estimate": (C.c_int, [H, _P(C.c_double), C.c_int, _P(C.c_double)]),
         "meg_step": (C.c_int, [H, C.c_int]),
         "meg_solve": (C.c_int, [H, C.c_double, C.c_int, _P(C.c_int)]),
         "meg_set_fstar": (C.c_int, [H, C.c_double]),
@@ -216,6 +217,13 @@ class Solve:
 
     def meg_warm_start(self, products: int = 40):
         _check(load().meg_warm_start(self.h, products), "meg_warm_start")
+
+    def meg_trace_exp_estimate(self, U, steps: int) -> float:
+        """Tr exp(M_t) by Hutchinson over the columns of U (n x k) with Lanczos quadrature."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        out = C.c_double()
+        _check(load().meg_trace_exp_estimate(self.h, _f64p(U), steps, C.byref(out)), "meg_trace_exp_estimate")
+        return out.value
 
     def meg_refine_subspace(self, products: int):
         _check(load().meg_refine_subspace(self.h, products), "meg_refine_subspace")

@@ -2438,6 +2438,206 @@ __global__ void __launch_bounds__(NT) k_bil_prep(const SolveDev* sd, int64_t m) 
     if (lane == 0) s.meas[i] = acc;
 }
 
+// ==========================================================================
+// Tr exp(M_t) by sampling (the note after Lemma 2: the scalar b of the exact
+// certificate can be estimated instead of computed): Hutchinson's estimator
+// Tr exp(M) = E[u^T exp(M) u] over the k probe vectors u (the columns of the
+// solve's block), each quadrature u^T exp(M) u = ||u||^2 e_1^T exp(T) e_1 from
+// `steps` Lanczos steps on A = M_t - c I (the operator the products apply)
+// with full reorthogonalisation (two classical Gram-Schmidt passes per step),
+// T the tridiagonal of the Lanczos coefficients, and exp(M) = e^c exp(A).
+// One block per probe column; the basis is kept column-major per slot:
+// column j of slot i at Qb + (i k + j) n.  ab per column: [0] ||u||^2,
+// [1 + i] alpha_i, [1 + LZ_MAX + i] beta_i.
+
+// block sum of one double (every thread gets the result)
+__device__ double lz_block_sum(double v, double* red) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
+    return t;
+}
+
+// column col of W (float storage) and of its bf16 split (tensor-core path) set to
+// the float vector q; U = V^T W for the combine's log X part
+__device__ void lz_set_w(const SolveDev& s, int col, const float* q, double* red) {
+    const int n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
+    float* W = (float*)s.W;
+    for (int i = tid; i < n; i += NT) {
+        const float w = q[i];
+        W[(size_t)i * k + col] = w;
+        if (s.Wsp) {
+            const size_t kp = (size_t)s.tc_kpad, P = (size_t)(s.tc_npad / 3);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const float r1 = w - __bfloat162float(hi);
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+            s.Wsp[(size_t)col * kp + i] = __bfloat16_as_ushort(hi);
+            s.Wsp[(P + col) * kp + i] = __bfloat16_as_ushort(mid);
+            s.Wsp[(2 * P + col) * kp + i] = __bfloat16_as_ushort(lo);
+        }
+    }
+    for (int l = 0; l < r; ++l) {
+        double u = 0.0;
+        for (int i = tid; i < n; i += NT) u += s.V[(size_t)i * r + l] * (double)q[i];
+        u = lz_block_sum(u, red);
+        if (tid == 0) s.sm[SM_U + l * 32 + col] = u;
+    }
+}
+
+// q_0 = u / ||u|| for probe column col of U (n x k, float64, row-major)
+__global__ void __launch_bounds__(NT) k_lz_start(const SolveDev* sd, const double* U, float* Qb, double* ab) {
+    pdl_wait();
+    pdl_trigger();
+    const SolveDev& s = *sd;
+    const int n = s.n, k = s.k, col = blockIdx.x, tid = threadIdx.x;
+    if (col >= k) return;
+    __shared__ double red[NT / 32];
+    double a = 0.0;
+    for (int i = tid; i < n; i += NT) a += U[(size_t)i * k + col] * U[(size_t)i * k + col];
+    const double nrm2 = lz_block_sum(a, red);
+    const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+    float* q = Qb + (size_t)col * n;
+    for (int i = tid; i < n; i += NT) q[i] = (float)(U[(size_t)i * k + col] * inv);
+    if (tid == 0) ab[(size_t)col * (2 * LZ_MAX + 1)] = nrm2;
+    __syncthreads();
+    lz_set_w(s, col, q, red);
+}
+
+// Lanczos step j of column col, after Z = (M_t - c I) W: alpha_j = q_j^T z,
+// w = z - alpha_j q_j - beta_{j-1} q_{j-1}, two classical Gram-Schmidt passes
+// against q_0..q_j, beta_j = ||w||, q_{j+1} = w / beta_j into slot j + 1 and
+// W (a zero vector if w vanished)
+__global__ void __launch_bounds__(NT) k_lz_step(const SolveDev* sd, float* Qb, double* ab, int j, int steps) {
+    pdl_wait();
+    pdl_trigger();
+    const SolveDev& s = *sd;
+    const int n = s.n, k = s.k, col = blockIdx.x, tid = threadIdx.x;
+    if (col >= k || j < 0 || j >= steps || steps > LZ_MAX) return;
+    const size_t slot = (size_t)k * n;
+    const float* q0 = Qb + (size_t)col * n;                 // slot i at q0 + i * slot
+    const float* z = (const float*)s.Z;
+    double* abc = ab + (size_t)col * (2 * LZ_MAX + 1);
+    __shared__ double red[NT / 32];
+    __shared__ double hred[NT / 32][LZ_MAX];
+    __shared__ double hs[LZ_MAX];
+    double a = 0.0;
+    for (int i = tid; i < n; i += NT) a += (double)q0[(size_t)j * slot + i] * (double)z[(size_t)i * k + col];
+    const double alpha = lz_block_sum(a, red);
+    const double bprev = j > 0 ? abc[1 + LZ_MAX + j - 1] : 0.0;
+    float* w = (float*)q0 + (size_t)(j + 1) * slot;
+    for (int i = tid; i < n; i += NT) {
+        double v = (double)z[(size_t)i * k + col] - alpha * (double)q0[(size_t)j * slot + i];
+        if (j > 0) v -= bprev * (double)q0[(size_t)(j - 1) * slot + i];
+        w[i] = (float)v;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        double h[LZ_MAX];
+#pragma unroll
+        for (int l = 0; l < LZ_MAX; ++l) h[l] = 0.0;
+        for (int i = tid; i < n; i += NT) {
+            const double wi = (double)w[i];
+#pragma unroll
+            for (int l = 0; l < LZ_MAX; ++l)
+                if (l <= j) h[l] += (double)q0[(size_t)l * slot + i] * wi;
+        }
+        const int lane = tid & 31, wid = tid >> 5;
+#pragma unroll
+        for (int l = 0; l < LZ_MAX; ++l) {
+            if (l > j) break;
+            double v = h[l];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) hred[wid][l] = v;
+        }
+        __syncthreads();
+        if (tid <= j) {
+            double t = 0.0;
+            for (int ww = 0; ww < NT / 32; ++ww) t += hred[ww][tid];
+            hs[tid] = t;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += NT) {
+            double v = (double)w[i];
+            for (int l = 0; l <= j; ++l) v -= hs[l] * (double)q0[(size_t)l * slot + i];
+            w[i] = (float)v;
+        }
+        __syncthreads();
+    }
+    double b2 = 0.0;
+    for (int i = tid; i < n; i += NT) b2 += (double)w[i] * (double)w[i];
+    const double beta = sqrt(lz_block_sum(b2, red));
+    if (tid == 0) {
+        abc[1 + j] = alpha;
+        abc[1 + LZ_MAX + j] = beta;
+    }
+    if (j + 1 < steps) {
+        const double inv = beta > 1e-300 ? 1.0 / beta : 0.0;
+        for (int i = tid; i < n; i += NT) w[i] = (float)((double)w[i] * inv);
+        __syncthreads();
+        lz_set_w(s, col, w, red);
+    }
+}
+
+// the estimate: per column the tridiagonal T (cut at the first beta_j below
+// 1e-10 of the local scale: an invariant subspace), its eigenpairs by Jacobi,
+// ||u||^2 sum_i (e_1^T y_i)^2 exp(theta_i + c); the mean over the columns
+__global__ void __launch_bounds__(NT) k_lz_quad(const SolveDev* sd, const double* ab, int steps, double* out) {
+    pdl_wait();
+    pdl_trigger();
+    const SolveDev& s = *sd;
+    const int k = s.k, tid = threadIdx.x;
+    __shared__ double A[MEG_KMAX * MEG_LDK], Qm[MEG_KMAX * MEG_LDK], Bm[MEG_KMAX * MEG_LDK];
+    __shared__ double wv[MEG_KMAX], pr[3 * MEG_KMAX + 8];
+    __shared__ int len_s;
+    const double c = s.sm[SM_SHIFT];
+    double total = 0.0;                                      // thread 0
+    for (int col = 0; col < k; ++col) {
+        const double* abc = ab + (size_t)col * (2 * LZ_MAX + 1);
+        if (tid == 0) {
+            int len = steps;
+            for (int j = 0; j + 1 < steps; ++j) {
+                const double scale = fabs(abc[1 + j]) + (j > 0 ? abc[1 + LZ_MAX + j - 1] : 0.0);
+                if (!(abc[1 + LZ_MAX + j] > 1e-10 * scale)) { len = j + 1; break; }
+            }
+            len_s = len;
+        }
+        __syncthreads();
+        const int len = len_s;
+        for (int e = tid; e < len * len; e += NT) {
+            const int a = e / len, b = e % len;
+            double v = 0.0;
+            if (a == b) v = abc[1 + a];
+            else if (b == a + 1) v = abc[1 + LZ_MAX + a];
+            else if (a == b + 1) v = abc[1 + LZ_MAX + b];
+            A[a * MEG_LDK + b] = v;
+        }
+        __syncthreads();
+        kxk_jacobi(A, Qm, Bm, wv, pr, len, 60);
+        if (tid == 0) {
+            double v = 0.0;
+            for (int i = 0; i < len; ++i) v += Qm[i] * Qm[i] * exp(wv[i] + c);   // row 0 of the eigenvectors
+            total += abc[0] * v;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) out[0] = total / (double)k;
+}
+
+cudaError_t launch_lz_start(const GroupLaunch& g, const double* U, float* Qb, double* ab, int k) {
+    return launch_k(k_lz_start, dim3(k), dim3(NT), 0, g.stream, 1, g.d_solves, U, Qb, ab);
+}
+cudaError_t launch_lz_step(const GroupLaunch& g, float* Qb, double* ab, int j, int steps, int k) {
+    return launch_k(k_lz_step, dim3(k), dim3(NT), 0, g.stream, 1, g.d_solves, Qb, ab, j, steps);
+}
+cudaError_t launch_lz_quad(const GroupLaunch& g, const double* ab, int steps, double* out) {
+    return launch_k(k_lz_quad, dim3(1), dim3(NT), 0, g.stream, 1, g.d_solves, ab, steps, out);
+}
+
 // Y = (2/Lb) sum_b r_b a_b (a_b^T W): block = MA_ROWS rows of Y times one chunk
 // of the batch.  Thread (row i, column group of 8) accumulates over the
 // chunk's rows; a warp reads 32 consecutive elements of a row of A per step,
@@ -2904,6 +3104,12 @@ cudaError_t launch_row_island(void (*row)(const SolveDev*, int, int), void (*isl
     cudaError_t e = launch_clustered<T>(row, g, smem, phase);
     if (e != cudaSuccess) return e;
     return launch_k(island, dim3(g.ns), dim3(NT), island_smem(), g.stream, 1, g.d_solves, g.ns, phase);
+}
+
+// Z = (M_t - c I) W for float storage, without the factor step (Lanczos products)
+cudaError_t launch_combine_rows(const GroupLaunch& g) {
+    if (g.prec == MEG_FP64) return cudaErrorNotSupported;
+    return launch_clustered<float>(k_combine<float>, g, combine_smem(g.prec), PH_ADVANCE);
 }
 
 cudaError_t launch_combine(const GroupLaunch& g, int phase) {

@@ -775,6 +775,67 @@ meg_status meg_refine_subspace(meg_handle h, int products) {
     return check_device_status(h);
 }
 
+meg_status meg_trace_exp_estimate(meg_handle h, const double* U, int steps, double* estimate) {
+    meg_status st = ready(h, "meg_trace_exp_estimate");
+    if (st != MEG_OK) return st;
+    if (h->in_group) return fail(MEG_ERR_STATE, "meg_trace_exp_estimate: solve belongs to a group");
+    if (!U || !estimate) return fail(MEG_ERR_INVALID_ARG, "meg_trace_exp_estimate: null argument");
+    if (steps < 1 || steps > LZ_MAX || steps > h->n)
+        return fail(MEG_ERR_INVALID_ARG, "meg_trace_exp_estimate: need 1 <= steps <= min(32, n)");
+    if (h->prec == MEG_FP64) return fail(MEG_ERR_INVALID_ARG, "meg_trace_exp_estimate: float storage only");
+    const int n = h->n, k = h->k;
+    const SolveDev& d = h->desc;
+    const size_t wbytes = sizeof(float) * (size_t)n * k;
+    const size_t spbytes = h->Wsp ? (size_t)2 * d.tc_npad * d.tc_kpad : 0;
+    const size_t nab = (size_t)k * (2 * LZ_MAX + 1);
+    // scratch: the probes, the Lanczos basis (steps + 1 slots of n x k), the coefficients,
+    // the result, and copies of W, its split and the small state (restored at the end)
+    char* buf = nullptr;
+    const size_t b_U = sizeof(double) * (size_t)n * k, b_Q = sizeof(float) * (size_t)(steps + 1) * n * k;
+    const size_t b_ab = sizeof(double) * (nab + 1), b_sm = sizeof(double) * SM_TOTAL;
+    const size_t off_Q = (b_U + 255) & ~(size_t)255, off_ab = (off_Q + b_Q + 255) & ~(size_t)255;
+    const size_t off_W = (off_ab + b_ab + 255) & ~(size_t)255, off_sp = (off_W + wbytes + 255) & ~(size_t)255;
+    const size_t off_sm = (off_sp + spbytes + 255) & ~(size_t)255, total = off_sm + b_sm;
+    if (cudaMallocAsync((void**)&buf, total, h->stream) != cudaSuccess)
+        return fail(MEG_ERR_OOM, "meg_trace_exp_estimate: scratch");
+    double* dU = (double*)buf;
+    float* Qb = (float*)(buf + off_Q);
+    double* ab = (double*)(buf + off_ab);
+    double* dout = ab + nab;
+    auto body = [&]() -> meg_status {
+        CU(cudaMemcpyAsync(buf + off_W, h->W, wbytes, cudaMemcpyDeviceToDevice, h->stream));
+        if (spbytes) CU(cudaMemcpyAsync(buf + off_sp, h->Wsp, spbytes, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(buf + off_sm, h->sm, b_sm, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(dU, U, b_U, cudaMemcpyHostToDevice, h->stream));
+        const GroupLaunch g = solo_launch(h);
+        const int kind = d.kind;
+        const bool dense = kind == MEG_DENSE_QUAD || kind == MEG_LINEAR;
+        CU(launch_lz_start(g, dU, Qb, ab, k));
+        for (int j = 0; j < steps; ++j) {
+            if (meas_kind(kind)) CU(launch_meas_batch(g));
+            if (j == 0) CU(launch_begin(g));
+            if (dense) CU(launch_dense(g));
+            if (kind == MEG_CSR_QUAD) CU(launch_csr(g));
+            if (meas_kind(kind)) CU(launch_meas_apply(g));
+            CU(launch_combine_rows(g));
+            CU(launch_lz_step(g, Qb, ab, j, steps, k));
+        }
+        CU(launch_lz_quad(g, ab, steps, dout));
+        CU(cudaMemcpyAsync(estimate, dout, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        return MEG_OK;
+    };
+    st = body();
+    // the iterate's block, its split and the small state as they were
+    cudaMemcpyAsync(h->W, buf + off_W, wbytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (spbytes) cudaMemcpyAsync(h->Wsp, buf + off_sp, spbytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(h->sm, buf + off_sm, b_sm, cudaMemcpyDeviceToDevice, h->stream);
+    cudaFreeAsync(buf, h->stream);
+    if (st != MEG_OK) return st;
+    CU(cudaStreamSynchronize(h->stream));
+    return check_device_status(h);
+}
+
 meg_status meg_step(meg_handle h, int nsteps) {
     meg_status st = ready(h, "meg_step");
     if (st != MEG_OK) return st;

@@ -454,6 +454,12 @@ cudaError_t meas_tc_init();
 // bilinear measurements: c_i = a_i^T b_i of the m pairs of one solve into meas[0, m)
 cudaError_t launch_bil_prep(const SolveDev* d_solve, int64_t m, cudaStream_t st);
 cudaError_t launch_combine(const GroupLaunch& g, int phase);
+cudaError_t launch_combine_rows(const GroupLaunch& g);
+// Hutchinson + Lanczos estimate of Tr exp(M_t) (one solve, float storage): at most LZ_MAX steps
+#define LZ_MAX 32
+cudaError_t launch_lz_start(const GroupLaunch& g, const double* U, float* Qb, double* ab, int k);
+cudaError_t launch_lz_step(const GroupLaunch& g, float* Qb, double* ab, int j, int steps, int k);
+cudaError_t launch_lz_quad(const GroupLaunch& g, const double* ab, int steps, double* out);
 cudaError_t launch_orthonormalise(const GroupLaunch& g, int phase);
 cudaError_t launch_chain_kernel(const GroupLaunch& g, int which, int phase);
 cudaError_t launch_objective(const GroupLaunch& g, double* out_f);
