@@ -2308,120 +2308,6 @@ __global__ void __launch_bounds__(NT) k_meas_finish(const SolveDev* sds, int ns)
     meas_batch_tail(s, lb, warm, sidx, Ps);
 }
 
-// Bilinear measurements (Section 7, eq. recoveryProb, trace-1 variables):
-// second half of the tensor-core batch pass over the stacked rows [A; B].
-// Block lb takes the MB_ROWS pairs i = MB_ROWS lb + ...; the parts of rows i
-// and m + i are added in part order, giving a_i^T [V | W], ||a_i||^2 and
-// b_i^T [V | W], ||b_i||^2.  Then
-//   r_i = tau (sum_l (mu_l - s)(a_i^T v_l)(b_i^T v_l) + s a_i^T b_i) - y_i
-//   (mode 1, the warm start's -grad f(0): r_i = -y_i),
-//   S_i = (tau/2) r_i b_i^T W,   S_{m+i} = (tau/2) r_i a_i^T W
-// for the apply pass.  a_i^T b_i is precomputed (meas[i], k_bil_prep).
-// Shift estimate: grad f = (tau/2)(A^T D B + B^T D A), D = diag(r), so
-// ||grad f|| <= tau ||A^T D B|| <= tau (||A^T |D| A|| ||B^T |D| B||)^(1/2);
-// each factor is estimated as for a weighted Wishart matrix, which gives
-//   g = (tau / n) (1 + sqrt(n/m))^2 (m sum_i r_i^2 ||a_i||^2 ||b_i||^2)^(1/2).
-// As for the minibatch estimate it only centres the shift; Rayleigh-Ritz is
-// exact.
-__global__ void __launch_bounds__(NT) k_bil_finish(const SolveDev* sds, int ns) {
-    pdl_wait();
-    pdl_trigger();
-    const int si = find_solve(sds, ns, PK_MEAS, blockIdx.x);
-    const SolveDev& s = sds[si];
-    const int lb = blockIdx.x - s.off[PK_MEAS];
-    const int64_t m = s.m;
-    const int nblk = (int)((m + MB_ROWS - 1) / MB_ROWS);
-    if (lb < 0 || lb >= nblk || s.kind != MEG_BILINEAR) return;
-    const int tid = threadIdx.x, n = s.n, k = s.k, r = s.r;
-    const bool warm = (s.mode == 1);
-    const int Lb = s.nb_meas, B = k_bucket(k), NC = 2 * B, KS = meas_ks(Lb, n);
-    __shared__ float Pp[2][MB_ROWS][2 * MEG_KMAX + 1];     // [a or b][pair][column], ||.||^2 last
-    __shared__ float rs[MB_ROWS];
-    for (int e = tid; e < 2 * MB_ROWS * (NC + 1); e += NT) {
-        const int side = e / (MB_ROWS * (NC + 1)), rem = e % (MB_ROWS * (NC + 1));
-        const int rr = rem / (NC + 1), c = rem % (NC + 1);
-        const int64_t i = (int64_t)lb * MB_ROWS + rr;
-        float acc = 0.f;
-        if (i < m) {
-            const float* p0 = s.mtp + ((size_t)(side ? m + i : i) * (NC + 1) + c) * KS;
-            for (int p = 0; p < KS; ++p) acc += __ldcg(p0 + p);
-        }
-        Pp[side][rr][c == NC ? 2 * MEG_KMAX : c] = acc;
-    }
-    __syncthreads();
-    double* sc = s.meas;               // [m] a_i^T b_i, then one bound partial per block
-    __shared__ double bsum;
-    if (tid < MB_ROWS) {
-        const int64_t i = (int64_t)lb * MB_ROWS + tid;
-        double contrib = 0.0;
-        float sr = 0.f;
-        double q = 0.0;                                     // a^T X b of this pair
-        if (i < m && !warm) {
-            // float terms: each product a_i^T v_l is a float-accurate sum
-            const double sv = s.sm[SM_S];
-            float qf = 0.f;
-            for (int l = 0; l < r; ++l)
-                qf = fmaf((float)(s.sm[SM_MU + l] - sv), Pp[0][tid][l] * Pp[1][tid][l], qf);
-            q = (double)qf + sv * sc[i];
-        }
-        // rank-p measurements: the p consecutive pairs of a measurement (an aligned
-        // group of lanes) add up to Tr(A^T X B) and share the residual
-        for (int o = 1; o < s.mrank; o <<= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-        if (i < m) {
-            const double res = s.tau * q - s.y[i / s.mrank];
-            sr = (float)(0.5 * s.tau * res);
-            const float na = Pp[0][tid][2 * MEG_KMAX], nb = Pp[1][tid][2 * MEG_KMAX], rf = (float)res;
-            contrib = (double)(rf * rf * na * nb);
-        }
-        rs[tid] = sr;
-        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
-        if (tid == 0) bsum = contrib;
-    }
-    __syncthreads();
-    // S rows: pair i's two rows, k values each; row i (a_i) takes b_i^T W, row
-    // m + i (b_i) takes a_i^T W.  With m a multiple of MB_ROWS both sides' rows
-    // are whole 32-row halves of image chunks: written as 16-byte pieces.
-    __shared__ float Sx[2][MB_ROWS][MEG_KMAX + 1];
-    for (int e = tid; e < 2 * MB_ROWS * k; e += NT) {
-        const int side = e / (MB_ROWS * k), rem = e % (MB_ROWS * k);
-        const int rr = rem / k, c = rem % k;
-        const int64_t i = (int64_t)lb * MB_ROWS + rr;
-        const float v = i < m ? rs[rr] * Pp[side ? 0 : 1][rr][B + c] : 0.f;
-        Sx[side][rr][c] = v;
-        if (m % MB_ROWS != 0 && i < m) mts_put(s.mts, k, side ? m + i : i, c, v);
-    }
-    if (m % MB_ROWS == 0) {
-        __syncthreads();
-        mts_put32(s.mts, k, (int64_t)lb * MB_ROWS, &Sx[0][0][0], MEG_KMAX + 1);
-        mts_put32(s.mts, k, m + (int64_t)lb * MB_ROWS, &Sx[1][0][0], MEG_KMAX + 1);
-    }
-    __shared__ int am_last;
-    if (tid == 0) {
-        sc[(size_t)m + lb] = bsum;
-        __threadfence();
-        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
-        am_last = (atomicAdd(c, 1u) == (unsigned)(nblk - 1));
-        if (am_last) *c = 0u;
-    }
-    __syncthreads();
-    if (!am_last) return;
-    __shared__ double red[NT];
-    const double* bp = sc + m;
-    double v = 0.0;
-    for (int q2 = tid; q2 < nblk; q2 += NT) v += __ldcg(bp + q2);
-    red[tid] = v;
-    __syncthreads();
-    for (int h = NT / 2; h > 0; h >>= 1) {
-        if (tid < h) red[tid] = red[tid] + red[tid + h];
-        __syncthreads();
-    }
-    if (tid == 0) {
-        const float fm = (float)m, fn = (float)n;
-        const float f = 1.f + sqrtf(fn / fm);
-        s.sm[SM_RESID_BOUND] = (double)((float)s.tau / fn * f * f * sqrtf(fm * (float)red[0]));
-    }
-}
-
 // c_i = a_i^T b_i of the bilinear pairs (bf16 products are exact in float;
 // sums in float64), one warp per pair, into meas[i].
 __global__ void __launch_bounds__(NT) k_bil_prep(const SolveDev* sd, int64_t m) {
@@ -3076,14 +2962,12 @@ cudaError_t launch_meas_batch(const GroupLaunch& g) {
     if ((g.meas_tc || g.meas_bil) && (e = launch_meas_tc_batch(g)) != cudaSuccess) return e;
     if (g.meas_tc && (e = launch_k(k_meas_finish, grid, blk, 0, g.stream, 1, g.d_solves, g.ns)) != cudaSuccess)
         return e;
-    if (g.meas_bil && (e = launch_k(k_bil_finish, grid, blk, 0, g.stream, 1, g.d_solves, g.ns)) != cudaSuccess)
-        return e;
     if (g.meas_plain) e = launch_k(k_meas_batch<float>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
     return e;
 }
 
 cudaError_t launch_meas_apply(const GroupLaunch& g) {
-    if (g.blocks[PK_MEAS] == 0) return cudaSuccess;
+    if (g.blocks[PK_MAP] == 0) return cudaSuccess;
     const dim3 grid(g.blocks[PK_MAP]), blk(NT);
     if (g.prec == MEG_FP64) return launch_k(k_meas_apply<double>, grid, blk, 0, g.stream, 1, g.d_solves, g.ns);
     cudaError_t e = cudaSuccess;

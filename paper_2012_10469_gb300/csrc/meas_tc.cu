@@ -32,11 +32,12 @@
 // then MEG_ERR_TIMEOUT is recorded, the CTA waits for its own MMAs, frees its
 // tensor memory and returns) and drains the accumulator with tcgen05.ld.
 //
-// Bilinear kind: the batch rows are the 2m stacked rows (row i = a_i, row
-// m + i = b_i), every step; the finish kernel pairs rows i and m + i into
-// r_i = tau a_i^T X b_i - y_i and writes S_i = (tau/2) r_i b_i^T W and
-// S_{m+i} = (tau/2) r_i a_i^T W, so the apply pass over the stacked rows gives
-// (tau/2) sum_i r_i (a_i b_i^T + b_i a_i^T) W = grad f W.
+// Bilinear kind: the batch rows are the stacked rows of [A; B] in 128-row
+// tiles of 64 pairs (their a, then their b), every step; the batch pass's
+// epilogue pairs the two halves into r_i = tau a_i^T X b_i - y_i and writes the
+// S of row a_i, (tau/2) r_i b_i^T W, and of row b_i, (tau/2) r_i a_i^T W, so the
+// apply pass over the stacked rows gives (tau/2) sum_i r_i (a_i b_i^T +
+// b_i a_i^T) W = grad f W.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -68,10 +69,14 @@ __device__ __forceinline__ int64_t batch_row(const SolveDev& s, bool warm, int b
                      (uint64_t)s.m);
 }
 
-// start of stacked row j: a_j for j < m; for the bilinear kind b_{j - m} for j >= m
+// start of batch row j: row j of A; for the bilinear kind row j of tile j / 128
+// (a of pair 64 (j / 128) + j mod 64 in its first 64 rows, b in the others),
+// nullptr for a padding pair past the last one
 __device__ __forceinline__ const unsigned short* stacked_row(const SolveDev& s, int64_t j) {
-    if (j < s.m) return (const unsigned short*)s.A + (size_t)j * s.n;
-    return (const unsigned short*)s.Bm + (size_t)(j - s.m) * s.n;
+    if (s.kind != MEG_BILINEAR) return (const unsigned short*)s.A + (size_t)j * s.n;
+    const int64_t i = (j >> 7) * 64 + (j & 63);
+    if (i >= s.m) return nullptr;
+    return (const unsigned short*)((j & 64) ? s.Bm : s.A) + (size_t)i * s.n;
 }
 
 // byte offset of element (row q, k) of a K-major 128-byte-swizzled tile
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(MT_THREADS) k_meas_tc_split(const SolveDev* sd
     const SolveDev& s = sds[si];
     const int lb = blockIdx.x - s.off[PK_MTB];
     const int Lb = s.nb_meas, n = s.n, k = s.k, r = s.r, tid = threadIdx.x;
-    const int G = (Lb + MT_BM - 1) / MT_BM * meas_ks(Lb, n);
+    const int G = (Lb + MT_BM - 1) / MT_BM * batch_ks(s.kind, Lb, n);
     if (!s.mtc || (s.kind != MEG_MEAS_STOCH && s.kind != MEG_BILINEAR) || lb < 0 || lb >= G) return;
     const int nch = (n + MT_BK - 1) / MT_BK;
     const bool warm = (s.mode == 1);
@@ -225,6 +230,92 @@ __global__ void __launch_bounds__(MT_THREADS) k_meas_tc_split(const SolveDev* sd
 }
 
 // ==========================================================================
+// Bilinear kind (Section 7, eq. recoveryProb, trace-1 variables): the end of a
+// batch-pass tile, whose rows 0-63 hold a_i^T [V | W] and ||a_i||^2 and rows
+// 64-127 the same for b_i (Ps, 128 x (NC + 1) floats), i = 64 tile + row:
+//   r_i = tau (sum_l (mu_l - s)(a_i^T v_l)(b_i^T v_l) + s a_i^T b_i) - y_i
+//   (mode 1, the warm start's -grad f(0): r_i = -y_i; rank-p measurement
+//   matrices: the p pairs of a measurement sum to tau Tr(A^T X B) and share
+//   its residual), with a_i^T b_i from meas[i];
+//   S of row a_i = (tau/2) r_i b_i^T W, S of row b_i = (tau/2) r_i a_i^T W, as
+//   16-byte pieces of the S image (the tile is image chunks 2 tile, 2 tile + 1);
+// and the shift estimate: grad f = (tau/2)(A^T D B + B^T D A), D = diag(r), so
+// ||grad f|| <= tau (||A^T |D| A|| ||B^T |D| B||)^(1/2), each factor estimated
+// as for a weighted Wishart matrix:
+//   g = (tau / n) (1 + sqrt(n/m))^2 (m sum_i r_i^2 ||a_i||^2 ||b_i||^2)^(1/2)
+// (m pairs).  Like the minibatch estimate it only centres the shift; Rayleigh-
+// Ritz is exact.  The last tile to finish combines the per-tile sums in a
+// fixed order.  Every thread of the block takes part.
+__device__ void bil_tile_finish(const SolveDev& s, int tile, const float* Ps, float* Sx) {
+    const int tid = threadIdx.x, n = s.n, k = s.k, r = s.r;
+    const int B = k_bucket(k), NC = 2 * B, ld = NC + 1;
+    const int64_t m = s.m, i0 = (int64_t)tile * 64;
+    const bool warm = (s.mode == 1);
+    double* sc = s.meas;                                    // [m] a_i^T b_i, then one partial per tile
+    __shared__ float sr_s[64];
+    __shared__ double bs[2];
+    if (tid < 64) {
+        const int64_t i = i0 + tid;
+        double q = 0.0;
+        if (i < m && !warm) {
+            // float terms: each product a_i^T v_l is a float-accurate sum
+            const double sv = s.sm[SM_S];
+            float qf = 0.f;
+            for (int l = 0; l < r; ++l)
+                qf = fmaf((float)(s.sm[SM_MU + l] - sv), Ps[tid * ld + l] * Ps[(64 + tid) * ld + l], qf);
+            q = (double)qf + sv * sc[i];
+        }
+        for (int o = 1; o < s.mrank; o <<= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        double contrib = 0.0;
+        float sr = 0.f;
+        if (i < m) {
+            const double res = s.tau * q - s.y[i / s.mrank];
+            sr = (float)(0.5 * s.tau * res);
+            const float rf = (float)res;
+            contrib = (double)(rf * rf * Ps[tid * ld + NC] * Ps[(64 + tid) * ld + NC]);
+        }
+        sr_s[tid] = sr;
+        for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+        if ((tid & 31) == 0) bs[tid >> 5] = contrib;
+    }
+    __syncthreads();
+    // S rows of the tile: row p < 64 (a_p) takes b_p^T W, row 64 + p (b_p) takes a_p^T W
+    for (int e = tid; e < 128 * k; e += MT_THREADS) {
+        const int rr = e / k, c = e % k, pp = rr & 63;
+        Sx[rr * (MEG_KMAX + 1) + c] = sr_s[pp] * Ps[(rr < 64 ? 64 + pp : pp) * ld + B + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+        mts_put32(s.mts, k, (int64_t)tile * 128 + 32 * h, Sx + 32 * h * (MEG_KMAX + 1), MEG_KMAX + 1);
+    __shared__ int am_last;
+    const int ntiles = (int)((m + 63) / 64);
+    if (tid == 0) {
+        sc[(size_t)m + tile] = bs[0] + bs[1];
+        __threadfence();
+        unsigned* c = s.ctr + (s.nb_red + RED_GROUP - 1) / RED_GROUP + 2;
+        am_last = (atomicAdd(c, 1u) == (unsigned)(ntiles - 1));
+        if (am_last) *c = 0u;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __shared__ double red[MT_THREADS];
+    double v = 0.0;
+    for (int q2 = tid; q2 < ntiles; q2 += MT_THREADS) v += __ldcg(sc + m + q2);
+    red[tid] = v;
+    __syncthreads();
+    for (int h = MT_THREADS / 2; h > 0; h >>= 1) {
+        if (tid < h) red[tid] = red[tid] + red[tid + h];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        const float fm = (float)m, fn = (float)n;
+        const float f = 1.f + sqrtf(fn / fm);
+        s.sm[SM_RESID_BOUND] = (double)((float)s.tau / fn * f * f * sqrtf(fm * (float)red[0]));
+    }
+}
+
+// ==========================================================================
 // Batch pass.  CTA (tile, part): 128 batch rows b times the columns [V | W]
 // (B each, zero beyond r and k), the part's K chunks of the n-long
 // contraction.  The B operand holds the three pieces of the float values,
@@ -240,7 +331,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_batch(const SolveDev*
     const SolveDev& s = sds[si];
     const int lb = blockIdx.x - s.off[PK_MTB];
     const int Lb = s.nb_meas, n = s.n, k = s.k, tid = threadIdx.x;
-    const int mtiles = (Lb + MT_BM - 1) / MT_BM, KS = meas_ks(Lb, n);
+    const int mtiles = (Lb + MT_BM - 1) / MT_BM, KS = batch_ks(s.kind, Lb, n);
     if (!s.mtc || (s.kind != MEG_MEAS_STOCH && s.kind != MEG_BILINEAR) || lb < 0 || lb >= mtiles * KS) return;
     const int mt = lb % mtiles, part = lb / mtiles;
     const int nch = (n + MT_BK - 1) / MT_BK;
@@ -259,7 +350,9 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_batch(const SolveDev*
     // A tile: thread = (row, half of the 64 columns), four 16-byte vectors
     const int arow = tid >> 1, ahalf = tid & 1;
     const int64_t ar = rowidx[arow];
-    const unsigned short* arp = ar >= 0 ? stacked_row(s, ar) : (const unsigned short*)s.A;
+    const unsigned short* rowp = ar >= 0 ? stacked_row(s, ar) : nullptr;
+    const bool live = rowp != nullptr;                      // a row of data (not past the batch)
+    const unsigned short* arp = live ? rowp : (const unsigned short*)s.A;
     float aa = 0.f;                                         // this thread's part of ||a||^2
     // accumulator drain: rows (lanes) and 16-column groups of this warp
     const int warp = tid >> 5, quarter = warp & 3, lane = tid & 31;
@@ -279,7 +372,7 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_batch(const SolveDev*
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int kc = ahalf * 4 + v;                   // 16-byte piece of the row
-            const bool pred = ar >= 0 && k0 + kc * 8 < n;
+            const bool pred = live && k0 + kc * 8 < n;
             cp_async16(As + arow * 128 + ((kc ^ (arow & 7)) << 4), pred ? arp + k0 + kc * 8 : arp, pred);
         }
         const unsigned short* src = s.mtb + (size_t)c * N * 64;
@@ -357,6 +450,26 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_batch(const SolveDev*
     cp_async_wait0();                                       // no copy in flight when the CTA ends
     // ---- partials of this part: columns, then ||a||^2 (the two threads of a row add theirs)
     aa += __shfl_xor_sync(0xffffffffu, aa, 1);
+    if (s.kind == MEG_BILINEAR) {
+        // the tile's 64 pairs are finished here: products through shared memory
+        // (the stage buffers are free: no copy in flight, the last MMA waited for)
+        float* Ps = (float*)m.a;
+        __syncthreads();
+        if (ok) {
+#pragma unroll
+            for (int gi = 0; gi < 2; ++gi) {
+                const int g = (warp >> 2) + 2 * gi;
+                if (g < ngroups)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) Ps[grow * (NC + 1) + 16 * g + j] = run[gi][j] + rlo[gi][j];
+            }
+            if (ahalf == 0) Ps[arow * (NC + 1) + NC] = aa;
+        }
+        __syncthreads();
+        if (ok) bil_tile_finish(s, mt, Ps, Ps + MT_BM * (NC + 1));
+        mt_teardown(m, tmem, s, !ok, MT_BATCH_COLS);
+        return;
+    }
     const int b = mt * MT_BM + grow;
     if (ok && b < Lb) {
         float* out = s.mtp + (size_t)b * (NC + 1) * KS + part;
@@ -423,7 +536,8 @@ __global__ void __launch_bounds__(MT_THREADS, 2) k_meas_tc_apply(const SolveDev*
             pv[j] = make_uint4(0u, 0u, 0u, 0u);
             if (b < Lb && i0 + ii < n) {
                 const int64_t row = full ? (int64_t)b : (int64_t)s.bidx[b];
-                pv[j] = *(const uint4*)(stacked_row(s, row) + i0 + ii);
+                const unsigned short* rp = stacked_row(s, row);
+                if (rp) pv[j] = *(const uint4*)(rp + i0 + ii);
             }
         }
     };

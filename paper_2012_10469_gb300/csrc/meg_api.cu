@@ -173,16 +173,18 @@ int blocks_of(const SolveDev& d, int kind) {
         case PK_DENSE: return (dense && !d.tc) ? d.nb_dm * d.nb_ds : 0;
         case PK_CSR: return d.kind == MEG_CSR_QUAD ? d.nb_csr : 0;
         case PK_DTC: return (dense && d.tc) ? (int)tc_chunks_of(d) : 0;
-        // minibatch: batch rows; bilinear: pairs (its batch rows are the 2 m stacked rows)
+        // minibatch: blocks of batch rows of the finish (the bilinear kind finishes
+        // its pairs in the batch pass's epilogue)
         case PK_MEAS:
-            if (bil) return (int)((d.m + MB_ROWS - 1) / MB_ROWS);
+            if (bil) return 0;
             return d.kind == MEG_MEAS_STOCH ? (d.nb_meas + MB_ROWS - 1) / MB_ROWS : 0;
         case PK_MAP:
             if (!meas_kind(d.kind)) return 0;
             return (d.mtc ? (d.n + MT_BM - 1) / MT_BM : (d.n + MA_ROWS - 1) / MA_ROWS) *
                    apply_slots(d.kind, d.nb_meas, d.n, d.mtc);
         case PK_MTB:
-            return (meas_kind(d.kind) && d.mtc) ? (d.nb_meas + MT_BM - 1) / MT_BM * meas_ks(d.nb_meas, d.n) : 0;
+            return (meas_kind(d.kind) && d.mtc) ? (d.nb_meas + MT_BM - 1) / MT_BM * batch_ks(d.kind, d.nb_meas, d.n)
+                                                : 0;
         default: return 0;
     }
 }
@@ -371,9 +373,9 @@ int64_t meg_footprint(int n, int r, int p, int precision, int kind) {
     if (kind == MEG_MEAS_STOCH)
         b += ts * (int64_t)MEAS_CHUNKS * n * k;   // (+ scratch of 8 (34 m + m/8) bytes and
                                                   //  4 (2 k_bucket(k) + 1) m tensor-core partials)
-    if (kind == MEG_BILINEAR)                     // apply-pass slots for large m (+ 8 (m + m/32) bytes and
+    if (kind == MEG_BILINEAR)                     // apply-pass slots for large m (+ 8 (m + m/32) bytes of
         b += ts * (int64_t)std::min(BIL_SLOTS_MAX, (4 * 152 + (n + MT_BM - 1) / MT_BM - 1) / ((n + MT_BM - 1) / MT_BM)) *
-             n * k;                               //  8 (2 k_bucket(k) + 1 + k) m of partials and S)
+             n * k;                               //  scratch and the S image, 12 P bytes per pair)
     if (precision == MEG_MIXED_BF16 && n % 8 == 0) b += 2 * (int64_t)((3 * k + 15) / 16 * 16) * ((n + 63) / 64 * 64);
     b += 4 * (nb_red + groups) * 2 * RED_MAX_ENTRIES;
     b += 4 * (groups + 3) + 8 * SM_TOTAL + 8;
@@ -559,7 +561,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
         const int pr = o->mrank <= 1 ? 1 : o->mrank;
         if (pr > 32 || (pr & (pr - 1)) != 0)
             return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: mrank must be 0, 1 or a power of two up to 32");
-        if (o->m > 0x3fffffff / pr)
+        if (o->m > 0x3fffff00 / pr)
             return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: m mrank too large (2 m mrank stacked rows)");
         if (!(o->tau > 0.0) || !std::isfinite(o->tau))
             return fail(MEG_ERR_INVALID_ARG, "meg_set_objective: tau must be positive and finite");
@@ -593,7 +595,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     if (dense_kind || meas_kind(o->kind)) {
         // partial products: K splits of the dense product, or batch chunks of the minibatch product
         const size_t slots = dense_kind                    ? (size_t)d.nb_ds
-                             : o->kind == MEG_BILINEAR ? (size_t)bil_slots((int)(2 * mp), n)
+                             : o->kind == MEG_BILINEAR ? (size_t)bil_slots((int)bil_rows(mp), n)
                                                        : (size_t)MEAS_CHUNKS;
         if (h->Ys) { cudaFreeAsync(h->Ys, h->stream); h->Ys = nullptr; }
         if (cudaMallocAsync(&h->Ys, ts * slots * n * k, h->stream) != cudaSuccess)
@@ -618,7 +620,7 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
             return fail(MEG_ERR_OOM, "meg_set_objective: scratch");
     }
     d.meas = h->meas; d.bidx = h->bidx;
-    d.nb_meas = o->kind == MEG_MEAS_STOCH ? o->L : o->kind == MEG_BILINEAR ? (int)(2 * mp) : 0;
+    d.nb_meas = o->kind == MEG_MEAS_STOCH ? o->L : o->kind == MEG_BILINEAR ? (int)bil_rows(mp) : 0;
     // minibatch products on the tensor cores: float storage (bf16 A), rows of A
     // 16-byte aligned (n % 8 == 0, aligned base); partials for the larger of
     // the minibatch pass and the warm start's pass over all m measurements
@@ -630,8 +632,8 @@ meg_status meg_set_objective(meg_handle h, const meg_objective_desc* o) {
     if (o->kind == MEG_BILINEAR ||
         (o->kind == MEG_MEAS_STOCH && h->prec != MEG_FP64 && n % 8 == 0 && ((uintptr_t)o->A % 16) == 0)) {
         const size_t cols = (size_t)2 * k_bucket(k) + 1;
-        const size_t rows = o->kind == MEG_BILINEAR
-                                ? (size_t)meas_ks(d.nb_meas, n) * d.nb_meas
+        const size_t rows = o->kind == MEG_BILINEAR     // (no partials: the batch pass finishes its tiles)
+                                ? 0
                                 : std::max((size_t)meas_ks(o->L, n) * o->L, (size_t)meas_ks((int)o->m, n) * o->m);
         // S: one row per batch row (bilinear: per stacked row)
         const size_t srows = o->kind == MEG_BILINEAR ? (size_t)d.nb_meas : (size_t)std::max<int64_t>(o->L, o->m);
@@ -1404,7 +1406,7 @@ int meg_group_kernels_per_step(meg_group g) {
     // minibatch: batch and apply passes (tensor cores: the operand split, batch pass, its
     // finish, apply pass; the bilinear kind shares the tensor-core passes and has its own finish)
     const bool tcp = g->gl.meas_tc || g->gl.meas_bil;
-    const int meas = g->has_meas ? (tcp ? 3 : 0) + (g->gl.meas_tc ? 1 : 0) + (g->gl.meas_bil ? 1 : 0) +
+    const int meas = g->has_meas ? (tcp ? 3 : 0) + (g->gl.meas_tc ? 1 : 0) +
                                        (g->gl.meas_plain ? 2 : 0)
                                  : 0;
     const int per = dense + csr + meas + (g->gl.prec == MEG_FP64 ? 6 : 4);

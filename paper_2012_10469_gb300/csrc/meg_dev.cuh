@@ -186,6 +186,15 @@ __device__ __forceinline__ void mts_put(unsigned short* img, int k, int64_t b, i
 }
 #endif
 
+// Bilinear kind: the stacked batch rows come in 128-row tiles, tile t holding
+// the 64 pairs 64 t .. 64 t + 63: its rows 0-63 are their a, rows 64-127 their b
+// (pairs past the last one are zero rows), so that one batch-pass CTA sees
+// both halves of its pairs and finishes them in its epilogue; the CTA covers
+// all of n (one part).
+__host__ __device__ __forceinline__ int64_t bil_rows(int64_t pairs) { return 128 * ((pairs + 63) / 64); }
+__host__ __device__ __forceinline__ int batch_ks(int kind, int Lb, int n) {
+    return kind == MEG_BILINEAR ? 1 : meas_ks(Lb, n);
+}
 // partial-product slots of a member's apply pass (k_combine adds them in order)
 __host__ __device__ __forceinline__ int apply_slots(int kind, int Lb, int n, int mtc) {
     return kind == MEG_BILINEAR ? bil_slots(Lb, n) : meas_slots(Lb, mtc);
