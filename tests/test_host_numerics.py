@@ -36,3 +36,31 @@ def test_one_pass_refined_factor_orthonormality():
             assert refined <= 16 * u * np.sqrt(k), (kappa, refined)
             if kappa >= 1e3:
                 assert plain >= 1e-3 * kappa ** 2 * u, (kappa, plain)   # what the refinement removes
+
+
+def test_bilinear_shift_estimate_bounds_the_gradient():
+    """The bilinear kind's size of grad f for the shift (the Wishart form of
+    the Cauchy-Schwarz bound, g = (tau/n)(1 + sqrt(n/m))^2 (m sum_i r_i^2
+    ||a_i||^2 ||b_i||^2)^(1/2)) lies above ||grad f||_2 on the Section 7
+    instance at X = 0 (the warm start's operator) and along the iterates, as
+    the shift of subspace iteration needs (a lower bound of the spectrum)."""
+    import math
+    import synth
+    from oracle import meg
+    n, rank = 96, 3
+    p = synth.bilinear_recovery(n, rank, seed=4)
+    obj = meg.BilinearMeasurements(p.A, p.B, p.y, p.tau)
+    m = obj.m
+    na2, nb2 = np.sum(p.A ** 2, 1), np.sum(p.B ** 2, 1)
+
+    def est(r):
+        return p.tau * (1 + math.sqrt(n / m)) ** 2 / n * math.sqrt(m * np.sum(r * r * na2 * nb2))
+
+    assert est(-obj.y) >= np.abs(np.linalg.eigvalsh(-obj.neg_grad0_apply(np.eye(n)))).max()
+    V0, lam0 = meg.warm_start_at(obj, rank, p.U, printed_sign=True)
+    X = meg.init_X1(V0, lam0, meg.eps_schedule(0))
+    eta = 1.0 / (p.tau * 0.4 * math.sqrt(rank * n))
+    for t in range(1, 6):
+        G = obj.grad_dense(X)
+        assert est(obj.residual(X)) >= np.abs(np.linalg.eigvalsh(0.5 * (G + G.T))).max(), t
+        X, _, _ = meg.lowrank_step(X, obj, t, eta, meg.eps_schedule(t), method="exact")
