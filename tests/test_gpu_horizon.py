@@ -15,7 +15,7 @@ The oracle's eigensolver runs to a residual of 1e-12 (subspace iteration
 for the dense and sparse problems, its block Krylov solver for the
 measurement problem, whose bulk of nearly equal eigenvalues makes subspace
 iteration slow), so its iterates are those of exact low-rank MEG.
-Tolerances (the benchmark spec): X_t relative Frobenius <= 1e-5, sigma_1..r
+Tolerances: X_t relative Frobenius <= 1e-5, sigma_1..r
 relative <= 1e-6, f relative <= 1e-6 (the denominator per workload is
 stated at each test).  Each test prints its measured errors.
 """
