@@ -804,6 +804,18 @@ def other_kernel_rooflines(device, stream, hbm_peak):
                                  "frac": alg / (ms / 1e3) / 1e9 / hbm_peak, "nnz": nnz}
     g.meg_group_destroy()
     s.meg_destroy()
+    out["minibatch_product_n2048"] = minibatch_timing(device, stream)
+    out["bilinear_n600_r20"] = bilinear_timing(device, stream, hbm_peak)
+    return out
+
+
+def minibatch_timing(device, stream):
+    """The n = 2048 stochastic-measurement workload (m = 50000, L = 256, bf16 A,
+    r = 4, p = 8): one minibatch product (operand split, batch pass, finish and
+    apply pass on the tensor cores) timed alone, warm, back to back."""
+    import torch
+    import synth
+    from paper_2012_10469_gb300 import binding as B
     prob = synth.config(3)
     n, L, k = prob.n, prob.L, 4 + 8
     s = B.Solve(n, 4, p=8, q=6, precision=B.MEG_MIXED_BF16, eta=1.0 / (4 * (1 + n / L)), seed=1003, stream=stream,
@@ -813,22 +825,20 @@ def other_kernel_rooflines(device, stream, hbm_peak):
     s.meg_set_objective(B.MEG_MEAS_STOCH, A=A, y=y, L=L)
     g = B.Group([s], stream=stream)
     ms = g.meg_group_time_product(50)
+    g.meg_group_destroy()
+    s.meg_destroy()
     alg = 2 * L * n * 2
     # tensor-core work of the two passes: bf16 A times the three bf16 pieces of the
     # float operands, [V | W] (2 k_bucket(k) columns) and S (k padded to 16 columns)
     kb = 8 if k <= 8 else 16 if k <= 16 else 32
     tflop = 2 * L * n * 3 * 2 * kb + 2 * n * L * 3 * ((k + 15) // 16 * 16)
-    out["minibatch_product_n2048"] = {"bound": "latency (L2-resident batch)", "engine": "tcgen05 (bf16, float pieces)",
-                                      "ms_per_launch": ms, "kernels": 3,
-                                      "bytes_per_launch": alg, "achieved_GBs": alg / (ms / 1e3) / 1e9,
-                                      "flops_implicit": 4 * L * n * k, "flops_explicit_syrk": n * (n + 1) * L,
-                                      "tensor_flops": tflop,
-                                      "tensor_TFLOPs": tflop / (ms / 1e3) / 1e12,
-                                      "tensor_frac_of_bf16_peak": tflop / (ms / 1e3) / 1e12 / BF16_TFLOPS}
-    g.meg_group_destroy()
-    s.meg_destroy()
-    out["bilinear_n600_r20"] = bilinear_timing(device, stream, hbm_peak)
-    return out
+    return {"bound": "latency (L2-resident batch)", "engine": "tcgen05 (bf16, float pieces)",
+            "ms_per_launch": ms, "kernels": 4,
+            "bytes_per_launch": alg, "achieved_GBs": alg / (ms / 1e3) / 1e9,
+            "flops_implicit": 4 * L * n * k, "flops_explicit_syrk": n * (n + 1) * L,
+            "tensor_flops": tflop,
+            "tensor_TFLOPs": tflop / (ms / 1e3) / 1e12,
+            "tensor_frac_of_bf16_peak": tflop / (ms / 1e3) / 1e12 / (BF16_TFLOPS or bf16_peak())}
 
 
 def bilinear_timing(device, stream, hbm_peak):
