@@ -140,7 +140,7 @@ typedef struct {
  *          (of B_i); y[m] double; trace scale tau > 0 (the tau-spectrahedron
  *          of the problem is mapped to the unit one, X' = X / tau); L is
  *          ignored.  Needs MEG_FP32 or MEG_MIXED_BF16, n % 8 == 0, A and B
- *          16-byte aligned and 1 <= m p <= 2^30 - 1 (both products run on
+ *          16-byte aligned and 1 <= m p <= 2^30 - 256 (both products run on
  *          the tensor cores over the 2 m p stacked rows [A; B]);
  *          MEG_ERR_INVALID_ARG otherwise.
  * Fields a kind does not use are ignored (zero them).
